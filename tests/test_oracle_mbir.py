@@ -1,0 +1,102 @@
+"""Pins of the oracle's MBIR pieces (Sec. 3: objective, gradient, optimizer).
+
+The optimizer's iterates are not printed in the paper; these tests pin what
+mathematics fixes: the gradient of the objective (central differences), the
+power-iteration norm (dense eigenvalue), and that with no prior and unit
+weights the accelerated gradient with restart converges to the least-squares
+solution of the dense system (normal equations).
+"""
+import math
+
+import numpy as np
+
+import oracle
+from test_oracle_radon import _closed_form_matrix
+
+RNG = np.random.default_rng(4242)
+
+
+def _tiny(N=8, A=24, D=14):
+    th = oracle.default_angles(A)
+    return th, _closed_form_matrix(N, D, th)
+
+
+def test_data_gradient_is_dense_normal_equation_residual():
+    N, A, D = 8, 10, 14
+    th, M = _tiny(N, A, D)
+    x = RNG.standard_normal((1, N, N))
+    b = RNG.standard_normal((1, A, D))
+    w = RNG.uniform(0.2, 1.0, (1, A, D))
+    G, g = oracle.data_grad(x, b, w, th)
+    r = M @ x.ravel() - b.ravel()
+    assert abs(G - 0.5 * np.sum(w.ravel() * r * r)) < 1e-10
+    assert np.abs(g.ravel() - M.T @ (w.ravel() * r)).max() < 1e-10
+
+
+def test_objective_gradient_matches_central_differences():
+    N, A, D = 8, 12, 14
+    th = oracle.default_angles(A)
+    x = 0.3 * RNG.standard_normal((2, N, N))
+    b = RNG.standard_normal((2, A, D))
+    w = RNG.uniform(0.2, 1.0, (2, A, D))
+    lam = 0.05
+    prior = oracle.PAPER_PRIOR
+    G, H, g = oracle.objective_grad(x, b, w, lam, prior, 3, th)
+    for _ in range(4):
+        d = RNG.standard_normal(x.shape)
+        h = 1e-6
+        Gp, Hp, _ = oracle.objective_grad(x + h * d, b, w, lam, prior, 3, th)
+        Gm, Hm, _ = oracle.objective_grad(x - h * d, b, w, lam, prior, 3, th)
+        fd = ((Gp + Hp) - (Gm + Hm)) / (2 * h)
+        an = float(np.sum(g * d))
+        assert abs(fd - an) <= 1e-6 * abs(an) + 1e-7
+
+
+def test_power_norm_matches_dense_eigenvalue():
+    N, A, D = 8, 10, 14
+    th, M = _tiny(N, A, D)
+    w = RNG.uniform(0.2, 1.0, (1, A, D))
+    lam = oracle.power_norm(N, A, D, w, RNG.standard_normal((1, N, N)), 300, th)
+    ev = np.linalg.eigvalsh(M.T @ (w.ravel()[:, None] * M)).max()
+    assert abs(lam - ev) <= 1e-8 * ev
+
+
+def test_no_prior_unit_weight_converges_to_least_squares():
+    N, A, D = 8, 24, 14
+    th, M = _tiny(N, A, D)
+    xt = RNG.standard_normal((N, N))
+    b = (M @ xt.ravel()).reshape(1, A, D) + 0.01 * RNG.standard_normal((1, A, D))
+    xls = np.linalg.lstsq(M, b.ravel(), rcond=None)[0]
+    L = np.linalg.norm(M, 2) ** 2
+    x, log = oracle.mbir_solve(b, None, N, 4000, 1.0 / L, lam=0.0, theta=th, return_log=True)
+    assert np.linalg.norm(x.ravel() - xls) <= 1e-8 * np.linalg.norm(xls)
+    assert any(e["restart"] for e in log)
+    # the same schedule without restart is markedly slower on this problem
+    x_nr = oracle.mbir_solve(b, None, N, 4000, 1.0 / L, lam=0.0, theta=th, restart=False)
+    assert np.linalg.norm(x_nr.ravel() - xls) > 1e3 * np.linalg.norm(x.ravel() - xls)
+
+
+def test_first_step_is_a_gradient_step_from_zero():
+    N, A, D = 8, 6, 14
+    th = oracle.default_angles(A)
+    b = RNG.standard_normal((1, A, D))
+    step = 1e-3
+    x1 = oracle.mbir_solve(b, None, N, 1, step, lam=0.0, theta=th)
+    # at x = 0 the gradient is -A^T b
+    assert np.abs(x1 - step * oracle.radon_adj(b, N, th)).max() < 1e-14
+
+
+def test_objective_decreases_with_prior():
+    N, A, D = 16, 12, 24
+    th = oracle.default_angles(A)
+    xt = np.zeros((1, N, N))
+    xt[0, 4:12, 5:11] = 1.0
+    b = oracle.radon_fwd(xt, A, D, th)
+    lam = 1e-3
+    L = 1.05 * oracle.power_norm(N, A, D, None, RNG.standard_normal((1, N, N)), 30, th) \
+        + lam * oracle.prior_lipschitz()
+    x, log = oracle.mbir_solve(b, None, N, 60, 1.0 / L, lam=lam, theta=th, dims=2, return_log=True)
+    G, H, _ = oracle.objective_grad(x, b, None, lam, oracle.PAPER_PRIOR, 2, th)
+    G0, H0, _ = oracle.objective_grad(np.zeros_like(x), b, None, lam, oracle.PAPER_PRIOR, 2, th)
+    assert G + H < 0.2 * (G0 + H0)
+    assert math.isfinite(G + H)
