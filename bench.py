@@ -1,0 +1,395 @@
+"""Benchmark: MBIR slice-iterations per second on the full synthetic volume.
+
+Workload (one GPU): 1024 slices of 2048 x 2048, 128 angles over [0, pi),
+2896 detector bins, kernel width 7, oversampling 2; Poisson data at I0 = 1e4
+from analytic ellipsoid line integrals (pixel size 1/N); weights = counts/I0;
+26-neighbour qGGMRF prior (p = 1.2, sigma = 1/0.7, c = 1e-4).  One step is one
+accelerated-gradient iteration over the whole resident volume: A, residual,
+A^T, prior, FP64 reductions and the update.  Inputs (17 GB per volume array)
+are far larger than L2, so no flush is needed between steps.
+
+  python bench.py [--gpus N --steps K --warmup W]      # CUDA path
+  python bench.py --impl reference ...                  # FP64 oracle on host cores
+
+Prints one JSON line (rank 0).  Under torchrun each rank solves its own
+replica volume (no collective on the data path; weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "MBIR slice-iter/s 2048²×128ang batched vs plain (err≤1e-4); A/Aᵀ HBM frac"
+UNIT = "slice-iter/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=2048)
+    ap.add_argument("--angles", type=int, default=128)
+    ap.add_argument("--det", type=int, default=2896)
+    ap.add_argument("--slices", type=int, default=1024)
+    ap.add_argument("--chunk", type=int, default=64, help="slices per launch (plan max_batch)")
+    ap.add_argument("--plain-slices", type=int, default=32)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-angles", type=int, default=16,
+                    help="angles of one slice timed by the oracle for the CPU baseline")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ------------------------------------------------------------- clocks ------
+class ClockSampler:
+    """nvidia-smi SM clock / throttle-reason samples during the timed region."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.samples = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                      "--format=csv,noheader,nounits"], capture_output=True,
+                                     text=True, timeout=5).stdout.strip()
+                if out:
+                    self.samples.append([v.strip() for v in out.split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        if self._t:
+            self._t.join(timeout=10)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4)
+                          if len(s) > 3 + i and s[3 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.samples)}
+
+
+# ------------------------------------------------------ roofline bytes -----
+def algorithmic_bytes(name, N, A, D, w, B):
+    """Compulsory HBM bytes of one launch over B slices: each kernel's inputs
+    read once and outputs written once (tables and L2-resident vectors not
+    counted)."""
+    R = N + w  # grid rows touched by the half-plane polar points (jmin..jmax)
+    Mh = D // 2 + 1
+    AM = A * Mh
+    img, sino = 4 * N * N, 4 * A * D
+    grid_rows = 8 * R * N
+    part = 8 * w * AM
+    per = {
+        "k_fwd_col": img + grid_rows,
+        "k_fwd_row": grid_rows + part,
+        "k_fwd_det": part + 3 * sino,
+        "k_adj_det": sino + 8 * AM,
+        "k_adj_row": 8 * AM + grid_rows,
+        "k_adj_col": grid_rows + img,
+        "k_prior": 3 * img,
+        "k_dots_gzx_gg": 3 * img,
+        "k_update": 5 * img,
+    }
+    return per.get(name, 0) * B
+
+
+def launch_units(name, B_total, chunk):
+    """Slices processed by one launch of each kernel."""
+    if name in ("k_prior", "k_dots_gzx_gg", "k_update"):
+        return B_total
+    return chunk
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            pk = json.load(fh)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def traffic_for(name):
+    """Per-launch DRAM bytes of `name` from the committed ncu summary, or None
+    when the kernel source changed since those counters were taken."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    try:
+        with open(path) as fh:
+            tab = json.load(fh)
+    except Exception:
+        return None
+    src = os.path.join(ROOT, "paper_2304_12934_gb300", "csrc", tab.get("source_file", ""))
+    try:
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    except Exception:
+        return None
+    if h != tab.get("source_sha256"):
+        return None
+    ent = tab.get("kernels", {}).get(name)
+    return None if ent is None else ent.get("bytes_per_launch_scaled")
+
+
+# ------------------------------------------------------------ CPU oracle ---
+def oracle_slice_iter_seconds(N, A, D, n_ang_sample):
+    """Time the FP64 oracle (as it stands) on a bounded sample: A and A^T of one
+    N x N slice restricted to n_ang_sample angles, plus the 26-neighbour prior
+    on a 3-slice stack; scaled to one slice-iteration over all A angles."""
+    import numpy as np
+    import oracle
+    from paper_2304_12934_gb300 import synth
+    oracle.build()
+    th = oracle.default_angles(A)[:: max(1, A // n_ang_sample)][:n_ang_sample]
+    f = synth.rasterize(N, synth.random_ellipses(N, synth.BASE_SEED, scale=1.0 / N))
+    t0 = time.perf_counter()
+    y = oracle.radon_fwd(f, th.shape[0], D, th)
+    t1 = time.perf_counter()
+    oracle.radon_adj(y, N, th)
+    t2 = time.perf_counter()
+    vol = np.stack([f, f, f])
+    oracle.prior_value_grad(vol, 3)
+    t3 = time.perf_counter()
+    scale = A / th.shape[0]
+    per_slice = (t1 - t0) * scale + (t2 - t1) * scale + (t3 - t2) / 3.0
+    return per_slice, dict(fwd_s=t1 - t0, adj_s=t2 - t1, prior_s=t3 - t2, angles=int(th.shape[0]))
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    N, A, D = args.n, args.angles, args.det
+    nang = max(1, min(args.cpu_angles // 4, A))
+    cores = os.cpu_count()
+    times = []
+    for i in range(args.warmup + args.steps):
+        per_slice, info = oracle_slice_iter_seconds(N, A, D, nang)
+        if i >= args.warmup:
+            times.append(per_slice)
+    per_slice = statistics.mean(times)
+    value = 1.0 / per_slice
+    sample = (f"per step: oracle A and A^T of one {N}x{N} slice over {nang} of {A} angles "
+              f"(D={D}) plus the 26-neighbour prior on 3 slices, scaled to one slice-iteration")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": per_slice * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"volume {N}x{N}x{args.slices}, {A} angles, {D} bins (sampled)",
+                       "n": N, "angles": A, "det": D},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------- CUDA path ---
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from paper_2304_12934_gb300 import api, synth
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    N, A, D, B, MB = args.n, args.angles, args.det, args.slices, min(args.chunk, args.slices)
+    theta = np.arange(A) * (math.pi / A)
+
+    # ---- inputs (untimed): replica volume per rank, seeded by rank
+    seed = synth.BASE_SEED + 1000 * rank
+    p_true = synth.ellipsoid_sinogram_torch(N, B, theta, D, dev, scale=1.0 / N, seed=seed)
+    b, wgt = synth.poisson_measurement_torch(p_true, 1e4, seed + 1)
+    del p_true
+    torch.cuda.empty_cache()
+    prior = api.Prior(lam=1e-2, dims=3)
+    plan = api.Plan(N, A, D, max_batch=MB, device=dev)
+
+    # step size: power iteration on 4 slices (the normal operator is block
+    # diagonal over slices) plus the prior curvature bound
+    v = torch.tensor(synth.random_start((4, N, N), seed + 2), dtype=torch.float32, device=dev)
+    lam_max = api.mbir_power_norm(plan, v, wgt[:4].contiguous(), n_iter=15)
+    step = 1.0 / (1.05 * lam_max + api.prior_lipschitz(prior))
+    del v
+
+    x = torch.zeros((B, N, N), device=dev)
+    st = api.SolveState(x)
+
+    # ---- warm-up
+    api.mbir_solve(plan, b, wgt, x, args.warmup, step, prior, state=st)
+    torch.cuda.synchronize()
+
+    # ---- timed region: exactly K iterations, events on the launch stream
+    stream = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches0 = api.launch_count()
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    api.profile_enable(True)
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        api.mbir_solve(plan, b, wgt, x, args.steps, step, prior, state=st)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    prof = api.profile_collect()
+    api.profile_enable(False)
+    gpu_launches = api.launch_count() - launches0
+    if ws > 1:
+        dist.barrier()
+    ms = e0.elapsed_time(e1)
+    t = torch.tensor([ms], device=dev, dtype=torch.float64)
+    if ws > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms = float(t.item())
+    ms_per_step = ms / args.steps
+    value = ws * B * args.steps / (ms / 1e3)
+
+    # ---- roofline of the dominant kernel
+    peak, peak_kind = measured_peaks()
+    dom = max(prof.items(), key=lambda kv: kv[1][1])
+    dname, (dcnt, dms) = dom
+    units = launch_units(dname, B, MB)
+    alg = algorithmic_bytes(dname, N, A, D, plan.kernel_width, units)
+    avg_s = dms / dcnt / 1e3
+    achieved = alg / avg_s / 1e9
+    kernels = {k: {"launches": c, "ms_total": round(m, 3), "share": round(m / sum(v[1] for v in prof.values()), 4),
+                   "gbs_alg": round(algorithmic_bytes(k, N, A, D, plan.kernel_width,
+                                                      launch_units(k, B, MB)) / (m / c / 1e3) / 1e9, 1)}
+               for k, (c, m) in sorted(prof.items(), key=lambda kv: -kv[1][1])}
+    roofline = {"bound": "hbm", "kernel": dname, "achieved": round(achieved, 1), "peak": peak,
+                "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic_for(dname),
+                "alg_bytes_per_launch": alg, "peak_kind": f"{peak_kind} hbm_gbs (burst copy)"}
+
+    # ---- batched vs plain on a subset (same inputs, same iteration)
+    plain = None
+    if rank == 0 and args.plain_slices > 0:
+        S = min(args.plain_slices, B)
+        with api.Plan(N, A, D, max_batch=1, device=dev) as p1:
+            xs = [torch.zeros((S, N, N), device=dev) for _ in range(2)]
+            bs, ws_ = b[:S].contiguous(), wgt[:S].contiguous()
+            res = []
+            for pl, xx in ((p1, xs[0]), (plan, xs[1])):
+                s2 = api.SolveState(xx)
+                api.mbir_solve(pl, bs, ws_, xx, 1, step, prior, state=s2)
+                torch.cuda.synchronize()
+                a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a0.record(stream)
+                api.mbir_solve(pl, bs, ws_, xx, 2, step, prior, state=s2)
+                a1.record(stream)
+                torch.cuda.synchronize()
+                res.append(S * 2 / (a0.elapsed_time(a1) / 1e3))
+            err = float((xs[0] - xs[1]).norm() / xs[1].norm().clamp(min=1e-30))
+            plain = {"plain_slice_iter_s": round(res[0], 2), "batched_slice_iter_s": round(res[1], 2),
+                     "slices": S, "rel_err_batched_vs_plain": err,
+                     "speedup": round(res[1] / res[0], 3)}
+            del xs
+
+    # ---- end to end through the host-buffer entry point (pinned memory)
+    e2e = None
+    if not args.no_e2e:
+        bh = b.cpu().pin_memory()
+        wh = wgt.cpu().pin_memory()
+        xh = x.cpu().pin_memory()
+        devbuf = {"b": b, "w": wgt, "x": x}
+        st_e = api.SolveState(x)
+        api.mbir_solve_host(plan, bh, wh, xh, 1, step, prior, state=st_e, dev=devbuf)
+        torch.cuda.synchronize()
+        if ws > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            api.mbir_solve_host(plan, bh, wh, xh, 1, step, prior, state=st_e, dev=devbuf)
+        t_e2e = time.perf_counter() - t0
+        tt = torch.tensor([t_e2e], device=dev, dtype=torch.float64)
+        if ws > 1:
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_e2e = float(tt.item())
+        e2e = {"value": ws * B * args.steps / t_e2e, "unit": UNIT,
+               "h2d_bytes_per_step": int(bh.numel() * 4 + wh.numel() * 4 + xh.numel() * 4),
+               "d2h_bytes_per_step": int(xh.numel() * 4),
+               "call": "mbir_solve_host(n_iter=1) per step: H2D b, w, x; one iteration; D2H x"}
+
+    # ---- CPU oracle baseline (rank 0, N = 1)
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        per_slice, info = oracle_slice_iter_seconds(N, A, D, args.cpu_angles)
+        cpu = {"value": 1.0 / per_slice, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+               "sample": (f"oracle A and A^T of one {N}x{N} slice over {info['angles']} of {A} "
+                          f"angles (D={D}; {info['fwd_s']:.1f}+{info['adj_s']:.1f} s) plus the "
+                          f"26-neighbour prior on 3 slices ({info['prior_s']:.1f} s), scaled to "
+                          f"one slice-iteration over all {A} angles")}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": ws,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32 (FP64 reductions)", "data": "synthetic",
+                "config": {"workload": f"volume {N}x{N}x{B}, {A} angles, {D} bins, Poisson I0=1e4, "
+                                       f"26-nbr qGGMRF, 1 MBIR iteration per step",
+                           "n": N, "angles": A, "det": D, "slices_per_gpu": B,
+                           "slices_per_launch": MB, "kernel_width": plan.kernel_width,
+                           "oversample": 2, "l2": "inputs 17 GB per volume array >> L2; no flush",
+                           "parallelism": f"replicas x{ws}"},
+                "roofline": roofline, "kernels": kernels, "batched_vs_plain": plain,
+                "e2e": e2e, "cpu_baseline": cpu, "gpu_launches": int(gpu_launches),
+                "clocks": clk.summary(), "solver": {"step": step, "restarts": st.n_restarts,
+                                                    "obj": list(st.obj)}}
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

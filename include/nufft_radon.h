@@ -1,0 +1,204 @@
+/*
+ * nufft_radon.h -- C ABI of the GB300 NUFFT parallel-beam Radon library.
+ *
+ * The operators follow arXiv 2304.12934 (tomoCAM):
+ *   A   = discrete Radon transform R (Sec. 2.1 Eq. radon_transform, Eq. line_eqn),
+ *         evaluated through the Fourier-slice theorem (Eq. fourier_radon) with a
+ *         NUFFT: row DFT, gridding on a 2x oversampled Cartesian grid, 2D FFT and
+ *         deapodisation (Sec. 2.2 Eqs. nufft, nufft2, nufft3, "in reverse order").
+ *   A^T = its exact adjoint R* (Sec. 3 Eq. transpose).
+ *   MBIR objective  Phi(f) = 1/2 ||A f - b||_W^2 + lambda H(f)  (Sec. 3 Eq. objfn,
+ *         gradient Eq. gradient), H the qGGMRF prior (Sec. 3 Eqs. reg2, reg3).
+ *   Solver: accelerated gradient with restart (Sec. 3, last paragraph).
+ *
+ * Discrete conventions (shared by every entry point):
+ *   image   x[b][iy][ix], float32, row-major, pixel centre (ix - N/2, iy - N/2)
+ *   sinogram y[b][a][i], float32, detector coordinate t_i = i - D/2
+ *   angle   theta_a (default a*pi/A); projection coordinate x cos(theta) + y sin(theta)
+ *   A is the band-limited operator y(a,i) = sum_n f_n K_D(t_i - s_n(a)) with the
+ *   Dirichlet kernel K_D of the length-D detector DFT (Nyquist bin weighted 1/2).
+ *
+ * Memory: every array argument is a DEVICE pointer unless stated otherwise; the
+ * caller owns it.  The plan owns its own scratch (allocated in tc_plan_create).
+ * Calls are asynchronous on the given stream (a cudaStream_t passed as void*,
+ * NULL = legacy default stream) unless stated otherwise; an error detected on
+ * the host is returned immediately, an asynchronous device error surfaces at a
+ * later call or synchronisation.  No C++ exception crosses this interface.
+ * A plan is not thread safe: calls on one plan must be serialised by the caller
+ * (one stream at a time).
+ */
+#ifndef NUFFT_RADON_H
+#define NUFFT_RADON_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status -- */
+#define TC_OK                0
+#define TC_ERR_INVALID_ARG  -1   /* bad size, NULL pointer, unsupported parameter */
+#define TC_ERR_OOM          -2   /* device or host allocation failed */
+#define TC_ERR_CUDA         -3   /* a CUDA runtime call failed */
+#define TC_ERR_TIMEOUT      -4   /* a bounded device wait expired */
+#define TC_ERR_UNSUPPORTED  -5   /* valid request this build does not implement */
+
+/* Human-readable text for a status code (static storage, never NULL). */
+const char *tc_status_string(int status);
+
+/* Text of the last CUDA error seen by this library on this thread (or ""). */
+const char *tc_last_error_detail(void);
+
+/* ------------------------------------------------------------ geometry ---- */
+/* Scan geometry of one family of slices (Sec. 2.1; Sec. 2.2 for sigma and w).
+ *   n             image side N; power of two, 16 <= N <= 4096
+ *   n_angles      A >= 1
+ *   n_det         D; even, 4 <= D <= 16384
+ *   angles        HOST pointer to A angles in radians, or NULL for a*pi/A;
+ *                 copied during tc_plan_create
+ *   oversample    sigma, the grid oversampling factor; must be 2
+ *   kernel_width  w, spreading-kernel width in grid points (Sec. 2.2: w about
+ *                 log10(1/eps)); 2 <= w <= 8; 7 gives ~1e-6 relative error
+ */
+typedef struct {
+    int n;
+    int n_angles;
+    int n_det;
+    const double *angles;
+    int oversample;
+    int kernel_width;
+} tc_geom;
+
+typedef struct tc_plan tc_plan;
+
+/* Build a plan: FP64 deapodisation factors, polar-point gridding tables sorted
+ * into per-row bins, twiddle tables, and scratch for max_batch slices per
+ * launch (larger batches are processed in chunks of max_batch).  Synchronous.
+ * Allocates device memory with cudaMalloc on the current device.
+ * Returns TC_OK and *out, or an error (and *out = NULL). */
+int tc_plan_create(const tc_geom *geom, int max_batch, tc_plan **out);
+
+/* Release a plan and its device memory (synchronises the device first).
+ * NULL is accepted. */
+int tc_plan_destroy(tc_plan *plan);
+
+/* Device bytes held by the plan (tables + scratch). */
+long long tc_plan_device_bytes(const tc_plan *plan);
+
+/* --------------------------------------------------------------- operators */
+/* y = A x  (Sec. 2.2 NUFFT steps in reverse order).
+ *   x  [batch][N][N] float32 in;  y [batch][A][D] float32 out (overwritten).
+ *   batch >= 0 (0 is a no-op).  x and y must not overlap. */
+int radon_fwd(tc_plan *plan, const float *x, float *y, int batch, void *stream);
+
+/* x = A^T y  (Sec. 3 Eq. transpose; exact adjoint of radon_fwd's operator).
+ *   y  [batch][A][D] float32 in;  x [batch][N][N] float32 out (overwritten). */
+int radon_adj(tc_plan *plan, const float *y, float *x, int batch, void *stream);
+
+/* ---------------------------------------------------------------- prior --- */
+/* qGGMRF prior (Sec. 3 Eqs. reg2, reg3; defaults of Sec. 5):
+ *   H(f) = sum_m sum_{n in N(m)} w_mn rho(f_m - f_n),
+ *   rho(d) = (|d|/sigma)^2 / (c + (|d|/sigma)^(2-p)),
+ *   w_mn proportional to 1/||m-n|| and summing to one over the neighbourhood.
+ *   dims = 2: 8 in-plane neighbours; dims = 3: 26 neighbours across slices
+ *   (slices of one call are consecutive along z).  Neighbours outside the
+ *   volume are left out without renormalising the weights.
+ *   lambda >= 0 scales H in the objective (0 disables the prior). */
+typedef struct {
+    double p;       /* 1.2 */
+    double sigma;   /* 1/0.7 */
+    double c;       /* 1e-4 */
+    double lambda;  /* 1.0 */
+    int dims;       /* 2 or 3 */
+} tc_prior;
+
+/* ----------------------------------------------------------------- MBIR --- */
+/* Gradient of Phi at x (Sec. 3 Eq. gradient plus the prior gradient):
+ *   grad = A^T W (A x - b) + lambda grad H(x)
+ *   b      [batch][A][D] measured sinogram (Beer-Lambert, Sec. 5)
+ *   w      [batch][A][D] statistical weights, or NULL for W = I
+ *   prior  HOST pointer, or NULL for no prior
+ *   grad   [batch][N][N] out
+ *   obj    DEVICE pointer to 2 doubles or NULL: obj[0] = 1/2 sum W (Ax-b)^2,
+ *          obj[1] = lambda H(x); FP64 reductions in a fixed order. */
+int mbir_grad(tc_plan *plan, const float *x, const float *b, const float *w,
+              const tc_prior *prior, float *grad, double *obj, int batch,
+              void *stream);
+
+/* Largest eigenvalue of A^T W A by power iteration (step-size estimate).
+ *   v      [batch][N][N] start vector in (must be nonzero), last iterate out
+ *   work   [batch][N][N] scratch
+ *   w      weights or NULL
+ *   lam_out HOST pointer: last Rayleigh quotient <v, A^T W A v>, ||v|| = 1.
+ * Synchronises the stream before returning. */
+int mbir_power_norm(tc_plan *plan, const float *w, float *v, float *work,
+                    int batch, int n_iter, double *lam_out, void *stream);
+
+/* Accelerated gradient with gradient restart (reading of Sec. 3's "monotonic
+ * accelerated gradient method with restart"):
+ *   x_{k+1} = z_k - step * grad Phi(z_k)
+ *   if restart and <grad Phi(z_k), x_{k+1} - x_k> > 0 then t_k := 1
+ *   t_{k+1} = (1 + sqrt(1 + 4 t_k^2)) / 2
+ *   z_{k+1} = x_{k+1} + ((t_k - 1) / t_{k+1}) (x_{k+1} - x_k)
+ * All scalars (objective, inner products, t, momentum) are FP64 on the device;
+ * no host round trip inside the loop. */
+typedef struct {
+    int n_iter;      /* iterations to run in this call (>= 0) */
+    double step;     /* constant step, 1/L with L >= ||A^T W A|| + lambda * 8/(sigma^2 c) */
+    int restart;     /* 1 = gradient restart, 0 = plain FISTA momentum */
+} tc_solve_opts;
+
+/* Solver state; resuming with the same state continues the iteration exactly.
+ *   z, g   caller-owned DEVICE buffers [batch][N][N] (momentum point, gradient)
+ *   t      momentum scalar t_k (host copy, updated on return)
+ *   k      iterations completed; k == 0 starts fresh (z := x, t := 1)
+ *   n_restarts  restarts taken so far
+ *   obj    objective terms (data, prior) at the last gradient point */
+typedef struct {
+    float *z;
+    float *g;
+    double t;
+    int k;
+    int n_restarts;
+    double obj[2];
+} tc_solve_state;
+
+/* Run opts->n_iter iterations on device buffers.
+ *   b, w   [batch][A][D] (w may be NULL);  x [batch][N][N] in/out.
+ * Synchronises the stream before returning (to fill the host fields of state). */
+int mbir_solve(tc_plan *plan, const float *b, const float *w, float *x, int batch,
+               const tc_prior *prior, const tc_solve_opts *opts,
+               tc_solve_state *state, void *stream);
+
+/* Same solve, end to end from HOST memory: b_host, w_host (or NULL) and
+ * x_host are HOST pointers (page-locked memory gives asynchronous copies);
+ * dev_b, dev_w, dev_x are caller-owned DEVICE buffers of the same sizes that
+ * receive the copies.  Inputs are copied host-to-device in slabs of max_batch
+ * slices on a second stream, overlapped with the first iterations' work; the
+ * result x is copied back to x_host.  Synchronises before returning. */
+int mbir_solve_host(tc_plan *plan, const float *b_host, const float *w_host,
+                    float *x_host, float *dev_b, float *dev_w, float *dev_x,
+                    int batch, const tc_prior *prior, const tc_solve_opts *opts,
+                    tc_solve_state *state, void *stream);
+
+/* ------------------------------------------------------------ profiling --- */
+/* Per-kernel device timing with CUDA events (no counterpart in the paper; it
+ * supports the roofline measurements).  While enabled, every kernel launch of
+ * this library is bracketed by two events on its stream.  Enabling (or
+ * re-enabling) discards earlier records. */
+int tc_profile_enable(int on);
+
+/* Synchronises the recorded events and fills counts[i] (launches) and ms[i]
+ * (summed device milliseconds) for kernel ids i < max_kernels (HOST arrays).
+ * Returns the number of kernel ids the library defines, or an error. */
+int tc_profile_collect(int max_kernels, long long *counts, double *ms);
+
+/* Name of kernel id (static storage; "" for an unknown id). */
+const char *tc_profile_kernel_name(int id);
+
+/* Kernel launches issued by this library since it was loaded (host counter). */
+long long tc_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NUFFT_RADON_H */

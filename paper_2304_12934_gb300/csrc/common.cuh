@@ -1,0 +1,163 @@
+// Internal definitions shared by the CUDA translation units of the NUFFT Radon
+// library: the plan layout, the by-value kernel argument block and complex
+// helpers.  Nothing here is part of the C ABI (include/nufft_radon.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/nufft_radon.h"
+
+#define TC_MAX_RADICES 24
+
+// Mixed-radix factorisation of the detector length D (odd primes first).
+struct RadixPlan {
+    int n;
+    int nrad;
+    int rad[TC_MAX_RADICES];
+};
+
+// Geometry and table pointers passed by value to every Radon kernel.
+struct KArgs {
+    int N, log2N;      // image side (power of two)
+    int G;             // oversampled grid side, 2N
+    int A, D, Mh;      // angles, detector bins, radial samples m = 0..D/2
+    int AM;            // A * Mh polar points per slice
+    int w;             // kernel width
+    int R;             // grid rows jy = jmin .. jmin + R - 1 touched by any point
+    int jmin, jmax;
+    int kmin, kmax;    // range of the row-entry sort key jx0
+    float beta, inv_h; // ES kernel: phi(z) = exp(beta (sqrt(1 - z^2) - 1)), z = offset / (w/2)
+    float invD;
+    const float *dea;          // [N] 1 / psi(i - N/2)  (from FP64)
+    const float2 *twN;         // [N] exp(-2 pi i k / N)
+    const float2 *twG;         // [N] exp(-2 pi i (k - N/2) / G)
+    const float2 *twD;         // [D] exp(-2 pi i k / D)
+    const int *row_off;        // [R + 1] first entry of each grid row
+    const int *ent_p;          // [E] polar point index a * Mh + m
+    const short *ent_key;      // [E] jx0 of the point (sort key within the row)
+    const unsigned char *ent_s;// [E] tap index of this row in the point's y footprint
+    const float *ent_ex;       // [E] gx - jx0
+    const float *ent_wy;       // [E] phi((s - (gy - jy0)) / (w/2))
+    const unsigned char *angle_flip; // [A] 1: theta was in [pi, 2 pi), data conjugated
+    RadixPlan rp;              // factorisation of D
+};
+
+struct tc_plan {
+    int device;
+    int max_batch;
+    KArgs k;
+    double *dea64;        // FP64 deapodisation factors (device)
+    float *dea;
+    float2 *twN, *twG, *twD;
+    int *row_off;
+    int *ent_p;
+    short *ent_key;
+    unsigned char *ent_s;
+    float *ent_ex, *ent_wy;
+    unsigned char *angle_flip;
+    long long n_entries;
+    // scratch for max_batch slices
+    float2 *tu;           // [MB][R][N]   column-pass output (fwd) / row-pass output (adj)
+    float2 *pv;           // [MB][w][AM]  interpolation partials (fwd) / spread weights (adj, plane 0)
+    float *sr;            // [MB][A][D]   weighted residual sinogram (MBIR)
+    double *partials;     // TC_N_SLOTS slots of `slot` per-block FP64 partial sums
+    int slot;
+    double *scal;         // device scalars of the solver
+    long long bytes;
+    // launch configuration
+    int cp_col;           // column pairs per CTA in the column passes
+    int threads_col, threads_row, threads_det;
+    size_t smem_col, smem_row_fwd, smem_row_adj, smem_det;
+};
+
+// ------------------------------------------------------------- complex ops --
+__host__ __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+__host__ __device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+// a += w * v for real weight w
+__device__ __forceinline__ void cfma(float2 &a, float wgt, float2 v) {
+    a.x = fmaf(wgt, v.x, a.x);
+    a.y = fmaf(wgt, v.y, a.y);
+}
+
+// Exponential-of-semicircle spreading kernel (Barnett, Magland, af Klinteberg
+// 2019), evaluated at z = offset / (w/2); zero for |z| >= 1.
+__device__ __forceinline__ float es_kernel(float z, float beta) {
+    const float q = 1.0f - z * z;
+    return q > 0.0f ? expf(beta * (sqrtf(q) - 1.0f)) : 0.0f;
+}
+
+// Block-wide FP64 sum of one float per thread; thread 0 gets the total.
+__device__ __forceinline__ double block_sum_f64(double d, double *red) {
+    for (int o = 16; o > 0; o >>= 1) d += __shfl_down_sync(0xffffffffu, d, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) red[wid] = d;
+    __syncthreads();
+    double tot = 0.0;
+    if (threadIdx.x == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+        for (int i = 0; i < nw; ++i) tot += red[i];
+    }
+    __syncthreads();
+    return tot;
+}
+
+// Reductions write one FP64 partial per block into a slot of plan->partials and
+// a single-block kernel sums the slot in a fixed order (deterministic).
+#define TC_RED_BLOCKS 1216   // fixed grid of the grid-stride reductions (152 SMs x 8)
+#define TC_RED_THREADS 256
+#define TC_N_SLOTS 4
+// Device scalar block of the solver (plan->scal).
+enum {
+    SC_DATA = 0,     // data term 1/2 sum W r^2 (accumulated over chunks)
+    SC_PRIOR,        // lambda H
+    SC_DOT_GZX,      // <g, z - x>
+    SC_DOT_GG,       // <g, g>
+    SC_T,            // momentum t_k
+    SC_BETA,         // momentum coefficient of this iteration
+    SC_RESTARTS,     // restart count (as double)
+    SC_K,            // iteration count (as double)
+    SC_STEP,         // step
+    SC_NORM,         // scratch norm / Rayleigh quotient
+    SC_COUNT = 16
+};
+
+// Launchers (defined in radon_kernels.cu / mbir_kernels.cu).
+int launch_radon_fwd_chunk(tc_plan *p, const float *x, float *y, int nb,
+                           const float *b, const float *w, float *resid,
+                           double *obj_acc, cudaStream_t s);
+int launch_radon_adj_chunk(tc_plan *p, const float *y, float *x, int nb,
+                           cudaStream_t s);
+int launch_prior_grad(tc_plan *p, const float *x, float *g, int nb,
+                      const tc_prior *pr, double *h_acc, cudaStream_t s);
+int launch_reduce_finalize(const double *partials, int n, double *acc,
+                           int accumulate, double scale, cudaStream_t s);
+int launch_dots_gzx_gg(tc_plan *p, const float *g, const float *z, const float *x,
+                       size_t n, cudaStream_t s);
+int launch_solver_scalar(tc_plan *p, int restart, cudaStream_t s);
+int launch_update(tc_plan *p, float *x, float *z, const float *g, size_t n,
+                  cudaStream_t s);
+int launch_dot(tc_plan *p, const float *a, const float *b, size_t n,
+               double *out_acc, cudaStream_t s);
+int launch_scale_by_inv_sqrt(float *v, size_t n, const double *sq, cudaStream_t s);
+int launch_copy(float *dst, const float *src, size_t n, cudaStream_t s);
+int launch_fill_scalars_fresh(tc_plan *p, double t, double k, double restarts,
+                              double step, cudaStream_t s);
+
+// Error plumbing (api.cu).
+int tc_cuda_fail(cudaError_t e, const char *where);
+#define TC_CUDA(call)                                              \
+    do {                                                           \
+        cudaError_t _e = (call);                                   \
+        if (_e != cudaSuccess) return tc_cuda_fail(_e, #call);     \
+    } while (0)
+#define TC_LAUNCHED(name)                                          \
+    do {                                                           \
+        cudaError_t _e = cudaGetLastError();                       \
+        if (_e != cudaSuccess) return tc_cuda_fail(_e, name);      \
+    } while (0)

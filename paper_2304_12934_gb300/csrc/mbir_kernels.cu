@@ -1,0 +1,297 @@
+// MBIR kernels (arXiv 2304.12934, Sec. 3): the qGGMRF prior value and
+// gradient (Eqs. reg2, reg3), FP64 reductions for the objective and the
+// restart test, and the accelerated-gradient update with restart.
+//
+// Vectors are FP32; every reduction accumulates at most a few FP32 products
+// per thread before promoting to FP64, then sums per-block FP64 partials in a
+// fixed order, so results are bit-reproducible run to run.
+#include "common.cuh"
+#include "profile.cuh"
+
+namespace {
+
+struct PriorArgs {
+    int N, B, dims;
+    float p, inv_sigma, c, qexp;  // qexp = 2 - p
+    float two_lambda;
+    float w1, w2, w3;             // weights at distance 1, sqrt 2, sqrt 3
+};
+
+// rho(d) = u^2 / (c + |u|^(2-p)), u = d / sigma, and its derivative in d.
+__device__ __forceinline__ void qggmrf(float d, const PriorArgs &a, float &rho, float &rhop) {
+    const float u = d * a.inv_sigma;
+    const float au = fabsf(u);
+    const float q = au > 0.f ? exp2f(a.qexp * log2f(au)) : 0.f;
+    const float inv = 1.0f / (a.c + q);
+    rho = u * u * inv;
+    rhop = u * a.inv_sigma * fmaf(a.p, q, 2.0f * a.c) * inv * inv;
+}
+
+__global__ void k_prior(const float *__restrict__ f, float *__restrict__ g,
+                        double *__restrict__ partials, const PriorArgs a) {
+    __shared__ double red[32];
+    const int N = a.N;
+    const size_t NN = (size_t)N * N;
+    const size_t total = NN * a.B;
+    double hacc = 0.0;
+    float hblk = 0.f;
+    int cnt = 0;
+    const int zlo = a.dims == 3 ? -1 : 0, zhi = a.dims == 3 ? 1 : 0;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const int ix = (int)(i % N);
+        const int iy = (int)((i / N) % N);
+        const int iz = (int)(i / NN);
+        const float fm = f[i];
+        float gs = 0.f, hs = 0.f;
+        for (int dz = zlo; dz <= zhi; ++dz) {
+            const int zz = iz + dz;
+            if (zz < 0 || zz >= a.B) continue;
+            for (int dy = -1; dy <= 1; ++dy) {
+                const int yy = iy + dy;
+                if (yy < 0 || yy >= N) continue;
+                for (int dx = -1; dx <= 1; ++dx) {
+                    const int xx = ix + dx;
+                    if (xx < 0 || xx >= N || (dz == 0 && dy == 0 && dx == 0)) continue;
+                    const int l1 = abs(dz) + abs(dy) + abs(dx);
+                    const float wgt = l1 == 1 ? a.w1 : (l1 == 2 ? a.w2 : a.w3);
+                    const float fn = f[(size_t)zz * NN + (size_t)yy * N + xx];
+                    float rho, rhop;
+                    qggmrf(fm - fn, a, rho, rhop);
+                    hs = fmaf(wgt, rho, hs);
+                    gs = fmaf(wgt, rhop, gs);
+                }
+            }
+        }
+        g[i] = fmaf(a.two_lambda, gs, g[i]);
+        hblk += hs;
+        if (++cnt == 8) {
+            hacc += (double)hblk;
+            hblk = 0.f;
+            cnt = 0;
+        }
+    }
+    hacc += (double)hblk;
+    const double tot = block_sum_f64(hacc, red);
+    if (threadIdx.x == 0) partials[blockIdx.x] = tot;
+}
+
+__global__ void k_reduce_finalize(const double *__restrict__ partials, int n,
+                                  double *acc, int accumulate, double scale) {
+    __shared__ double red[32];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s += partials[i];
+    const double tot = block_sum_f64(s, red);
+    if (threadIdx.x == 0) *acc = (accumulate ? *acc : 0.0) + scale * tot;
+}
+
+__global__ void k_dots_gzx_gg(const float4 *__restrict__ g, const float4 *__restrict__ z,
+                              const float4 *__restrict__ x, size_t n4,
+                              double *__restrict__ p_gzx, double *__restrict__ p_gg) {
+    __shared__ double red[32];
+    double a1 = 0.0, a2 = 0.0;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const float4 gv = g[i], zv = z[i], xv = x[i];
+        float d = gv.x * (zv.x - xv.x);
+        d = fmaf(gv.y, zv.y - xv.y, d);
+        d = fmaf(gv.z, zv.z - xv.z, d);
+        d = fmaf(gv.w, zv.w - xv.w, d);
+        float q = gv.x * gv.x;
+        q = fmaf(gv.y, gv.y, q);
+        q = fmaf(gv.z, gv.z, q);
+        q = fmaf(gv.w, gv.w, q);
+        a1 += (double)d;
+        a2 += (double)q;
+    }
+    const double t1 = block_sum_f64(a1, red);
+    const double t2 = block_sum_f64(a2, red);
+    if (threadIdx.x == 0) {
+        p_gzx[blockIdx.x] = t1;
+        p_gg[blockIdx.x] = t2;
+    }
+}
+
+__global__ void k_dot(const float4 *__restrict__ a, const float4 *__restrict__ b, size_t n4,
+                      double *__restrict__ part) {
+    __shared__ double red[32];
+    double acc = 0.0;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const float4 u = a[i], v = b[i];
+        float d = u.x * v.x;
+        d = fmaf(u.y, v.y, d);
+        d = fmaf(u.z, v.z, d);
+        d = fmaf(u.w, v.w, d);
+        acc += (double)d;
+    }
+    const double t = block_sum_f64(acc, red);
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
+// One thread: restart test and momentum coefficient, all in FP64.
+__global__ void k_solver_scalar(double *sc, int restart) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const double step = sc[SC_STEP];
+    // <g, x_{k+1} - x_k> with x_{k+1} = z_k - step g
+    const double dot = sc[SC_DOT_GZX] - step * sc[SC_DOT_GG];
+    double t = sc[SC_T];
+    if (restart && dot > 0.0) {
+        t = 1.0;
+        sc[SC_RESTARTS] += 1.0;
+    }
+    const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
+    sc[SC_BETA] = (t - 1.0) / tn;
+    sc[SC_T] = tn;
+    sc[SC_K] += 1.0;
+    sc[SC_NORM] = dot;
+}
+
+__global__ void k_update(float4 *__restrict__ x, float4 *__restrict__ z,
+                         const float4 *__restrict__ g, size_t n4, const double *__restrict__ sc) {
+    const float step = (float)sc[SC_STEP];
+    const float beta = (float)sc[SC_BETA];
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const float4 xv = x[i], zv = z[i], gv = g[i];
+        float4 xn, zn;
+        xn.x = fmaf(-step, gv.x, zv.x);
+        xn.y = fmaf(-step, gv.y, zv.y);
+        xn.z = fmaf(-step, gv.z, zv.z);
+        xn.w = fmaf(-step, gv.w, zv.w);
+        zn.x = fmaf(beta, xn.x - xv.x, xn.x);
+        zn.y = fmaf(beta, xn.y - xv.y, xn.y);
+        zn.z = fmaf(beta, xn.z - xv.z, xn.z);
+        zn.w = fmaf(beta, xn.w - xv.w, xn.w);
+        x[i] = xn;
+        z[i] = zn;
+    }
+}
+
+__global__ void k_scale_inv_sqrt(float4 *__restrict__ v, size_t n4, const double *__restrict__ sq) {
+    const float s = (float)(1.0 / sqrt(*sq));
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4;
+         i += (size_t)gridDim.x * blockDim.x) {
+        float4 a = v[i];
+        a.x *= s; a.y *= s; a.z *= s; a.w *= s;
+        v[i] = a;
+    }
+}
+
+__global__ void k_fill_scalars(double *sc, double t, double k, double restarts, double step) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        sc[SC_T] = t;
+        sc[SC_K] = k;
+        sc[SC_RESTARTS] = restarts;
+        sc[SC_STEP] = step;
+        sc[SC_BETA] = 0.0;
+    }
+}
+
+int grid_for(size_t n4) {
+    size_t b = (n4 + TC_RED_THREADS - 1) / TC_RED_THREADS;
+    return (int)(b < TC_RED_BLOCKS ? (b ? b : 1) : TC_RED_BLOCKS);
+}
+
+}  // namespace
+
+int launch_prior_grad(tc_plan *p, const float *x, float *g, int nb,
+                      const tc_prior *pr, double *h_acc, cudaStream_t s) {
+    PriorArgs a;
+    a.N = p->k.N;
+    a.B = nb;
+    a.dims = pr->dims;
+    a.p = (float)pr->p;
+    a.inv_sigma = (float)(1.0 / pr->sigma);
+    a.c = (float)pr->c;
+    a.qexp = (float)(2.0 - pr->p);
+    a.two_lambda = (float)(2.0 * pr->lambda);
+    // w_mn proportional to 1/distance, normalised over the full neighbourhood
+    double z;
+    if (pr->dims == 3) z = 6.0 + 12.0 / sqrt(2.0) + 8.0 / sqrt(3.0);
+    else z = 4.0 + 4.0 / sqrt(2.0);
+    a.w1 = (float)(1.0 / z);
+    a.w2 = (float)(1.0 / (sqrt(2.0) * z));
+    a.w3 = (float)(1.0 / (sqrt(3.0) * z));
+    const int blocks = TC_RED_BLOCKS;
+    double *part = p->partials + (size_t)1 * p->slot;
+    TC_PROFILED(TCK_PRIOR, s,
+                k_prior<<<blocks, TC_RED_THREADS, 0, s>>>(x, g, part, a));
+    TC_LAUNCHED("k_prior");
+    if (h_acc) return launch_reduce_finalize(part, blocks, h_acc, 0, pr->lambda, s);
+    return TC_OK;
+}
+
+int launch_reduce_finalize(const double *partials, int n, double *acc,
+                           int accumulate, double scale, cudaStream_t s) {
+    TC_PROFILED(TCK_REDUCE, s,
+                k_reduce_finalize<<<1, 256, 0, s>>>(partials, n, acc, accumulate, scale));
+    TC_LAUNCHED("k_reduce_finalize");
+    return TC_OK;
+}
+
+int launch_dots_gzx_gg(tc_plan *p, const float *g, const float *z, const float *x,
+                       size_t n, cudaStream_t s) {
+    const size_t n4 = n / 4;
+    const int blocks = grid_for(n4);
+    double *p1 = p->partials + (size_t)2 * p->slot, *p2 = p->partials + (size_t)3 * p->slot;
+    TC_PROFILED(TCK_DOTS, s,
+                k_dots_gzx_gg<<<blocks, TC_RED_THREADS, 0, s>>>(
+        reinterpret_cast<const float4 *>(g), reinterpret_cast<const float4 *>(z),
+        reinterpret_cast<const float4 *>(x), n4, p1, p2));
+    TC_LAUNCHED("k_dots_gzx_gg");
+    int rc = launch_reduce_finalize(p1, blocks, p->scal + SC_DOT_GZX, 0, 1.0, s);
+    if (rc) return rc;
+    return launch_reduce_finalize(p2, blocks, p->scal + SC_DOT_GG, 0, 1.0, s);
+}
+
+int launch_dot(tc_plan *p, const float *a, const float *b, size_t n,
+               double *out_acc, cudaStream_t s) {
+    const size_t n4 = n / 4;
+    const int blocks = grid_for(n4);
+    double *part = p->partials + (size_t)2 * p->slot;
+    TC_PROFILED(TCK_DOT, s,
+                k_dot<<<blocks, TC_RED_THREADS, 0, s>>>(reinterpret_cast<const float4 *>(a),
+                                            reinterpret_cast<const float4 *>(b), n4, part));
+    TC_LAUNCHED("k_dot");
+    return launch_reduce_finalize(part, blocks, out_acc, 0, 1.0, s);
+}
+
+int launch_solver_scalar(tc_plan *p, int restart, cudaStream_t s) {
+    TC_PROFILED(TCK_SCALAR, s,
+                k_solver_scalar<<<1, 32, 0, s>>>(p->scal, restart));
+    TC_LAUNCHED("k_solver_scalar");
+    return TC_OK;
+}
+
+int launch_update(tc_plan *p, float *x, float *z, const float *g, size_t n,
+                  cudaStream_t s) {
+    const size_t n4 = n / 4;
+    TC_PROFILED(TCK_UPDATE, s,
+                k_update<<<grid_for(n4), TC_RED_THREADS, 0, s>>>(
+        reinterpret_cast<float4 *>(x), reinterpret_cast<float4 *>(z),
+        reinterpret_cast<const float4 *>(g), n4, p->scal));
+    TC_LAUNCHED("k_update");
+    return TC_OK;
+}
+
+int launch_scale_by_inv_sqrt(float *v, size_t n, const double *sq, cudaStream_t s) {
+    const size_t n4 = n / 4;
+    TC_PROFILED(TCK_SCALE, s,
+                k_scale_inv_sqrt<<<grid_for(n4), TC_RED_THREADS, 0, s>>>(reinterpret_cast<float4 *>(v), n4, sq));
+    TC_LAUNCHED("k_scale_inv_sqrt");
+    return TC_OK;
+}
+
+int launch_copy(float *dst, const float *src, size_t n, cudaStream_t s) {
+    TC_CUDA(cudaMemcpyAsync(dst, src, n * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    return TC_OK;
+}
+
+int launch_fill_scalars_fresh(tc_plan *p, double t, double k, double restarts,
+                              double step, cudaStream_t s) {
+    TC_PROFILED(TCK_FILL, s,
+                k_fill_scalars<<<1, 32, 0, s>>>(p->scal, t, k, restarts, step));
+    TC_LAUNCHED("k_fill_scalars");
+    return TC_OK;
+}

@@ -1,0 +1,348 @@
+// Plan construction for the NUFFT Radon operators (host side).
+//
+// Everything geometric is computed here once, in FP64, and uploaded:
+//   * deapodisation factors 1/psi(x), psi the Fourier transform of the
+//     spreading kernel (Sec. 2.2 Eq. nufft3's "division by the Fourier
+//     transform of the kernel"), by Gauss-Legendre quadrature;
+//   * the polar points k = (m/D)(cos theta, sin theta), m = 0..D/2, on the
+//     2x oversampled grid g = k G (Sec. 2.2, Fig. gridding), reduced to the
+//     upper half plane (theta in [0, pi)) using conj symmetry of real data;
+//   * per grid row, the list of (point, tap) pairs whose w x w footprint
+//     touches that row, sorted by the point's first column jx0 -- the sorted
+//     bins that make spreading a deterministic gather;
+//   * twiddle tables and the mixed-radix factorisation of D.
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+#include "common.cuh"
+
+int radon_configure_kernels(tc_plan *p);
+
+namespace {
+
+const double kPi = 3.14159265358979323846264338327950288;
+
+double es_phi(double z, double beta) {
+    const double q = 1.0 - z * z;
+    return q > 0.0 ? std::exp(beta * (std::sqrt(q) - 1.0)) : 0.0;
+}
+
+// Gauss-Legendre nodes/weights on [-1, 1] by Newton iteration on P_n.
+void gauss_legendre(int n, std::vector<double> &x, std::vector<double> &w) {
+    x.assign(n, 0.0);
+    w.assign(n, 0.0);
+    for (int i = 0; i < n; ++i) {
+        double z = std::cos(kPi * (i + 0.75) / (n + 0.5));
+        double dp = 0.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = z;
+            for (int k = 2; k <= n; ++k) {
+                const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            dp = n * (z * p1 - p0) / (z * z - 1.0);
+            const double dz = p1 / dp;
+            z -= dz;
+            if (std::fabs(dz) < 1e-16) break;
+        }
+        double p0 = 1.0, p1 = z;
+        for (int k = 2; k <= n; ++k) {
+            const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+            p0 = p1;
+            p1 = p2;
+        }
+        dp = n * (z * p1 - p0) / (z * z - 1.0);
+        x[i] = z;
+        w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+}
+
+int ilog2(int v) {
+    int r = 0;
+    while ((1 << r) < v) ++r;
+    return r;
+}
+
+// Odd primes (largest first), then radix 4, then one radix 2.
+bool factor_radices(int n, RadixPlan &rp) {
+    rp.n = n;
+    rp.nrad = 0;
+    std::vector<int> odd;
+    int m = n, twos = 0;
+    while (m % 2 == 0) {
+        m /= 2;
+        ++twos;
+    }
+    for (int p = 3; (long long)p * p <= m; p += 2)
+        while (m % p == 0) {
+            odd.push_back(p);
+            m /= p;
+        }
+    if (m > 1) odd.push_back(m);
+    std::sort(odd.rbegin(), odd.rend());
+    std::vector<int> r(odd.begin(), odd.end());
+    while (twos >= 2) {
+        r.push_back(4);
+        twos -= 2;
+    }
+    if (twos) r.push_back(2);
+    if ((int)r.size() > TC_MAX_RADICES) return false;
+    for (size_t i = 0; i < r.size(); ++i) rp.rad[i] = r[i];
+    rp.nrad = (int)r.size();
+    return true;
+}
+
+struct Entry {
+    int key, p, s;
+    float ex, wy;
+};
+
+template <class T>
+int upload(T **dst, const std::vector<T> &src, long long &bytes) {
+    const size_t nb = src.size() * sizeof(T);
+    *dst = nullptr;
+    if (nb == 0) return TC_OK;
+    cudaError_t e = cudaMalloc((void **)dst, nb);
+    if (e != cudaSuccess) return tc_cuda_fail(e, "cudaMalloc(plan table)");
+    bytes += (long long)nb;
+    TC_CUDA(cudaMemcpy(*dst, src.data(), nb, cudaMemcpyHostToDevice));
+    return TC_OK;
+}
+
+int alloc_dev(void **dst, size_t nb, long long &bytes) {
+    *dst = nullptr;
+    cudaError_t e = cudaMalloc(dst, nb ? nb : 16);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return e == cudaErrorMemoryAllocation ? TC_ERR_OOM : tc_cuda_fail(e, "cudaMalloc(scratch)");
+    }
+    bytes += (long long)nb;
+    return TC_OK;
+}
+
+}  // namespace
+
+void tc_plan_free(tc_plan *p) {
+    if (!p) return;
+    void *ptrs[] = {p->dea64, p->dea, p->twN, p->twG, p->twD, p->row_off, p->ent_p,
+                    p->ent_key, p->ent_s, p->ent_ex, p->ent_wy, p->tu, p->pv,
+                    p->sr, p->partials, p->scal, p->angle_flip};
+    for (void *q : ptrs)
+        if (q) cudaFree(q);
+    delete p;
+}
+
+int tc_plan_build(const tc_geom *geom, int max_batch, tc_plan **out) {
+    const int N = geom->n, A = geom->n_angles, D = geom->n_det, w = geom->kernel_width;
+    tc_plan *p = new tc_plan();
+    std::memset(p, 0, sizeof(*p));
+    *out = nullptr;
+    TC_CUDA(cudaGetDevice(&p->device));
+    p->max_batch = max_batch;
+    KArgs &k = p->k;
+    k.N = N;
+    k.log2N = ilog2(N);
+    k.G = 2 * N;
+    k.A = A;
+    k.D = D;
+    k.Mh = D / 2 + 1;
+    k.AM = A * k.Mh;
+    k.w = w;
+    const double h = 0.5 * w;
+    const double beta = 2.30 * w;  // ES shape parameter for sigma = 2 (Barnett et al. 2019)
+    k.beta = (float)beta;
+    k.inv_h = (float)(1.0 / h);
+    k.invD = (float)(1.0 / D);
+    if (!factor_radices(D, k.rp)) {
+        tc_plan_free(p);
+        return TC_ERR_UNSUPPORTED;
+    }
+    const int G = k.G;
+
+    // angles reduced to [0, pi); a flipped angle uses conj symmetry of real data
+    std::vector<double> th(A);
+    std::vector<unsigned char> flip(A, 0);
+    for (int a = 0; a < A; ++a) {
+        double t = geom->angles ? geom->angles[a] : a * kPi / A;
+        if (!std::isfinite(t)) {
+            tc_plan_free(p);
+            return TC_ERR_INVALID_ARG;
+        }
+        t = std::fmod(t, 2.0 * kPi);
+        if (t < 0.0) t += 2.0 * kPi;
+        if (t >= kPi) {
+            t -= kPi;
+            flip[a] = 1;
+        }
+        th[a] = t;
+    }
+
+    // deapodisation: psi(x) = int_{-h}^{h} phi(u/h) cos(2 pi u x / G) du
+    std::vector<double> gx, gw;
+    gauss_legendre(4 * w + 48, gx, gw);
+    std::vector<double> dea64(N);
+    std::vector<float> dea(N);
+    for (int i = 0; i < N; ++i) {
+        const double xv = i - N / 2;
+        double s = 0.0;
+        for (size_t q = 0; q < gx.size(); ++q) {
+            const double u = gx[q] * h;
+            s += gw[q] * h * es_phi(gx[q], beta) * std::cos(2.0 * kPi * u * xv / G);
+        }
+        dea64[i] = 1.0 / s;
+        dea[i] = (float)dea64[i];
+    }
+
+    // polar points and per-row entries
+    const int Mh = k.Mh;
+    const long long npts = (long long)A * Mh;
+    std::vector<int> jx0(npts), jy0(npts);
+    std::vector<double> exv(npts), eyv(npts);
+    int jymin = 1 << 30, jymax = -(1 << 30), kmin = 1 << 30, kmax = -(1 << 30);
+    for (int a = 0; a < A; ++a) {
+        const double c = std::cos(th[a]), s = std::sin(th[a]);
+        for (int m = 0; m < Mh; ++m) {
+            const long long pidx = (long long)a * Mh + m;
+            const double r = (double)m * G / D;
+            const double gxv = r * c, gyv = r * s;
+            const int x0 = (int)std::floor(gxv - h) + 1;
+            const int y0 = (int)std::floor(gyv - h) + 1;
+            jx0[pidx] = x0;
+            jy0[pidx] = y0;
+            exv[pidx] = gxv - x0;
+            eyv[pidx] = gyv - y0;
+            jymin = std::min(jymin, y0);
+            jymax = std::max(jymax, y0 + w - 1);
+            kmin = std::min(kmin, x0);
+            kmax = std::max(kmax, x0);
+        }
+    }
+    k.jmin = (int)std::floor(-h) + 1;
+    k.jmax = (int)std::floor(N - h) + w;
+    if (jymin < k.jmin || jymax > k.jmax || k.jmax - k.jmin + 1 > G) {
+        tc_plan_free(p);
+        return TC_ERR_INVALID_ARG;
+    }
+    k.R = k.jmax - k.jmin + 1;
+    k.kmin = kmin;
+    k.kmax = kmax;
+    const int R = k.R;
+    std::vector<int> cnt(R + 1, 0);
+    for (long long q = 0; q < npts; ++q)
+        for (int s = 0; s < w; ++s) cnt[jy0[q] + s - k.jmin + 1]++;
+    for (int r = 0; r < R; ++r) cnt[r + 1] += cnt[r];
+    std::vector<Entry> ents((size_t)cnt[R]);
+    std::vector<int> fillp(cnt.begin(), cnt.end() - 1);
+    for (long long q = 0; q < npts; ++q)
+        for (int s = 0; s < w; ++s) {
+            const int r = jy0[q] + s - k.jmin;
+            Entry &e = ents[fillp[r]++];
+            e.key = jx0[q];
+            e.p = (int)q;
+            e.s = s;
+            e.ex = (float)exv[q];
+            e.wy = (float)es_phi((s - eyv[q]) / h, beta);
+        }
+    for (int r = 0; r < R; ++r)
+        std::sort(ents.begin() + cnt[r], ents.begin() + cnt[r + 1],
+                  [](const Entry &u, const Entry &v) { return u.key != v.key ? u.key < v.key : u.p < v.p; });
+    const size_t E = ents.size();
+    std::vector<int> ep(E);
+    std::vector<short> ek(E);
+    std::vector<unsigned char> es(E);
+    std::vector<float> eex(E), ewy(E);
+    for (size_t i = 0; i < E; ++i) {
+        ep[i] = ents[i].p;
+        ek[i] = (short)ents[i].key;
+        es[i] = (unsigned char)ents[i].s;
+        eex[i] = ents[i].ex;
+        ewy[i] = ents[i].wy;
+    }
+    p->n_entries = (long long)E;
+
+    // twiddles
+    std::vector<float2> twN(N), twG(N), twD(D);
+    for (int i = 0; i < N; ++i) {
+        const double a1 = -2.0 * kPi * i / N;
+        twN[i] = make_float2((float)std::cos(a1), (float)std::sin(a1));
+        const double a2 = -2.0 * kPi * (i - N / 2) / G;
+        twG[i] = make_float2((float)std::cos(a2), (float)std::sin(a2));
+    }
+    for (int i = 0; i < D; ++i) {
+        const double a3 = -2.0 * kPi * i / D;
+        twD[i] = make_float2((float)std::cos(a3), (float)std::sin(a3));
+    }
+
+    long long bytes = 0;
+    int rc = TC_OK;
+#define UP(dst, src)                              \
+    if ((rc = upload(&(dst), (src), bytes))) {    \
+        tc_plan_free(p);                          \
+        return rc;                                \
+    }
+    UP(p->dea64, dea64);
+    UP(p->dea, dea);
+    UP(p->twN, twN);
+    UP(p->twG, twG);
+    UP(p->twD, twD);
+    UP(p->row_off, cnt);
+    UP(p->ent_p, ep);
+    UP(p->ent_key, ek);
+    UP(p->ent_s, es);
+    UP(p->ent_ex, eex);
+    UP(p->ent_wy, ewy);
+    UP(p->angle_flip, flip);
+#undef UP
+    k.dea = p->dea;
+    k.twN = p->twN;
+    k.twG = p->twG;
+    k.twD = p->twD;
+    k.row_off = p->row_off;
+    k.ent_p = p->ent_p;
+    k.ent_key = p->ent_key;
+    k.ent_s = p->ent_s;
+    k.ent_ex = p->ent_ex;
+    k.ent_wy = p->ent_wy;
+    k.angle_flip = p->angle_flip;
+
+    // launch configuration
+    int cp = 4;
+    while (cp > 1 && (cp * 2 * N * 8 > 96 * 1024 || 2 * cp * N / 16 > 1024 || 2 * cp > N)) cp >>= 1;
+    p->cp_col = cp;
+    p->threads_col = std::max(64, 2 * cp * N / 16);
+    p->threads_row = std::max(128, N / 8);
+    p->threads_det = 256;
+    p->smem_col = (size_t)cp * 2 * N * sizeof(float2);
+    p->smem_row_fwd = (size_t)2 * N * sizeof(float2);
+    p->smem_row_adj = p->smem_row_fwd + (size_t)2 * (kmax - kmin + 1) * sizeof(int);
+    p->smem_det = (size_t)(3 * D + k.rp.rad[0]) * sizeof(float2);
+    if (p->threads_col > 1024 || p->threads_row > 1024 || p->smem_det > 200 * 1024 ||
+        p->smem_row_adj > 200 * 1024) {
+        tc_plan_free(p);
+        return TC_ERR_UNSUPPORTED;
+    }
+
+    // scratch
+    const size_t MB = (size_t)max_batch;
+    p->slot = std::max(TC_RED_BLOCKS, (int)(((A + 1) / 2) * MB));
+    if ((rc = alloc_dev((void **)&p->tu, MB * R * N * sizeof(float2), bytes)) ||
+        (rc = alloc_dev((void **)&p->pv, MB * w * (size_t)k.AM * sizeof(float2), bytes)) ||
+        (rc = alloc_dev((void **)&p->sr, MB * (size_t)A * D * sizeof(float), bytes)) ||
+        (rc = alloc_dev((void **)&p->partials, (size_t)TC_N_SLOTS * p->slot * sizeof(double), bytes)) ||
+        (rc = alloc_dev((void **)&p->scal, SC_COUNT * sizeof(double), bytes))) {
+        tc_plan_free(p);
+        return rc;
+    }
+    TC_CUDA(cudaMemset(p->scal, 0, SC_COUNT * sizeof(double)));
+    p->bytes = bytes;
+    if ((rc = radon_configure_kernels(p))) {
+        tc_plan_free(p);
+        return rc;
+    }
+    *out = p;
+    return TC_OK;
+}

@@ -1,0 +1,328 @@
+// NUFFT Radon projector A and back-projector A^T (arXiv 2304.12934, Sec. 2.2
+// Eqs. nufft, nufft2, nufft3 and their reverse order; Sec. 3 Eq. transpose).
+//
+// Forward, per slice (image f, N x N, grid G = 2N, kernel width w):
+//   col pass   deapodise by 1/(psi(x) psi(y)) and FFT_G along y of two real
+//              columns packed as one complex column; keep grid rows
+//              jy = jmin..jmax (the half plane touched by the polar points)
+//   row pass   FFT_G along x of one grid row (G outputs from N non-zero
+//              inputs, as two N-point FFTs), then the interpolation partial
+//              phi(gy - jy) * sum_t phi(gx - jx_t) F(jx_t, jy) of every polar
+//              point whose y-footprint contains the row, stored per tap row
+//              (no atomics: every (point, tap row) slot has one writer)
+//   det pass   sum the w partials of each point, C2R inverse DFT of length D
+//              of two angles packed as one complex row, scale 1/D, epilogue
+// Adjoint, per slice, the transposes in reverse order:
+//   det pass   real-to-complex DFT of two sinogram rows, Hermitian weights
+//   row pass   spread by gather: every grid cell of the row sums the polar
+//              points whose footprint covers it, read from per-row bins
+//              sorted by jx0 (atomic-free, fixed summation order), then an
+//              inverse FFT_G along x evaluated at the N image columns
+//   col pass   Hermitian completion, inverse FFT_G along y at the N image
+//              rows for two columns at once, real part, deapodise
+#include "common.cuh"
+#include "profile.cuh"
+#include "fft.cuh"
+
+namespace {
+
+__device__ __forceinline__ float2 grid_cell(const float2 *eo, int N, int c) {
+    // cell c of a G-row stored as [even cells | odd cells]
+    return eo[(c & 1) * N + (c >> 1)];
+}
+
+// ------------------------------------------------------------ forward ------
+__global__ void __launch_bounds__(512) k_fwd_col(const float *__restrict__ x, float2 *__restrict__ T,
+                          const KArgs g, int CP) {
+    extern __shared__ float2 sm[];  // [CP][2][N]
+    const int N = g.N, b = blockIdx.y;
+    const int x0base = blockIdx.x * CP * 2;
+    const float *xs = x + (size_t)b * N * N;
+    for (int idx = threadIdx.x; idx < N * CP; idx += blockDim.x) {
+        const int pp = idx % CP, iy = idx / CP;
+        const int xc = x0base + 2 * pp;
+        const float2 f = *reinterpret_cast<const float2 *>(xs + (size_t)iy * N + xc);
+        const float dy = g.dea[iy];
+        const float2 z = make_float2(f.x * g.dea[xc] * dy, f.y * g.dea[xc + 1] * dy);
+        const int q = (iy - N / 2) & (N - 1);
+        sm[(pp * 2) * N + q] = z;
+        sm[(pp * 2 + 1) * N + q] = cmul(z, g.twG[iy]);
+    }
+    __syncthreads();
+    fft_pow2<-1>(sm, N, g.log2N, 2 * CP, g.twN);
+    float2 *Tb = T + (size_t)b * g.R * N;
+    const int Gm = g.G - 1;
+    for (int idx = threadIdx.x; idx < g.R * CP; idx += blockDim.x) {
+        const int pp = idx % CP, r = idx / CP;
+        const int jy = g.jmin + r;
+        const float2 *eo = sm + pp * 2 * N;
+        const float2 zp = grid_cell(eo, N, jy & Gm);
+        const float2 zm = cconj(grid_cell(eo, N, (-jy) & Gm));
+        const float2 d = csub(zp, zm);
+        float4 o;
+        o.x = 0.5f * (zp.x + zm.x);
+        o.y = 0.5f * (zp.y + zm.y);
+        o.z = 0.5f * d.y;   // (zp - zm) / (2i)
+        o.w = -0.5f * d.x;
+        *reinterpret_cast<float4 *>(Tb + (size_t)r * N + x0base + 2 * pp) = o;
+    }
+}
+
+__global__ void __launch_bounds__(512) k_fwd_row(const float2 *__restrict__ T, float2 *__restrict__ P,
+                          const KArgs g) {
+    extern __shared__ float2 sm[];  // [2][N]
+    const int N = g.N, r = blockIdx.x, b = blockIdx.y;
+    const float2 *Tr = T + ((size_t)b * g.R + r) * N;
+    for (int ix = threadIdx.x; ix < N; ix += blockDim.x) {
+        const float2 v = Tr[ix];
+        const int q = (ix - N / 2) & (N - 1);
+        sm[q] = v;
+        sm[N + q] = cmul(v, g.twG[ix]);
+    }
+    __syncthreads();
+    fft_pow2<-1>(sm, N, g.log2N, 2, g.twN);
+    float2 *Pb = P + (size_t)b * g.w * g.AM;
+    const int e1 = g.row_off[r + 1];
+    const int Gm = g.G - 1;
+    for (int e = g.row_off[r] + threadIdx.x; e < e1; e += blockDim.x) {
+        const int key = g.ent_key[e];
+        const float ex = g.ent_ex[e];
+        float2 acc = make_float2(0.f, 0.f);
+        for (int t = 0; t < g.w; ++t) {
+            const float wt = es_kernel(((float)t - ex) * g.inv_h, g.beta);
+            cfma(acc, wt, grid_cell(sm, N, (key + t) & Gm));
+        }
+        const float wy = g.ent_wy[e];
+        Pb[(size_t)g.ent_s[e] * g.AM + g.ent_p[e]] = cscale(acc, wy);
+    }
+}
+
+// mode bits
+#define DET_WRITE_Y 1
+#define DET_RESID 2
+#define DET_OBJ 4
+
+__global__ void __launch_bounds__(256) k_fwd_det(const float2 *__restrict__ P, float *__restrict__ y,
+                          const float *__restrict__ bsino, const float *__restrict__ wsino,
+                          float *__restrict__ resid, double *__restrict__ partials,
+                          const KArgs g, int mode) {
+    extern __shared__ float2 sm[];  // [D] bufA, [D] bufB, [D] tw, [rad0] root
+    __shared__ double red[32];
+    const int D = g.D, Mh = g.Mh, A = g.A;
+    const int a0 = 2 * blockIdx.x, b = blockIdx.y;
+    const bool has1 = (a0 + 1) < A;
+    float2 *bufA = sm, *bufB = sm + D, *tw = sm + 2 * D, *root0 = sm + 3 * D;
+    const int R0 = g.rp.rad[0], per0 = D / R0;
+    for (int k = threadIdx.x; k < D; k += blockDim.x) tw[k] = g.twD[k];
+    for (int k = threadIdx.x; k < R0; k += blockDim.x) root0[k] = g.twD[k * per0];
+    const float2 *Pb = P + (size_t)b * g.w * g.AM;
+    for (int m = threadIdx.x; m < Mh; m += blockDim.x) {
+        float2 c0 = make_float2(0.f, 0.f), c1 = make_float2(0.f, 0.f);
+        for (int s = 0; s < g.w; ++s) {
+            const float2 *pl = Pb + (size_t)s * g.AM;
+            c0 = cadd(c0, pl[(size_t)a0 * Mh + m]);
+            if (has1) c1 = cadd(c1, pl[(size_t)(a0 + 1) * Mh + m]);
+        }
+        if (g.angle_flip[a0]) c0 = cconj(c0);
+        if (has1 && g.angle_flip[a0 + 1]) c1 = cconj(c1);
+        const float sg = (m & 1) ? -1.f : 1.f;
+        float2 X0 = cscale(c0, sg), X1 = cscale(c1, sg);
+        if (2 * m == D) { X0.y = 0.f; X1.y = 0.f; }
+        bufA[m] = make_float2(X0.x - X1.y, X0.y + X1.x);
+        if (m > 0 && 2 * m < D) bufA[D - m] = make_float2(X0.x + X1.y, X1.x - X0.y);
+    }
+    __syncthreads();
+    const float2 *res = fft_mixed<+1>(bufA, bufB, g.rp, tw, root0);
+    float objv = 0.f;
+    for (int i = threadIdx.x; i < D; i += blockDim.x) {
+        const float2 z = res[i];
+        const float yv[2] = {z.x * g.invD, z.y * g.invD};
+        for (int h = 0; h < 2; ++h) {
+            if (h == 1 && !has1) break;
+            const size_t o = ((size_t)b * A + a0 + h) * D + i;
+            float v = yv[h];
+            if (mode & DET_WRITE_Y) y[o] = v;
+            if (mode & DET_RESID) {
+                const float r = bsino ? v - bsino[o] : v;
+                const float wt = wsino ? wsino[o] : 1.f;
+                resid[o] = wt * r;
+                objv = fmaf(0.5f * wt * r, r, objv);
+            }
+        }
+    }
+    if (mode & DET_OBJ) {
+        const double tot = block_sum_f64(objv, red);
+        if (threadIdx.x == 0) partials[(size_t)b * gridDim.x + blockIdx.x] = tot;
+    }
+}
+
+// ------------------------------------------------------------ adjoint ------
+__global__ void __launch_bounds__(256) k_adj_det(const float *__restrict__ ysino, float2 *__restrict__ V,
+                          const KArgs g) {
+    extern __shared__ float2 sm[];
+    const int D = g.D, Mh = g.Mh, A = g.A;
+    const int a0 = 2 * blockIdx.x, b = blockIdx.y;
+    const bool has1 = (a0 + 1) < A;
+    float2 *bufA = sm, *bufB = sm + D, *tw = sm + 2 * D, *root0 = sm + 3 * D;
+    const int R0 = g.rp.rad[0], per0 = D / R0;
+    for (int k = threadIdx.x; k < D; k += blockDim.x) tw[k] = g.twD[k];
+    for (int k = threadIdx.x; k < R0; k += blockDim.x) root0[k] = g.twD[k * per0];
+    const float *y0 = ysino + ((size_t)b * A + a0) * D;
+    for (int i = threadIdx.x; i < D; i += blockDim.x)
+        bufA[i] = make_float2(y0[i], has1 ? y0[D + i] : 0.f);
+    __syncthreads();
+    const float2 *Z = fft_mixed<-1>(bufA, bufB, g.rp, tw, root0);
+    float2 *Vb = V + (size_t)b * g.w * g.AM;
+    for (int m = threadIdx.x; m < Mh; m += blockDim.x) {
+        const float2 zp = Z[m];
+        const float2 zm = cconj(Z[m == 0 ? 0 : D - m]);
+        // Y_a0 = (zp + zm)/2, Y_a1 = (zp - zm)/(2i); weight mu_m nu_m (-1)^m / D
+        const float mn = (m == 0 || 2 * m == D) ? 1.f : 2.f;
+        const float sc = ((m & 1) ? -mn : mn) * 0.5f * g.invD;
+        float2 v0 = make_float2(sc * (zp.x + zm.x), sc * (zp.y + zm.y));
+        if (g.angle_flip[a0]) v0 = cconj(v0);
+        Vb[(size_t)a0 * Mh + m] = v0;
+        if (has1) {
+            float2 v1 = make_float2(sc * (zp.y - zm.y), -sc * (zp.x - zm.x));
+            if (g.angle_flip[a0 + 1]) v1 = cconj(v1);
+            Vb[(size_t)(a0 + 1) * Mh + m] = v1;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(512) k_adj_row(const float2 *__restrict__ V, float2 *__restrict__ U,
+                          const KArgs g) {
+    extern __shared__ float2 sm[];  // [2][N] grid row, then run tables
+    const int N = g.N, G = g.G, r = blockIdx.x, b = blockIdx.y;
+    const int nkeys = g.kmax - g.kmin + 1;
+    int *rstart = reinterpret_cast<int *>(sm + 2 * N);
+    int *rlen = rstart + nkeys;
+    const int e0 = g.row_off[r], e1 = g.row_off[r + 1];
+    for (int k = threadIdx.x; k < nkeys; k += blockDim.x) rlen[k] = 0;
+    __syncthreads();
+    for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+        const int key = g.ent_key[e];
+        if (e == e0 || g.ent_key[e - 1] != key) rstart[key - g.kmin] = e;
+    }
+    __syncthreads();
+    for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+        const int key = g.ent_key[e];
+        if (e == e1 - 1 || g.ent_key[e + 1] != key) rlen[key - g.kmin] = e + 1 - rstart[key - g.kmin];
+    }
+    __syncthreads();
+    const float2 *Vb = V + (size_t)b * g.w * g.AM;
+    for (int c = threadIdx.x; c < G; c += blockDim.x) {
+        float2 acc = make_float2(0.f, 0.f);
+        for (int t = 0; t < g.w; ++t) {
+            for (int rep = 0; rep < 2; ++rep) {
+                const int k = c - t - rep * G;
+                if (k < g.kmin || k > g.kmax) continue;
+                const int ki = k - g.kmin;
+                const int len = rlen[ki];
+                if (len == 0) continue;
+                const int st = rstart[ki];
+                for (int e = st; e < st + len; ++e) {
+                    const float wt = g.ent_wy[e] * es_kernel(((float)t - g.ent_ex[e]) * g.inv_h, g.beta);
+                    cfma(acc, wt, Vb[g.ent_p[e]]);
+                }
+            }
+        }
+        sm[(c & 1) * N + (c >> 1)] = acc;
+    }
+    __syncthreads();
+    fft_pow2<+1>(sm, N, g.log2N, 2, g.twN);
+    float2 *Ur = U + ((size_t)b * g.R + r) * N;
+    for (int ix = threadIdx.x; ix < N; ix += blockDim.x) {
+        const int q = (ix - N / 2) & (N - 1);
+        Ur[ix] = cadd(sm[q], cmul(sm[N + q], cconj(g.twG[ix])));
+    }
+}
+
+__global__ void __launch_bounds__(512) k_adj_col(const float2 *__restrict__ U, float *__restrict__ x,
+                          const KArgs g, int CP) {
+    extern __shared__ float2 sm[];  // [CP][2][N]
+    const int N = g.N, G = g.G, b = blockIdx.y;
+    const int x0base = blockIdx.x * CP * 2;
+    const float2 *Ub = U + (size_t)b * g.R * N;
+    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int idx = threadIdx.x; idx < G * CP; idx += blockDim.x) {
+        const int pp = idx % CP, jy = idx / CP;
+        const int xc = x0base + 2 * pp;
+        const int jn = (G - jy) & (G - 1);
+        const int js_p = jy <= g.jmax ? jy : jy - G;
+        const int js_n = jn <= g.jmax ? jn : jn - G;
+        const float4 up = (js_p >= g.jmin)
+            ? *reinterpret_cast<const float4 *>(Ub + (size_t)(js_p - g.jmin) * N + xc) : zero4;
+        const float4 un = (js_n >= g.jmin)
+            ? *reinterpret_cast<const float4 *>(Ub + (size_t)(js_n - g.jmin) * N + xc) : zero4;
+        // Hermitian parts of the two columns, packed as H0 + i H1
+        const float h0x = 0.5f * (up.x + un.x), h0y = 0.5f * (up.y - un.y);
+        const float h1x = 0.5f * (up.z + un.z), h1y = 0.5f * (up.w - un.w);
+        sm[(pp * 2 + (jy & 1)) * N + (jy >> 1)] = make_float2(h0x - h1y, h0y + h1x);
+    }
+    __syncthreads();
+    fft_pow2<+1>(sm, N, g.log2N, 2 * CP, g.twN);
+    float *xb = x + (size_t)b * N * N;
+    for (int idx = threadIdx.x; idx < N * CP; idx += blockDim.x) {
+        const int pp = idx % CP, iy = idx / CP;
+        const int xc = x0base + 2 * pp;
+        const int q = (iy - N / 2) & (N - 1);
+        const float2 *eo = sm + pp * 2 * N;
+        const float2 v = cadd(eo[q], cmul(eo[N + q], cconj(g.twG[iy])));
+        const float dy = g.dea[iy];
+        *reinterpret_cast<float2 *>(xb + (size_t)iy * N + xc) =
+            make_float2(v.x * g.dea[xc] * dy, v.y * g.dea[xc + 1] * dy);
+    }
+}
+
+}  // namespace
+
+int launch_radon_fwd_chunk(tc_plan *p, const float *x, float *y, int nb,
+                           const float *b, const float *w, float *resid,
+                           double *obj_acc, cudaStream_t s) {
+    const KArgs &g = p->k;
+    dim3 gc(g.N / (2 * p->cp_col), nb);
+    TC_PROFILED(TCK_FWD_COL, s, k_fwd_col<<<gc, p->threads_col, p->smem_col, s>>>(x, p->tu, g, p->cp_col));
+    TC_LAUNCHED("k_fwd_col");
+    dim3 gr(g.R, nb);
+    TC_PROFILED(TCK_FWD_ROW, s, k_fwd_row<<<gr, p->threads_row, p->smem_row_fwd, s>>>(p->tu, p->pv, g));
+    TC_LAUNCHED("k_fwd_row");
+    dim3 gd((g.A + 1) / 2, nb);
+    int mode = 0;
+    if (y) mode |= DET_WRITE_Y;
+    if (resid) mode |= DET_RESID;
+    if (resid && obj_acc) mode |= DET_OBJ;
+    TC_PROFILED(TCK_FWD_DET, s, k_fwd_det<<<gd, p->threads_det, p->smem_det, s>>>(p->pv, y, b, w, resid, p->partials, g, mode));
+    TC_LAUNCHED("k_fwd_det");
+    if (mode & DET_OBJ) {
+        int rc = launch_reduce_finalize(p->partials, gd.x * gd.y, obj_acc, 1, 1.0, s);
+        if (rc) return rc;
+    }
+    return TC_OK;
+}
+
+int launch_radon_adj_chunk(tc_plan *p, const float *y, float *x, int nb,
+                           cudaStream_t s) {
+    const KArgs &g = p->k;
+    dim3 gd((g.A + 1) / 2, nb);
+    TC_PROFILED(TCK_ADJ_DET, s, k_adj_det<<<gd, p->threads_det, p->smem_det, s>>>(y, p->pv, g));
+    TC_LAUNCHED("k_adj_det");
+    dim3 gr(g.R, nb);
+    TC_PROFILED(TCK_ADJ_ROW, s, k_adj_row<<<gr, p->threads_row, p->smem_row_adj, s>>>(p->pv, p->tu, g));
+    TC_LAUNCHED("k_adj_row");
+    dim3 gc(g.N / (2 * p->cp_col), nb);
+    TC_PROFILED(TCK_ADJ_COL, s, k_adj_col<<<gc, p->threads_col, p->smem_col, s>>>(p->tu, x, g, p->cp_col));
+    TC_LAUNCHED("k_adj_col");
+    return TC_OK;
+}
+
+int radon_configure_kernels(tc_plan *p) {
+    // opt in to large dynamic shared memory where needed
+    TC_CUDA(cudaFuncSetAttribute(k_fwd_col, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem_col));
+    TC_CUDA(cudaFuncSetAttribute(k_adj_col, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem_col));
+    TC_CUDA(cudaFuncSetAttribute(k_fwd_row, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem_row_fwd));
+    TC_CUDA(cudaFuncSetAttribute(k_adj_row, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem_row_adj));
+    TC_CUDA(cudaFuncSetAttribute(k_fwd_det, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem_det));
+    TC_CUDA(cudaFuncSetAttribute(k_adj_det, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem_det));
+    return TC_OK;
+}

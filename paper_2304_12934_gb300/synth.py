@@ -182,3 +182,59 @@ WORKLOADS = {
 def det_for(n: int) -> int:
     """Detector width for a side n: 2*round(n/sqrt 2) (covers the image disk)."""
     return 2 * int(round(n / math.sqrt(2.0)))
+
+
+# ------------------------------------------------- large volumes (torch) ----
+def ellipsoid_bodies(n: int, nz: int, n_ellipsoids: int = 10, scale: float = 1.0,
+                     seed: int = BASE_SEED):
+    """Seeded ellipsoids rotated about z only (same draws as
+    ellipsoid_volume_slices): rows (cx, cy, cz, a, b, c, phi, rho)."""
+    rng = np.random.default_rng(seed)
+    h, hz = n / 2.0, nz / 2.0
+    rows = []
+    for _ in range(n_ellipsoids):
+        r = 0.7 * math.sqrt(rng.uniform())
+        ang = rng.uniform(0.0, 2.0 * math.pi)
+        a, b = rng.uniform(0.05, 0.35, size=2)
+        cz = rng.uniform(-0.6, 0.6)
+        c = rng.uniform(0.1, 0.4)
+        phi = rng.uniform(0.0, math.pi)
+        rho = rng.uniform(0.0, 1.0)
+        rows.append((r * math.cos(ang) * h, r * math.sin(ang) * h, cz * hz,
+                     a * h, b * h, c * hz, phi, rho * scale))
+    return np.array(rows, dtype=np.float64)
+
+
+def ellipsoid_sinogram_torch(n, nz, theta, n_det, device, scale=1.0, seed=BASE_SEED,
+                             z_chunk=64):
+    """Analytic line integrals [nz, A, D] (float32, on `device`) of the
+    ellipsoid phantom: slice z of an ellipsoid is an ellipse with semi-axes
+    scaled by k = sqrt(1 - ((z - cz)/c)^2), whose projection is
+    2 rho a b sqrt(k^2 r^2 - d^2) / r^2, r^2 = a^2 cos^2(th - phi) + b^2 sin^2(th - phi)."""
+    import torch
+    bodies = ellipsoid_bodies(n, nz, scale=scale, seed=seed)
+    th = torch.as_tensor(np.asarray(theta, np.float64), device=device)
+    t = torch.arange(n_det, device=device, dtype=torch.float64) - n_det // 2
+    out = torch.empty((nz, th.shape[0], n_det), device=device, dtype=torch.float32)
+    zc = torch.arange(nz, device=device, dtype=torch.float64) - nz // 2
+    for z0 in range(0, nz, z_chunk):
+        z1 = min(nz, z0 + z_chunk)
+        acc = torch.zeros((z1 - z0, th.shape[0], n_det), device=device, dtype=torch.float64)
+        for cx, cy, cz, a, b, c, phi, rho in bodies:
+            k2 = (1.0 - ((zc[z0:z1] - cz) / c) ** 2).clamp(min=0.0)
+            r2 = (a * torch.cos(th - phi)) ** 2 + (b * torch.sin(th - phi)) ** 2
+            tc = cx * torch.cos(th) + cy * torch.sin(th)
+            d = t[None, :] - tc[:, None]
+            rem = k2[:, None, None] * r2[None, :, None] - (d * d)[None]
+            acc += 2.0 * rho * a * b * torch.sqrt(rem.clamp(min=0.0)) / r2[None, :, None]
+        out[z0:z1] = acc.float()
+    return out
+
+
+def poisson_measurement_torch(p_true, i0: float, seed: int):
+    """Torch version of poisson_measurement (same model, on p_true's device)."""
+    import torch
+    g = torch.Generator(device=p_true.device)
+    g.manual_seed(seed)
+    counts = torch.poisson((i0 * torch.exp(-p_true.double())), generator=g).clamp_(min=1.0)
+    return (-torch.log(counts / i0)).float(), (counts / i0).float()

@@ -1,0 +1,65 @@
+"""The C-ABI library loads on a machine without a GPU and exports every
+function that include/*.h declares (no compute calls here)."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        for m in re.finditer(r"^[A-Za-z_][\w\s\*]*?\b([a-z_][a-z0-9_]*)\s*\(", src, flags=re.M):
+            names.add(m.group(1))
+    return names
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for fn in ("radon_fwd", "radon_adj", "mbir_grad", "mbir_solve", "tc_plan_create",
+               "tc_plan_destroy", "tc_status_string"):
+        assert fn in names
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_2304_12934_gb300 import build
+    path = build.build()
+    lib = ctypes.CDLL(path)
+    missing = [n for n in sorted(_declared()) if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_status_strings_without_gpu():
+    from paper_2304_12934_gb300 import api
+    L = api.load()
+    assert L.tc_status_string(0) == b"ok"
+    assert L.tc_status_string(-1) == b"invalid argument"
+    assert L.tc_status_string(12345) == b"unknown status"
+
+
+def test_invalid_geometry_rejected_on_host():
+    """Argument checks run before any CUDA call."""
+    from paper_2304_12934_gb300 import api
+    L = api.load()
+    h = ctypes.c_void_p()
+    for n, a, d, os_, w in ((100, 10, 20, 2, 7), (64, 10, 21, 2, 7), (64, 0, 20, 2, 7),
+                            (64, 10, 20, 3, 7), (64, 10, 20, 2, 9), (8, 10, 20, 2, 7)):
+        g = api._Geom(n, a, d, ctypes.POINTER(ctypes.c_double)(), os_, w)
+        assert L.tc_plan_create(ctypes.byref(g), 1, ctypes.byref(h)) == -1
+        assert not h.value
+    assert L.radon_fwd(None, None, None, 1, None) == -1
+    assert L.tc_plan_destroy(None) == 0
+
+
+def test_product_path_does_not_import_oracle():
+    for f in glob.glob(os.path.join(ROOT, "paper_2304_12934_gb300", "**", "*.*"), recursive=True):
+        if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+            src = open(f).read()
+            assert "import oracle" not in src and "from oracle" not in src, f
+            assert "radon_oracle" not in src, f
