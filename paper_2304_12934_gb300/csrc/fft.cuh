@@ -1,10 +1,11 @@
 // Shared-memory FFTs used by the NUFFT passes.
 //
 // fft_pow2   : in-place Stockham autosort FFT of `cnt` back-to-back power-of-two
-//              transforms of length n (radix-4 stages, one radix-2 stage when
-//              log2 n is odd).  Each stage loads all of its butterflies into
-//              registers, synchronises, then stores, so a single buffer
-//              suffices.  Requires blockDim.x >= cnt * n / 16.
+//              transforms of length n: radix-16 stages with register
+//              butterflies, then one radix-8/4/2 stage.  Each stage loads all
+//              of its butterflies into registers, synchronises, then stores,
+//              so a single (padded) buffer suffices.  Requires
+//              blockDim.x >= cnt * n / 16.
 // fft_mixed  : out-of-place Stockham FFT of one length-n transform for an
 //              arbitrary factorisation (the detector length D, e.g. 2896 =
 //              181 * 4 * 4), one output per thread and stage, ping-pong buffers.
@@ -28,81 +29,141 @@ __device__ __forceinline__ float2 mul_si(float2 v) {
     return SIGN > 0 ? make_float2(-v.y, v.x) : make_float2(v.y, -v.x);
 }
 
+// Shared-memory index padding: one float2 of padding after every 16, so the
+// strided butterfly stores of the first stages hit distinct banks.
+__host__ __device__ __forceinline__ int spad(int i) { return i + (i >> 4); }
+// float2 elements to allocate for m padded elements
+__host__ __device__ __forceinline__ int spad_size(int m) { return m + (m >> 4) + 1; }
+
+// In-register DFTs of length 2, 4, 8, 16 (natural order in and out).
 template <int SIGN>
-__device__ void fft_pow2(float2 *s, int n, int log2n, int cnt,
-                         const float2 *__restrict__ tw) {
-    const int nt = blockDim.x, tid = threadIdx.x;
-    int Ns = 1, logNs = 0;
-    while (Ns < n) {
-        const int rem = log2n - logNs;
-        if (rem >= 2) {
-            // radix 4
-            const int logper = log2n - 2, per = 1 << logper;
-            const int total = cnt << logper;
-            const int twstride = n >> (logNs + 2);
-            float2 v[4][4];
+__device__ __forceinline__ void dft4(float2 &x0, float2 &x1, float2 &x2, float2 &x3) {
+    const float2 a0 = cadd(x0, x2), a1 = csub(x0, x2);
+    const float2 b0 = cadd(x1, x3), b1 = mul_si<SIGN>(csub(x1, x3));
+    x0 = cadd(a0, b0);
+    x1 = cadd(a1, b1);
+    x2 = csub(a0, b0);
+    x3 = csub(a1, b1);
+}
+
+// exp(SIGN * 2 pi i j / 16) for the constant twiddles of the 8- and 16-point DFTs
+template <int SIGN>
+__device__ __forceinline__ float2 w16(int j) {
+    const float c1 = 0.92387953251128674f, s1 = 0.38268343236508977f, r2 = 0.70710678118654752f;
+    float cr, ci;
+    switch (j) {
+        case 1: cr = c1; ci = s1; break;
+        case 2: cr = r2; ci = r2; break;
+        case 3: cr = s1; ci = c1; break;
+        case 4: cr = 0.f; ci = 1.f; break;
+        case 6: cr = -r2; ci = r2; break;
+        case 9: cr = -c1; ci = -s1; break;
+        default: cr = 1.f; ci = 0.f; break;
+    }
+    return make_float2(cr, SIGN > 0 ? ci : -ci);
+}
+
+template <int SIGN, int R>
+__device__ __forceinline__ void dft_reg(float2 *v) {
+    if (R == 2) {
+        const float2 t = v[0];
+        v[0] = cadd(t, v[1]);
+        v[1] = csub(t, v[1]);
+    } else if (R == 4) {
+        dft4<SIGN>(v[0], v[1], v[2], v[3]);
+    } else if (R == 8) {
+        // n = 4 n1 + n2, k = k1 + 2 k2: DFT2 over n1, twiddle W8^(n2 k1), DFT4 over n2
+        float2 y[4][2];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const int it = tid + i * nt;
-                if (it < total) {
-                    const int tr = it >> logper, j = it & (per - 1), k = j & (Ns - 1);
-                    const float2 *src = s + (tr << log2n) + j;
-                    v[i][0] = src[0];
+        for (int n2 = 0; n2 < 4; ++n2) {
+            y[n2][0] = cadd(v[n2], v[4 + n2]);
+            y[n2][1] = csub(v[n2], v[4 + n2]);
+        }
+        y[1][1] = cmul(y[1][1], w16<SIGN>(2));
+        y[2][1] = mul_si<SIGN>(y[2][1]);
+        y[3][1] = cmul(y[3][1], w16<SIGN>(6));
 #pragma unroll
-                    for (int q = 1; q < 4; ++q)
-                        v[i][q] = cmul(src[q * per], tw_get<SIGN>(tw, q * k * twstride));
-                }
-            }
-            __syncthreads();
+        for (int k1 = 0; k1 < 2; ++k1) {
+            dft4<SIGN>(y[0][k1], y[1][k1], y[2][k1], y[3][k1]);
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const int it = tid + i * nt;
-                if (it < total) {
-                    const int tr = it >> logper, j = it & (per - 1), k = j & (Ns - 1);
-                    const float2 a0 = cadd(v[i][0], v[i][2]), a1 = csub(v[i][0], v[i][2]);
-                    const float2 b0 = cadd(v[i][1], v[i][3]), b1 = mul_si<SIGN>(csub(v[i][1], v[i][3]));
-                    float2 *dst = s + (tr << log2n) + ((j >> logNs) << (logNs + 2)) + k;
-                    dst[0] = cadd(a0, b0);
-                    dst[Ns] = cadd(a1, b1);
-                    dst[2 * Ns] = csub(a0, b0);
-                    dst[3 * Ns] = csub(a1, b1);
-                }
-            }
-            __syncthreads();
-            Ns <<= 2;
-            logNs += 2;
-        } else {
-            // radix 2 (last stage when log2 n is odd)
-            const int logper = log2n - 1, per = 1 << logper;
-            const int total = cnt << logper;
-            const int twstride = n >> (logNs + 1);
-            float2 v[8][2];
+            for (int k2 = 0; k2 < 4; ++k2) v[k1 + 2 * k2] = y[k2][k1];
+        }
+    } else if (R == 16) {
+        // n = 4 n1 + n2, k = k1 + 4 k2: DFT4 over n1, twiddle W16^(n2 k1), DFT4 over n2
+        float2 y[4][4];
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const int it = tid + i * nt;
-                if (it < total) {
-                    const int tr = it >> logper, j = it & (per - 1), k = j & (Ns - 1);
-                    const float2 *src = s + (tr << log2n) + j;
-                    v[i][0] = src[0];
-                    v[i][1] = cmul(src[per], tw_get<SIGN>(tw, k * twstride));
-                }
-            }
-            __syncthreads();
+        for (int n2 = 0; n2 < 4; ++n2) {
+            y[n2][0] = v[n2];
+            y[n2][1] = v[4 + n2];
+            y[n2][2] = v[8 + n2];
+            y[n2][3] = v[12 + n2];
+            dft4<SIGN>(y[n2][0], y[n2][1], y[n2][2], y[n2][3]);
+        }
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const int it = tid + i * nt;
-                if (it < total) {
-                    const int tr = it >> logper, j = it & (per - 1), k = j & (Ns - 1);
-                    float2 *dst = s + (tr << log2n) + ((j >> logNs) << (logNs + 1)) + k;
-                    dst[0] = cadd(v[i][0], v[i][1]);
-                    dst[Ns] = csub(v[i][0], v[i][1]);
-                }
-            }
-            __syncthreads();
-            Ns <<= 1;
-            logNs += 1;
+        for (int n2 = 1; n2 < 4; ++n2)
+#pragma unroll
+            for (int k1 = 1; k1 < 4; ++k1) y[n2][k1] = cmul(y[n2][k1], w16<SIGN>(n2 * k1));
+#pragma unroll
+        for (int k1 = 0; k1 < 4; ++k1) {
+            dft4<SIGN>(y[0][k1], y[1][k1], y[2][k1], y[3][k1]);
+#pragma unroll
+            for (int k2 = 0; k2 < 4; ++k2) v[k1 + 4 * k2] = y[k2][k1];
         }
     }
+}
+
+// One in-place Stockham stage of radix R over cnt transforms of length n
+// (padded indexing).  Every thread loads its IT butterflies, the block
+// synchronises, then all store.
+template <int SIGN, int R, int LOGR, int IT>
+__device__ __forceinline__ void stockham_stage(float2 *s, int log2n, int cnt, int Ns, int logNs,
+                                               const float2 *__restrict__ tw) {
+    const int nt = blockDim.x, tid = threadIdx.x;
+    const int logper = log2n - LOGR, per = 1 << logper;
+    const int total = cnt << logper;
+    const int twshift = log2n - logNs - LOGR;  // twiddle stride n / (Ns R)
+    float2 v[IT][R];
+#pragma unroll
+    for (int i = 0; i < IT; ++i) {
+        const int it = tid + i * nt;
+        if (it < total) {
+            const int tr = it >> logper, j = it & (per - 1), k = j & (Ns - 1);
+            const int base = (tr << log2n) + j;
+            v[i][0] = s[spad(base)];
+#pragma unroll
+            for (int q = 1; q < R; ++q)
+                v[i][q] = cmul(s[spad(base + q * per)], tw_get<SIGN>(tw, (q * k) << twshift));
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < IT; ++i) {
+        const int it = tid + i * nt;
+        if (it < total) {
+            const int tr = it >> logper, j = it & (per - 1), k = j & (Ns - 1);
+            dft_reg<SIGN, R>(v[i]);
+            const int base = (tr << log2n) + ((j >> logNs) << (logNs + LOGR)) + k;
+#pragma unroll
+            for (int q = 0; q < R; ++q) s[spad(base + q * Ns)] = v[i][q];
+        }
+    }
+    __syncthreads();
+}
+
+// In-place FFT of cnt back-to-back length-n transforms (n = 2^log2n) in the
+// padded shared buffer s: radix-16 stages, then one radix-8/4/2 stage.
+// Requires blockDim.x >= cnt * n / 16.
+template <int SIGN>
+__device__ void fft_pow2(float2 *s, int n, int log2n, int cnt, const float2 *__restrict__ tw) {
+    int logNs = 0;
+    while (log2n - logNs >= 4) {
+        stockham_stage<SIGN, 16, 4, 1>(s, log2n, cnt, 1 << logNs, logNs, tw);
+        logNs += 4;
+    }
+    const int rem = log2n - logNs;
+    if (rem == 3) stockham_stage<SIGN, 8, 3, 2>(s, log2n, cnt, 1 << logNs, logNs, tw);
+    else if (rem == 2) stockham_stage<SIGN, 4, 2, 4>(s, log2n, cnt, 1 << logNs, logNs, tw);
+    else if (rem == 1) stockham_stage<SIGN, 2, 1, 8>(s, log2n, cnt, 1 << logNs, logNs, tw);
 }
 
 // Out-of-place mixed-radix Stockham; returns the buffer holding the result.

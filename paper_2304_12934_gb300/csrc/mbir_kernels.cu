@@ -17,63 +17,124 @@ struct PriorArgs {
     float w1, w2, w3;             // weights at distance 1, sqrt 2, sqrt 3
 };
 
-// rho(d) = u^2 / (c + |u|^(2-p)), u = d / sigma, and its derivative in d.
+// rho(d) = u^2 / (c + |u|^(2-p)), u = d / sigma, and its derivative in d
+// (fast approximate log2 / exp2 / reciprocal: ~1e-7 relative error).
 __device__ __forceinline__ void qggmrf(float d, const PriorArgs &a, float &rho, float &rhop) {
     const float u = d * a.inv_sigma;
     const float au = fabsf(u);
-    const float q = au > 0.f ? exp2f(a.qexp * log2f(au)) : 0.f;
-    const float inv = 1.0f / (a.c + q);
+    const float q = au > 0.f ? exp2f(a.qexp * __log2f(au)) : 0.f;
+    const float inv = __fdividef(1.0f, a.c + q);
     rho = u * u * inv;
     rhop = u * a.inv_sigma * fmaf(a.p, q, 2.0f * a.c) * inv * inv;
 }
 
-__global__ void k_prior(const float *__restrict__ f, float *__restrict__ g,
-                        double *__restrict__ partials, const PriorArgs a) {
+// qGGMRF prior on a volume [B][N][N] (slices consecutive along z).
+// A CTA owns a PTX x PTY column of voxels and marches along z holding a ring
+// (tile + 1-voxel halo) of two f planes in shared memory.  Each unordered
+// neighbour pair is evaluated once, at its lower voxel, along the 13 forward
+// directions (9 towards z+1, 4 in-plane); both voxels read the pair's rho'
+// from shared memory (the z+1 pairs are kept one step for the voxel above).
+// dims = 2 skips the z pairs and uses the 8-neighbour weights.
+#define PTX 32
+#define PTY 12
+#define PRX (PTX + 2)
+#define PRY (PTY + 2)
+#define PRS (PRX * PRY)
+#define PRIOR_THREADS 480
+
+__global__ void __launch_bounds__(PRIOR_THREADS) k_prior(const float *__restrict__ f, float *__restrict__ g,
+                                                          double *__restrict__ partials, const PriorArgs a) {
+    __shared__ float fpl[2][PRS];
+    __shared__ float Eu[2][9][PRS];
+    __shared__ float Ep[4][PRS];
     __shared__ double red[32];
-    const int N = a.N;
+    const int N = a.N, B = a.B;
     const size_t NN = (size_t)N * N;
-    const size_t total = NN * a.B;
+    const int h = threadIdx.x;
+    const int hx = h % PRX, hy = h / PRX;
+    const int x = blockIdx.x * PTX - 1 + hx, y = blockIdx.y * PTY - 1 + hy;
+    const bool ring = h < PRS;
+    const bool inb = ring && x >= 0 && x < N && y >= 0 && y < N;
+    const bool interior = inb && hx >= 1 && hx <= PTX && hy >= 1 && hy <= PTY;
+    const bool three = a.dims == 3;
+    // in-plane forward directions (dx, dy): (1,0) (-1,1) (0,1) (1,1)
+    const int pdx[4] = {1, -1, 0, 1}, pdy[4] = {0, 1, 1, 1};
+    const float pw[4] = {a.w1, a.w2, a.w1, a.w2};
+    auto ring_in = [&](int dx, int dy) {
+        const int nx = hx + dx, ny = hy + dy;
+        if (nx < 0 || nx >= PRX || ny < 0 || ny >= PRY) return false;
+        const int gx = x + dx, gy = y + dy;
+        return gx >= 0 && gx < N && gy >= 0 && gy < N;
+    };
+    auto is_interior = [&](int dx, int dy) {
+        const int nx = hx + dx, ny = hy + dy;
+        return nx >= 1 && nx <= PTX && ny >= 1 && ny <= PTY && x + dx < N && y + dy < N &&
+               x + dx >= 0 && y + dy >= 0;
+    };
+    if (ring) {
+        for (int u = 0; u < 9; ++u) {
+            Eu[0][u][h] = 0.f;
+            Eu[1][u][h] = 0.f;
+        }
+        fpl[0][h] = inb ? f[(size_t)y * N + x] : 0.f;
+    }
     double hacc = 0.0;
-    float hblk = 0.f;
-    int cnt = 0;
-    const int zlo = a.dims == 3 ? -1 : 0, zhi = a.dims == 3 ? 1 : 0;
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-         i += (size_t)gridDim.x * blockDim.x) {
-        const int ix = (int)(i % N);
-        const int iy = (int)((i / N) % N);
-        const int iz = (int)(i / NN);
-        const float fm = f[i];
-        float gs = 0.f, hs = 0.f;
-        for (int dz = zlo; dz <= zhi; ++dz) {
-            const int zz = iz + dz;
-            if (zz < 0 || zz >= a.B) continue;
-            for (int dy = -1; dy <= 1; ++dy) {
-                const int yy = iy + dy;
-                if (yy < 0 || yy >= N) continue;
-                for (int dx = -1; dx <= 1; ++dx) {
-                    const int xx = ix + dx;
-                    if (xx < 0 || xx >= N || (dz == 0 && dy == 0 && dx == 0)) continue;
-                    const int l1 = abs(dz) + abs(dy) + abs(dx);
-                    const float wgt = l1 == 1 ? a.w1 : (l1 == 2 ? a.w2 : a.w3);
-                    const float fn = f[(size_t)zz * NN + (size_t)yy * N + xx];
-                    float rho, rhop;
-                    qggmrf(fm - fn, a, rho, rhop);
-                    hs = fmaf(wgt, rho, hs);
-                    gs = fmaf(wgt, rhop, gs);
+    for (int z = 0; z < B; ++z) {
+        const int cur = z & 1, nxt = cur ^ 1;
+        const bool up = three && z + 1 < B;
+        if (ring && up) fpl[nxt][h] = inb ? f[(size_t)(z + 1) * NN + (size_t)y * N + x] : 0.f;
+        // 2D: slices are independent, each step loads its own plane
+        if (ring && !three && z > 0) fpl[cur][h] = inb ? f[(size_t)z * NN + (size_t)y * N + x] : 0.f;
+        __syncthreads();
+        float hs = 0.f;
+        if (ring) {
+            const float fm = fpl[cur][h];
+#pragma unroll
+            for (int u = 0; u < 9; ++u) {
+                const int dx = u % 3 - 1, dy = u / 3 - 1;
+                float e = 0.f;
+                if (up && inb && ring_in(dx, dy) && (interior || is_interior(dx, dy))) {
+                    float rho, rp;
+                    qggmrf(fm - fpl[nxt][h + dy * PRX + dx], a, rho, rp);
+                    e = rp;
+                    if (interior) hs = fmaf((dx == 0 && dy == 0) ? a.w1 : ((dx == 0 || dy == 0) ? a.w2 : a.w3), rho, hs);
                 }
+                Eu[cur][u][h] = e;
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                float e = 0.f;
+                if (inb && ring_in(pdx[q], pdy[q]) && (interior || is_interior(pdx[q], pdy[q]))) {
+                    float rho, rp;
+                    qggmrf(fm - fpl[cur][h + pdy[q] * PRX + pdx[q]], a, rho, rp);
+                    e = rp;
+                    if (interior) hs = fmaf(pw[q], rho, hs);
+                }
+                Ep[q][h] = e;
             }
         }
-        g[i] = fmaf(a.two_lambda, gs, g[i]);
-        hblk += hs;
-        if (++cnt == 8) {
-            hacc += (double)hblk;
-            hblk = 0.f;
-            cnt = 0;
+        __syncthreads();
+        if (interior) {
+            float gs = 0.f;
+            if (three) {
+#pragma unroll
+                for (int u = 0; u < 9; ++u) {
+                    const int dx = u % 3 - 1, dy = u / 3 - 1;
+                    const float wu = (dx == 0 && dy == 0) ? a.w1 : ((dx == 0 || dy == 0) ? a.w2 : a.w3);
+                    gs = fmaf(wu, Eu[cur][u][h] - Eu[nxt][u][h - dy * PRX - dx], gs);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                gs = fmaf(pw[q], Ep[q][h] - Ep[q][h - pdy[q] * PRX - pdx[q]], gs);
+            const size_t i = (size_t)z * NN + (size_t)y * N + x;
+            g[i] = fmaf(a.two_lambda, gs, g[i]);
+            hacc += 2.0 * (double)hs;
         }
+        __syncthreads();
     }
-    hacc += (double)hblk;
     const double tot = block_sum_f64(hacc, red);
-    if (threadIdx.x == 0) partials[blockIdx.x] = tot;
+    if (threadIdx.x == 0) partials[blockIdx.y * gridDim.x + blockIdx.x] = tot;
 }
 
 __global__ void k_reduce_finalize(const double *__restrict__ partials, int n,
@@ -213,10 +274,12 @@ int launch_prior_grad(tc_plan *p, const float *x, float *g, int nb,
     a.w1 = (float)(1.0 / z);
     a.w2 = (float)(1.0 / (sqrt(2.0) * z));
     a.w3 = (float)(1.0 / (sqrt(3.0) * z));
-    const int blocks = TC_RED_BLOCKS;
+    dim3 grid((a.N + PTX - 1) / PTX, (a.N + PTY - 1) / PTY);
+    const int blocks = grid.x * grid.y;
+    if (blocks > p->slot) return TC_ERR_UNSUPPORTED;
     double *part = p->partials + (size_t)1 * p->slot;
     TC_PROFILED(TCK_PRIOR, s,
-                k_prior<<<blocks, TC_RED_THREADS, 0, s>>>(x, g, part, a));
+                k_prior<<<grid, PRIOR_THREADS, 0, s>>>(x, g, part, a));
     TC_LAUNCHED("k_prior");
     if (h_acc) return launch_reduce_finalize(part, blocks, h_acc, 0, pr->lambda, s);
     return TC_OK;

@@ -18,6 +18,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "fft.cuh"
 
 int radon_configure_kernels(tc_plan *p);
 
@@ -155,6 +156,7 @@ int tc_plan_build(const tc_geom *geom, int max_batch, tc_plan **out) {
     const double h = 0.5 * w;
     const double beta = 2.30 * w;  // ES shape parameter for sigma = 2 (Barnett et al. 2019)
     k.beta = (float)beta;
+    k.beta_l2 = (float)(beta / std::log(2.0));
     k.inv_h = (float)(1.0 / h);
     k.invD = (float)(1.0 / D);
     if (!factor_radices(D, k.rp)) {
@@ -316,9 +318,10 @@ int tc_plan_build(const tc_geom *geom, int max_batch, tc_plan **out) {
     p->threads_col = std::max(64, 2 * cp * N / 16);
     p->threads_row = std::max(128, N / 8);
     p->threads_det = 256;
-    p->smem_col = (size_t)cp * 2 * N * sizeof(float2);
-    p->smem_row_fwd = (size_t)2 * N * sizeof(float2);
-    p->smem_row_adj = p->smem_row_fwd + (size_t)2 * (kmax - kmin + 1) * sizeof(int);
+    p->smem_col = (size_t)spad_size(cp * 2 * N) * sizeof(float2);
+    p->smem_row_fwd = (size_t)spad_size(2 * N) * sizeof(float2);
+    p->smem_row_adj = p->smem_row_fwd + (size_t)SPREAD_CHUNK * (sizeof(float2) + sizeof(float)) +
+                      (size_t)2 * (kmax - kmin + 1) * sizeof(short);
     p->smem_det = (size_t)(3 * D + k.rp.rad[0]) * sizeof(float2);
     if (p->threads_col > 1024 || p->threads_row > 1024 || p->smem_det > 200 * 1024 ||
         p->smem_row_adj > 200 * 1024) {
@@ -328,7 +331,8 @@ int tc_plan_build(const tc_geom *geom, int max_batch, tc_plan **out) {
 
     // scratch
     const size_t MB = (size_t)max_batch;
-    p->slot = std::max(TC_RED_BLOCKS, (int)(((A + 1) / 2) * MB));
+    p->slot = std::max(std::max(TC_RED_BLOCKS, (int)(((A + 1) / 2) * MB)),
+                       ((N + 31) / 32) * ((N + 11) / 12));  // prior tiles (32 x 12)
     if ((rc = alloc_dev((void **)&p->tu, MB * R * N * sizeof(float2), bytes)) ||
         (rc = alloc_dev((void **)&p->pv, MB * w * (size_t)k.AM * sizeof(float2), bytes)) ||
         (rc = alloc_dev((void **)&p->sr, MB * (size_t)A * D * sizeof(float), bytes)) ||

@@ -26,9 +26,10 @@
 
 namespace {
 
-__device__ __forceinline__ float2 grid_cell(const float2 *eo, int N, int c) {
-    // cell c of a G-row stored as [even cells | odd cells]
-    return eo[(c & 1) * N + (c >> 1)];
+// Padded shared-memory slot of cell c of a G-row stored as [even | odd] halves
+// starting at element `base`.
+__device__ __forceinline__ int cell_slot(int base, int N, int c) {
+    return spad(base + (c & 1) * N + (c >> 1));
 }
 
 // ------------------------------------------------------------ forward ------
@@ -45,8 +46,8 @@ __global__ void __launch_bounds__(512) k_fwd_col(const float *__restrict__ x, fl
         const float dy = g.dea[iy];
         const float2 z = make_float2(f.x * g.dea[xc] * dy, f.y * g.dea[xc + 1] * dy);
         const int q = (iy - N / 2) & (N - 1);
-        sm[(pp * 2) * N + q] = z;
-        sm[(pp * 2 + 1) * N + q] = cmul(z, g.twG[iy]);
+        sm[spad((pp * 2) * N + q)] = z;
+        sm[spad((pp * 2 + 1) * N + q)] = cmul(z, g.twG[iy]);
     }
     __syncthreads();
     fft_pow2<-1>(sm, N, g.log2N, 2 * CP, g.twN);
@@ -55,9 +56,8 @@ __global__ void __launch_bounds__(512) k_fwd_col(const float *__restrict__ x, fl
     for (int idx = threadIdx.x; idx < g.R * CP; idx += blockDim.x) {
         const int pp = idx % CP, r = idx / CP;
         const int jy = g.jmin + r;
-        const float2 *eo = sm + pp * 2 * N;
-        const float2 zp = grid_cell(eo, N, jy & Gm);
-        const float2 zm = cconj(grid_cell(eo, N, (-jy) & Gm));
+        const float2 zp = sm[cell_slot(pp * 2 * N, N, jy & Gm)];
+        const float2 zm = cconj(sm[cell_slot(pp * 2 * N, N, (-jy) & Gm)]);
         const float2 d = csub(zp, zm);
         float4 o;
         o.x = 0.5f * (zp.x + zm.x);
@@ -76,8 +76,8 @@ __global__ void __launch_bounds__(512) k_fwd_row(const float2 *__restrict__ T, f
     for (int ix = threadIdx.x; ix < N; ix += blockDim.x) {
         const float2 v = Tr[ix];
         const int q = (ix - N / 2) & (N - 1);
-        sm[q] = v;
-        sm[N + q] = cmul(v, g.twG[ix]);
+        sm[spad(q)] = v;
+        sm[spad(N + q)] = cmul(v, g.twG[ix]);
     }
     __syncthreads();
     fft_pow2<-1>(sm, N, g.log2N, 2, g.twN);
@@ -89,8 +89,8 @@ __global__ void __launch_bounds__(512) k_fwd_row(const float2 *__restrict__ T, f
         const float ex = g.ent_ex[e];
         float2 acc = make_float2(0.f, 0.f);
         for (int t = 0; t < g.w; ++t) {
-            const float wt = es_kernel(((float)t - ex) * g.inv_h, g.beta);
-            cfma(acc, wt, grid_cell(sm, N, (key + t) & Gm));
+            const float wt = es_kernel_fast(((float)t - ex) * g.inv_h, g.beta_l2);
+            cfma(acc, wt, sm[cell_slot(0, N, (key + t) & Gm)]);
         }
         const float wy = g.ent_wy[e];
         Pb[(size_t)g.ent_s[e] * g.AM + g.ent_p[e]] = cscale(acc, wy);
@@ -190,51 +190,89 @@ __global__ void __launch_bounds__(256) k_adj_det(const float *__restrict__ ysino
     }
 }
 
+// Spreading of one grid row, atomic-free.  The row's (point, tap) entries are
+// sorted by jx0 (the key), so entries with one key form a run.  Entries are
+// taken in chunks: every thread stages one entry's u = phi_y * V[p] and
+// gx - jx0 in shared memory and the run table of the chunk is built.  Then,
+// in w phases by (key - kmin) mod w, one thread per (key, tap t) sums
+// u * phi(t - (gx - jx0)) over the key's run and adds it to cell key + t:
+// keys of one phase are at least w apart, so no two threads touch the same
+// cell.  Keys whose window could wrap (mod G) onto a low key's window are
+// added last by one thread.  Every cell's summation order is fixed, so the
+// result is bit-reproducible.
 __global__ void __launch_bounds__(512) k_adj_row(const float2 *__restrict__ V, float2 *__restrict__ U,
                           const KArgs g) {
-    extern __shared__ float2 sm[];  // [2][N] grid row, then run tables
-    const int N = g.N, G = g.G, r = blockIdx.x, b = blockIdx.y;
+    extern __shared__ float2 sm[];
+    const int N = g.N, G = g.G, w = g.w, r = blockIdx.x, b = blockIdx.y;
     const int nkeys = g.kmax - g.kmin + 1;
-    int *rstart = reinterpret_cast<int *>(sm + 2 * N);
-    int *rlen = rstart + nkeys;
+    const int hsz = spad_size(2 * N);
+    float2 *cu = sm + hsz;                                     // [SPREAD_CHUNK]
+    float *cex = reinterpret_cast<float *>(cu + SPREAD_CHUNK);   // [SPREAD_CHUNK]
+    short *rstart = reinterpret_cast<short *>(cex + SPREAD_CHUNK);  // [nkeys]
+    short *rlen = rstart + nkeys;                              // [nkeys]
     const int e0 = g.row_off[r], e1 = g.row_off[r + 1];
-    for (int k = threadIdx.x; k < nkeys; k += blockDim.x) rlen[k] = 0;
-    __syncthreads();
-    for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-        const int key = g.ent_key[e];
-        if (e == e0 || g.ent_key[e - 1] != key) rstart[key - g.kmin] = e;
-    }
-    __syncthreads();
-    for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-        const int key = g.ent_key[e];
-        if (e == e1 - 1 || g.ent_key[e + 1] != key) rlen[key - g.kmin] = e + 1 - rstart[key - g.kmin];
-    }
-    __syncthreads();
+    for (int c = threadIdx.x; c < hsz; c += blockDim.x) sm[c] = make_float2(0.f, 0.f);
     const float2 *Vb = V + (size_t)b * g.w * g.AM;
-    for (int c = threadIdx.x; c < G; c += blockDim.x) {
-        float2 acc = make_float2(0.f, 0.f);
-        for (int t = 0; t < g.w; ++t) {
-            for (int rep = 0; rep < 2; ++rep) {
-                const int k = c - t - rep * G;
-                if (k < g.kmin || k > g.kmax) continue;
-                const int ki = k - g.kmin;
+    const int nlow = nkeys < G - w + 1 ? nkeys : G - w + 1;
+    for (int c0 = e0; c0 < e1; c0 += SPREAD_CHUNK) {
+        const int n = (e1 - c0) < SPREAD_CHUNK ? (e1 - c0) : SPREAD_CHUNK;
+        for (int k = threadIdx.x; k < nkeys; k += blockDim.x) rlen[k] = 0;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            const int e = c0 + i;
+            cu[i] = cscale(Vb[g.ent_p[e]], g.ent_wy[e]);
+            cex[i] = g.ent_ex[e];
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            const int key = g.ent_key[c0 + i];
+            if (i == 0 || g.ent_key[c0 + i - 1] != key) rstart[key - g.kmin] = (short)i;
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            const int key = g.ent_key[c0 + i];
+            if (i == n - 1 || g.ent_key[c0 + i + 1] != key)
+                rlen[key - g.kmin] = (short)(i + 1 - rstart[key - g.kmin]);
+        }
+        __syncthreads();
+        for (int ph = 0; ph < w; ++ph) {
+            const int nk = (nlow - ph + w - 1) / w;
+            for (int item = threadIdx.x; item < nk * w; item += blockDim.x) {
+                const int j = item / w, t = item - j * w;
+                const int ki = ph + j * w;
                 const int len = rlen[ki];
                 if (len == 0) continue;
                 const int st = rstart[ki];
-                for (int e = st; e < st + len; ++e) {
-                    const float wt = g.ent_wy[e] * es_kernel(((float)t - g.ent_ex[e]) * g.inv_h, g.beta);
-                    cfma(acc, wt, Vb[g.ent_p[e]]);
+                float2 acc = make_float2(0.f, 0.f);
+                for (int e = st; e < st + len; ++e)
+                    cfma(acc, es_kernel_fast(((float)t - cex[e]) * g.inv_h, g.beta_l2), cu[e]);
+                const int c = (g.kmin + ki + t) & (G - 1);
+                float2 &hc = sm[cell_slot(0, N, c)];
+                hc = cadd(hc, acc);
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            for (int ki = nlow; ki < nkeys; ++ki) {
+                const int len = rlen[ki];
+                if (len == 0) continue;
+                const int st = rstart[ki];
+                for (int t = 0; t < w; ++t) {
+                    float2 acc = make_float2(0.f, 0.f);
+                    for (int e = st; e < st + len; ++e)
+                        cfma(acc, es_kernel_fast(((float)t - cex[e]) * g.inv_h, g.beta_l2), cu[e]);
+                    const int c = (g.kmin + ki + t) & (G - 1);
+                    float2 &hc = sm[cell_slot(0, N, c)];
+                    hc = cadd(hc, acc);
                 }
             }
         }
-        sm[(c & 1) * N + (c >> 1)] = acc;
+        __syncthreads();
     }
-    __syncthreads();
     fft_pow2<+1>(sm, N, g.log2N, 2, g.twN);
     float2 *Ur = U + ((size_t)b * g.R + r) * N;
     for (int ix = threadIdx.x; ix < N; ix += blockDim.x) {
         const int q = (ix - N / 2) & (N - 1);
-        Ur[ix] = cadd(sm[q], cmul(sm[N + q], cconj(g.twG[ix])));
+        Ur[ix] = cadd(sm[spad(q)], cmul(sm[spad(N + q)], cconj(g.twG[ix])));
     }
 }
 
@@ -258,7 +296,7 @@ __global__ void __launch_bounds__(512) k_adj_col(const float2 *__restrict__ U, f
         // Hermitian parts of the two columns, packed as H0 + i H1
         const float h0x = 0.5f * (up.x + un.x), h0y = 0.5f * (up.y - un.y);
         const float h1x = 0.5f * (up.z + un.z), h1y = 0.5f * (up.w - un.w);
-        sm[(pp * 2 + (jy & 1)) * N + (jy >> 1)] = make_float2(h0x - h1y, h0y + h1x);
+        sm[cell_slot(pp * 2 * N, N, jy)] = make_float2(h0x - h1y, h0y + h1x);
     }
     __syncthreads();
     fft_pow2<+1>(sm, N, g.log2N, 2 * CP, g.twN);
@@ -267,8 +305,8 @@ __global__ void __launch_bounds__(512) k_adj_col(const float2 *__restrict__ U, f
         const int pp = idx % CP, iy = idx / CP;
         const int xc = x0base + 2 * pp;
         const int q = (iy - N / 2) & (N - 1);
-        const float2 *eo = sm + pp * 2 * N;
-        const float2 v = cadd(eo[q], cmul(eo[N + q], cconj(g.twG[iy])));
+        const float2 v = cadd(sm[spad(pp * 2 * N + q)],
+                              cmul(sm[spad(pp * 2 * N + N + q)], cconj(g.twG[iy])));
         const float dy = g.dea[iy];
         *reinterpret_cast<float2 *>(xb + (size_t)iy * N + xc) =
             make_float2(v.x * g.dea[xc] * dy, v.y * g.dea[xc + 1] * dy);
