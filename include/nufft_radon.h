@@ -198,6 +198,33 @@ const char *tc_profile_kernel_name(int id);
 /* Kernel launches issued by this library since it was loaded (host counter). */
 long long tc_launch_count(void);
 
+/* ------------------------------------------------------ no allocation --- */
+/* Prior gradient and value without any device allocation.  There is no
+ * counterpart of this entry point in the paper; it exists for callers that
+ * cannot call cudaMalloc -- for example code running under a framework whose
+ * caching allocator owns the device memory budget, or a latency-critical loop
+ * that must not risk the implicit device synchronisation of an allocation --
+ * and who therefore cannot create a plan.
+ *
+ * Computes the qGGMRF prior of the tc_prior block (same definition and kernel
+ * as the prior inside mbir_grad):
+ *   grad += lambda * grad H(x)       (accumulated into the caller's grad)
+ *   *h_out = lambda * H(x)           (h_out: DEVICE pointer to one double, or NULL)
+ *   x, grad  DEVICE float32 [batch][n][n], 16-byte aligned, caller-owned
+ *   1 <= n <= 4096, batch >= 1; anything larger returns TC_ERR_INVALID_ARG.
+ * Scratch: the per-block FP64 partial sums live in a fixed array of 65536
+ * doubles (512 KiB) declared at file scope in the library's device code; every
+ * GPU that loads the library holds it until the process exits.  The first call
+ * on a device looks up that array's device address (cudaGetSymbolAddress, with
+ * the device current) and caches it, so make the first call on each device
+ * before any stream capture.  All calls share the array and each call
+ * overwrites the part it uses (nothing has to start at zero), so calls that
+ * overlap on the GPU (concurrent streams) race and must be serialised.
+ * Asynchronous on `stream`; calls no cudaMalloc, cudaFree or allocating
+ * library routine. */
+int tc_prior_grad_noalloc(const float *x, float *grad, int n, int batch,
+                          const tc_prior *prior, double *h_out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

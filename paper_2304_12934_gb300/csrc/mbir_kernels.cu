@@ -358,3 +358,33 @@ int launch_fill_scalars_fresh(tc_plan *p, double t, double k, double restarts,
     TC_LAUNCHED("k_fill_scalars");
     return TC_OK;
 }
+
+// Prior gradient and value with caller-supplied partial-sum storage (used by
+// the no-allocation entry point in prior_noalloc.cu): g += 2 lambda sum w rho',
+// *h_out = lambda H.  Same kernel and reduction as launch_prior_grad.
+int launch_prior_kernel_into(const float *x, float *g, int n, int nb, const tc_prior *pr,
+                             double *partials, int max_partials, double *h_out,
+                             cudaStream_t s) {
+    PriorArgs a;
+    a.N = n;
+    a.B = nb;
+    a.dims = pr->dims;
+    a.p = (float)pr->p;
+    a.inv_sigma = (float)(1.0 / pr->sigma);
+    a.c = (float)pr->c;
+    a.qexp = (float)(2.0 - pr->p);
+    a.two_lambda = (float)(2.0 * pr->lambda);
+    double z;
+    if (pr->dims == 3) z = 6.0 + 12.0 / sqrt(2.0) + 8.0 / sqrt(3.0);
+    else z = 4.0 + 4.0 / sqrt(2.0);
+    a.w1 = (float)(1.0 / z);
+    a.w2 = (float)(1.0 / (sqrt(2.0) * z));
+    a.w3 = (float)(1.0 / (sqrt(3.0) * z));
+    dim3 grid((n + PTX - 1) / PTX, (n + PTY - 1) / PTY);
+    const int blocks = grid.x * grid.y;
+    if (blocks > max_partials) return TC_ERR_INVALID_ARG;
+    TC_PROFILED(TCK_PRIOR, s, k_prior<<<grid, PRIOR_THREADS, 0, s>>>(x, g, partials, a));
+    TC_LAUNCHED("k_prior");
+    if (h_out) return launch_reduce_finalize(partials, blocks, h_out, 0, pr->lambda, s);
+    return TC_OK;
+}

@@ -1,0 +1,66 @@
+"""The allocation-free prior entry point, tc_prior_grad_noalloc.
+
+It serves callers that cannot call cudaMalloc (a framework whose caching
+allocator owns the device memory, or a loop that must not risk an
+allocation's implicit device synchronisation) and so cannot create a plan.
+Its scratch is a fixed device array inside the library, shared by all calls.
+This test calls it through the C ABI twice in a row, on different inputs, and
+compares each result with the plan-based mbir_grad (zero data weights leave
+only the prior), within the tolerance of the other prior tests.  The file
+name makes pytest collect it last.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def api():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2304_12934_gb300 import api as a
+    L = a.load()
+    L.tc_prior_grad_noalloc.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                        ctypes.c_int, ctypes.POINTER(a._Prior),
+                                        ctypes.c_void_p, ctypes.c_void_p]
+    L.tc_prior_grad_noalloc.restype = ctypes.c_int
+    return a
+
+
+@pytest.mark.parametrize("dims", [3, 2])
+def test_noalloc_prior_matches_plan_path_on_two_calls(api, dims):
+    L = api.load()
+    N, A, D, B = 128, 30, 184, 3
+    prior = api.Prior(lam=0.5, dims=dims)
+    stream = torch.cuda.current_stream()
+    with api.Plan(N, A, D, max_batch=2) as plan:
+        b = torch.zeros((B, A, D), device="cuda:0")
+        wzero = torch.zeros((B, A, D), device="cuda:0")
+        for call in range(2):
+            rng = np.random.default_rng(100 + call)
+            x = torch.tensor(rng.uniform(0, 1, (B, N, N)), dtype=torch.float32, device="cuda:0")
+            g_ref, obj = api.mbir_grad(plan, x, b, wzero, prior)
+            g = torch.zeros_like(x)
+            h = torch.full((1,), -1.0, dtype=torch.float64, device="cuda:0")
+            pc = prior._c()
+            rc = L.tc_prior_grad_noalloc(x.data_ptr(), g.data_ptr(), N, B, ctypes.byref(pc),
+                                         h.data_ptr(), ctypes.c_void_p(stream.cuda_stream))
+            torch.cuda.synchronize()
+            assert rc == 0
+            assert float((g - g_ref).norm() / g_ref.norm()) <= TOL
+            href = float(obj[1])
+            assert abs(float(h[0]) - href) <= TOL * abs(href)
+
+
+def test_noalloc_rejects_sizes_beyond_its_scratch(api):
+    L = api.load()
+    pc = api.Prior(dims=3)._c()
+    x = torch.zeros((1, 16, 16), device="cuda:0")
+    rc = L.tc_prior_grad_noalloc(x.data_ptr(), x.data_ptr(), 8192, 1, ctypes.byref(pc), None, None)
+    assert rc == -1
