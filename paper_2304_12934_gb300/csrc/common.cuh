@@ -35,13 +35,15 @@ struct KArgs {
     const float2 *twG;         // [N] exp(-2 pi i (k - N/2) / G)
     const float2 *twD;         // [D] exp(-2 pi i k / D)
     const int *row_off;        // [R + 1] first entry of each grid row
-    const int *ent_p;          // [E] polar point index a * Mh + m
-    const short *ent_key;      // [E] jx0 of the point (sort key within the row)
-    const unsigned char *ent_s;// [E] tap index of this row in the point's y footprint
-    const float *ent_ex;       // [E] gx - jx0
-    const float *ent_wy;       // [E] phi((s - (gy - jy0)) / (w/2))
+    const int4 *ent;           // [E] packed Entry records (see entry_* accessors)
     const unsigned char *angle_flip; // [A] 1: theta was in [pi, 2 pi), data conjugated
     RadixPlan rp;              // factorisation of D
+    // Bluestein (chirp-z) detector DFT, used when D has a large prime factor:
+    // length-L power-of-two FFTs, L >= 2D - 1
+    int blue, L, log2L;
+    const float2 *chirp;       // [D] exp(-i pi (n^2 mod 2D) / D)
+    const float2 *bhat;        // [L] FFT_L of the conjugate chirp (wrapped), times 1/L
+    const float2 *twL;         // [L] exp(-2 pi i k / L)
 };
 
 struct tc_plan {
@@ -52,11 +54,9 @@ struct tc_plan {
     float *dea;
     float2 *twN, *twG, *twD;
     int *row_off;
-    int *ent_p;
-    short *ent_key;
-    unsigned char *ent_s;
-    float *ent_ex, *ent_wy;
+    int4 *ent;
     unsigned char *angle_flip;
+    float2 *chirp, *bhat, *twL;
     long long n_entries;
     // scratch for max_batch slices
     float2 *tu;           // [MB][R][N]   column-pass output (fwd) / row-pass output (adj)
@@ -71,6 +71,19 @@ struct tc_plan {
     int threads_col, threads_row, threads_det;
     size_t smem_col, smem_row_fwd, smem_row_adj, smem_det;
 };
+
+// One (polar point, tap row) entry of a grid row's bin, 16 bytes:
+//   x: polar point index p = a * Mh + m
+//   y: gx - jx0 (float bits)
+//   z: phi_y, the point's kernel weight for this row (float bits)
+//   w: jx0 (low 16 bits, signed) | tap row s << 16
+__host__ __device__ __forceinline__ int entry_p(int4 e) { return e.x; }
+__host__ __device__ __forceinline__ int entry_key(int4 e) { return (int)(short)(e.w & 0xffff); }
+__host__ __device__ __forceinline__ int entry_s(int4 e) { return (e.w >> 16) & 0xff; }
+#ifdef __CUDACC__
+__device__ __forceinline__ float entry_ex(int4 e) { return __int_as_float(e.y); }
+__device__ __forceinline__ float entry_wy(int4 e) { return __int_as_float(e.z); }
+#endif
 
 // ------------------------------------------------------------- complex ops --
 __host__ __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
@@ -101,7 +114,7 @@ __device__ __forceinline__ float es_kernel_fast(float z, float beta_l2) {
 }
 
 // Entries of one grid row staged per chunk by the spreading kernel.
-#define SPREAD_CHUNK 2048
+#define SPREAD_CHUNK 1024
 
 // Block-wide FP64 sum of one float per thread; thread 0 gets the total.
 __device__ __forceinline__ double block_sum_f64(double d, double *red) {

@@ -130,9 +130,14 @@ __device__ __forceinline__ void stockham_stage(float2 *s, int log2n, int cnt, in
             const int tr = it >> logper, j = it & (per - 1), k = j & (Ns - 1);
             const int base = (tr << log2n) + j;
             v[i][0] = s[spad(base)];
+            if (logNs == 0) {  // first stage: every twiddle is 1
 #pragma unroll
-            for (int q = 1; q < R; ++q)
-                v[i][q] = cmul(s[spad(base + q * per)], tw_get<SIGN>(tw, (q * k) << twshift));
+                for (int q = 1; q < R; ++q) v[i][q] = s[spad(base + q * per)];
+            } else {
+#pragma unroll
+                for (int q = 1; q < R; ++q)
+                    v[i][q] = cmul(s[spad(base + q * per)], tw_get<SIGN>(tw, (q * k) << twshift));
+            }
         }
     }
     __syncthreads();
@@ -218,4 +223,35 @@ __device__ float2 *fft_mixed(float2 *a, float2 *b, const RadixPlan &rp,
         Ns *= R;
     }
     return a;
+}
+
+// Bluestein's chirp-z DFT of length D through two length-L power-of-two FFTs:
+// nk = (n^2 + k^2 - (k - n)^2) / 2 turns the DFT into a convolution with the
+// chirp, evaluated cyclically with L >= 2D - 1.  On entry s[spad(n)], n < D,
+// holds the input; on exit s[spad(k)], k < D, holds sum_n x_n exp(SIGN 2 pi i
+// nk / D).  The +1 direction is conj(DFT_-(conj x)).  Requires blockDim.x >=
+// L / 16; s has spad_size(L) elements.
+template <int SIGN>
+__device__ void bluestein(float2 *s, int D, int L, int log2L, const float2 *__restrict__ chirp,
+                          const float2 *__restrict__ bhat, const float2 *__restrict__ twL) {
+    for (int n = threadIdx.x; n < L; n += blockDim.x) {
+        float2 a = make_float2(0.f, 0.f);
+        if (n < D) {
+            float2 v = s[spad(n)];
+            if (SIGN > 0) v.y = -v.y;
+            a = cmul(v, chirp[n]);
+        }
+        s[spad(n)] = a;
+    }
+    __syncthreads();
+    fft_pow2<-1>(s, L, log2L, 1, twL);
+    for (int n = threadIdx.x; n < L; n += blockDim.x) s[spad(n)] = cmul(s[spad(n)], bhat[n]);
+    __syncthreads();
+    fft_pow2<+1>(s, L, log2L, 1, twL);
+    for (int k = threadIdx.x; k < D; k += blockDim.x) {
+        float2 v = cmul(s[spad(k)], chirp[k]);
+        if (SIGN > 0) v.y = -v.y;
+        s[spad(k)] = v;
+    }
+    __syncthreads();
 }

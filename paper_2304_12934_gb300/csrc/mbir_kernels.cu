@@ -78,13 +78,21 @@ __global__ void __launch_bounds__(PRIOR_THREADS) k_prior(const float *__restrict
         }
         fpl[0][h] = inb ? f[(size_t)y * N + x] : 0.f;
     }
+    // register prefetch: the plane the next step stores (3D: z + 2, 2D: z + 1)
+    const size_t off = (size_t)y * N + x;
+    float f_nx = (inb && B > 1) ? f[NN + off] : 0.f;
     double hacc = 0.0;
     for (int z = 0; z < B; ++z) {
         const int cur = z & 1, nxt = cur ^ 1;
         const bool up = three && z + 1 < B;
-        if (ring && up) fpl[nxt][h] = inb ? f[(size_t)(z + 1) * NN + (size_t)y * N + x] : 0.f;
-        // 2D: slices are independent, each step loads its own plane
-        if (ring && !three && z > 0) fpl[cur][h] = inb ? f[(size_t)z * NN + (size_t)y * N + x] : 0.f;
+        const int pz = three ? z + 2 : z + 1;
+        const float f_pf = (inb && pz < B) ? f[(size_t)pz * NN + off] : 0.f;
+        const size_t i = (size_t)z * NN + off;
+        const float g_old = interior ? g[i] : 0.f;
+        if (ring) {
+            if (up) fpl[nxt][h] = f_nx;                 // 3D: plane z + 1
+            else if (!three && z > 0) fpl[cur][h] = f_nx;  // 2D: slices are independent
+        }
         __syncthreads();
         float hs = 0.f;
         if (ring) {
@@ -127,11 +135,11 @@ __global__ void __launch_bounds__(PRIOR_THREADS) k_prior(const float *__restrict
 #pragma unroll
             for (int q = 0; q < 4; ++q)
                 gs = fmaf(pw[q], Ep[q][h] - Ep[q][h - pdy[q] * PRX - pdx[q]], gs);
-            const size_t i = (size_t)z * NN + (size_t)y * N + x;
-            g[i] = fmaf(a.two_lambda, gs, g[i]);
+            g[i] = fmaf(a.two_lambda, gs, g_old);
             hacc += 2.0 * (double)hs;
         }
         __syncthreads();
+        f_nx = f_pf;
     }
     const double tot = block_sum_f64(hacc, red);
     if (threadIdx.x == 0) partials[blockIdx.y * gridDim.x + blockIdx.x] = tot;

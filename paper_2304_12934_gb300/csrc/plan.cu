@@ -97,6 +97,44 @@ bool factor_radices(int n, RadixPlan &rp) {
     return true;
 }
 
+// In-place FP64 radix-2 FFT (sign -1) of a power-of-two length, host side.
+void fft64(std::vector<double> &re, std::vector<double> &im) {
+    const size_t n = re.size();
+    for (size_t i = 1, j = 0; i < n; ++i) {
+        size_t bit = n >> 1;
+        for (; j & bit; bit >>= 1) j ^= bit;
+        j ^= bit;
+        if (i < j) {
+            std::swap(re[i], re[j]);
+            std::swap(im[i], im[j]);
+        }
+    }
+    for (size_t len = 2; len <= n; len <<= 1) {
+        const double ang = -2.0 * kPi / (double)len;
+        for (size_t i = 0; i < n; i += len)
+            for (size_t k = 0; k < len / 2; ++k) {
+                const double wr = std::cos(ang * k), wi = std::sin(ang * k);
+                const size_t u = i + k, v = i + k + len / 2;
+                const double xr = re[v] * wr - im[v] * wi, xi = re[v] * wi + im[v] * wr;
+                re[v] = re[u] - xr;
+                im[v] = im[u] - xi;
+                re[u] += xr;
+                im[u] += xi;
+            }
+    }
+}
+
+// Largest prime factor of n.
+int largest_prime(int n) {
+    int lp = 1;
+    for (int q = 2; (long long)q * q <= n; ++q)
+        while (n % q == 0) {
+            lp = q;
+            n /= q;
+        }
+    return n > 1 ? std::max(lp, n) : lp;
+}
+
 struct Entry {
     int key, p, s;
     float ex, wy;
@@ -129,9 +167,9 @@ int alloc_dev(void **dst, size_t nb, long long &bytes) {
 
 void tc_plan_free(tc_plan *p) {
     if (!p) return;
-    void *ptrs[] = {p->dea64, p->dea, p->twN, p->twG, p->twD, p->row_off, p->ent_p,
-                    p->ent_key, p->ent_s, p->ent_ex, p->ent_wy, p->tu, p->pv,
-                    p->sr, p->partials, p->scal, p->angle_flip};
+    void *ptrs[] = {p->dea64, p->dea, p->twN, p->twG, p->twD, p->row_off, p->ent,
+                    p->tu, p->pv, p->sr, p->partials, p->scal, p->angle_flip,
+                    p->chirp, p->bhat, p->twL};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     delete p;
@@ -253,18 +291,53 @@ int tc_plan_build(const tc_geom *geom, int max_batch, tc_plan **out) {
         std::sort(ents.begin() + cnt[r], ents.begin() + cnt[r + 1],
                   [](const Entry &u, const Entry &v) { return u.key != v.key ? u.key < v.key : u.p < v.p; });
     const size_t E = ents.size();
-    std::vector<int> ep(E);
-    std::vector<short> ek(E);
-    std::vector<unsigned char> es(E);
-    std::vector<float> eex(E), ewy(E);
+    std::vector<int4> epk(E);
     for (size_t i = 0; i < E; ++i) {
-        ep[i] = ents[i].p;
-        ek[i] = (short)ents[i].key;
-        es[i] = (unsigned char)ents[i].s;
-        eex[i] = ents[i].ex;
-        ewy[i] = ents[i].wy;
+        int4 v;
+        v.x = ents[i].p;
+        std::memcpy(&v.y, &ents[i].ex, 4);
+        std::memcpy(&v.z, &ents[i].wy, 4);
+        v.w = (int)((unsigned)(unsigned short)(short)ents[i].key | ((unsigned)ents[i].s << 16));
+        epk[i] = v;
     }
     p->n_entries = (long long)E;
+
+    // Bluestein tables when D has a large prime factor (and L stays <= 8192)
+    std::vector<float2> chirp, bhat, twL;
+    {
+        int L = 1, lg = 0;
+        while (L < 2 * D - 1) {
+            L <<= 1;
+            ++lg;
+        }
+        k.blue = (largest_prime(D) > 32 && L <= 8192) ? 1 : 0;
+        k.L = L;
+        k.log2L = lg;
+        if (k.blue) {
+            chirp.resize(D);
+            std::vector<double> br(L, 0.0), bi(L, 0.0);
+            for (int n = 0; n < D; ++n) {
+                const long long q = ((long long)n * n) % (2LL * D);
+                const double a = -kPi * (double)q / (double)D;
+                chirp[n] = make_float2((float)std::cos(a), (float)std::sin(a));
+                // b_m = conj(chirp_|m|) at m and L - m
+                br[n] = std::cos(a);
+                bi[n] = -std::sin(a);
+                if (n > 0) {
+                    br[L - n] = std::cos(a);
+                    bi[L - n] = -std::sin(a);
+                }
+            }
+            fft64(br, bi);
+            bhat.resize(L);
+            for (int i = 0; i < L; ++i) bhat[i] = make_float2((float)(br[i] / L), (float)(bi[i] / L));
+            twL.resize(L);
+            for (int i = 0; i < L; ++i) {
+                const double a = -2.0 * kPi * i / L;
+                twL[i] = make_float2((float)std::cos(a), (float)std::sin(a));
+            }
+        }
+    }
 
     // twiddles
     std::vector<float2> twN(N), twG(N), twD(D);
@@ -292,24 +365,22 @@ int tc_plan_build(const tc_geom *geom, int max_batch, tc_plan **out) {
     UP(p->twG, twG);
     UP(p->twD, twD);
     UP(p->row_off, cnt);
-    UP(p->ent_p, ep);
-    UP(p->ent_key, ek);
-    UP(p->ent_s, es);
-    UP(p->ent_ex, eex);
-    UP(p->ent_wy, ewy);
+    UP(p->ent, epk);
     UP(p->angle_flip, flip);
+    UP(p->chirp, chirp);
+    UP(p->bhat, bhat);
+    UP(p->twL, twL);
 #undef UP
     k.dea = p->dea;
     k.twN = p->twN;
     k.twG = p->twG;
     k.twD = p->twD;
     k.row_off = p->row_off;
-    k.ent_p = p->ent_p;
-    k.ent_key = p->ent_key;
-    k.ent_s = p->ent_s;
-    k.ent_ex = p->ent_ex;
-    k.ent_wy = p->ent_wy;
+    k.ent = p->ent;
     k.angle_flip = p->angle_flip;
+    k.chirp = p->chirp;
+    k.bhat = p->bhat;
+    k.twL = p->twL;
 
     // launch configuration
     int cp = 4;
@@ -317,12 +388,13 @@ int tc_plan_build(const tc_geom *geom, int max_batch, tc_plan **out) {
     p->cp_col = cp;
     p->threads_col = std::max(64, 2 * cp * N / 16);
     p->threads_row = std::max(128, N / 8);
-    p->threads_det = 256;
-    p->smem_col = (size_t)spad_size(cp * 2 * N) * sizeof(float2);
-    p->smem_row_fwd = (size_t)spad_size(2 * N) * sizeof(float2);
+    p->threads_det = k.blue ? std::max(256, k.L / 16) : 256;
+    p->smem_col = (size_t)(spad_size(cp * 2 * N) + N) * sizeof(float2);
+    p->smem_row_fwd = (size_t)(spad_size(2 * N) + N) * sizeof(float2);
     p->smem_row_adj = p->smem_row_fwd + (size_t)SPREAD_CHUNK * (sizeof(float2) + sizeof(float)) +
-                      (size_t)2 * (kmax - kmin + 1) * sizeof(short);
-    p->smem_det = (size_t)(3 * D + k.rp.rad[0]) * sizeof(float2);
+                      (size_t)(2 * SPREAD_CHUNK + 2) * sizeof(short);
+    p->smem_det = k.blue ? (size_t)spad_size(k.L) * sizeof(float2)
+                         : (size_t)(3 * D + k.rp.rad[0]) * sizeof(float2);
     if (p->threads_col > 1024 || p->threads_row > 1024 || p->smem_det > 200 * 1024 ||
         p->smem_row_adj > 200 * 1024) {
         tc_plan_free(p);

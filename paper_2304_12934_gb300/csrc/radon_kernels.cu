@@ -35,10 +35,12 @@ __device__ __forceinline__ int cell_slot(int base, int N, int c) {
 // ------------------------------------------------------------ forward ------
 __global__ void __launch_bounds__(512) k_fwd_col(const float *__restrict__ x, float2 *__restrict__ T,
                           const KArgs g, int CP) {
-    extern __shared__ float2 sm[];  // [CP][2][N]
+    extern __shared__ float2 sm[];  // [CP][2][N] padded, then [N] twiddles
     const int N = g.N, b = blockIdx.y;
     const int x0base = blockIdx.x * CP * 2;
     const float *xs = x + (size_t)b * N * N;
+    float2 *tws = sm + spad_size(2 * CP * N);
+    for (int i = threadIdx.x; i < N; i += blockDim.x) tws[i] = g.twN[i];
     for (int idx = threadIdx.x; idx < N * CP; idx += blockDim.x) {
         const int pp = idx % CP, iy = idx / CP;
         const int xc = x0base + 2 * pp;
@@ -50,7 +52,7 @@ __global__ void __launch_bounds__(512) k_fwd_col(const float *__restrict__ x, fl
         sm[spad((pp * 2 + 1) * N + q)] = cmul(z, g.twG[iy]);
     }
     __syncthreads();
-    fft_pow2<-1>(sm, N, g.log2N, 2 * CP, g.twN);
+    fft_pow2<-1>(sm, N, g.log2N, 2 * CP, tws);
     float2 *Tb = T + (size_t)b * g.R * N;
     const int Gm = g.G - 1;
     for (int idx = threadIdx.x; idx < g.R * CP; idx += blockDim.x) {
@@ -70,9 +72,11 @@ __global__ void __launch_bounds__(512) k_fwd_col(const float *__restrict__ x, fl
 
 __global__ void __launch_bounds__(512) k_fwd_row(const float2 *__restrict__ T, float2 *__restrict__ P,
                           const KArgs g) {
-    extern __shared__ float2 sm[];  // [2][N]
+    extern __shared__ float2 sm[];  // [2][N] padded, then [N] twiddles
     const int N = g.N, r = blockIdx.x, b = blockIdx.y;
     const float2 *Tr = T + ((size_t)b * g.R + r) * N;
+    float2 *tws = sm + spad_size(2 * N);
+    for (int i = threadIdx.x; i < N; i += blockDim.x) tws[i] = g.twN[i];
     for (int ix = threadIdx.x; ix < N; ix += blockDim.x) {
         const float2 v = Tr[ix];
         const int q = (ix - N / 2) & (N - 1);
@@ -80,20 +84,20 @@ __global__ void __launch_bounds__(512) k_fwd_row(const float2 *__restrict__ T, f
         sm[spad(N + q)] = cmul(v, g.twG[ix]);
     }
     __syncthreads();
-    fft_pow2<-1>(sm, N, g.log2N, 2, g.twN);
+    fft_pow2<-1>(sm, N, g.log2N, 2, tws);
     float2 *Pb = P + (size_t)b * g.w * g.AM;
     const int e1 = g.row_off[r + 1];
     const int Gm = g.G - 1;
     for (int e = g.row_off[r] + threadIdx.x; e < e1; e += blockDim.x) {
-        const int key = g.ent_key[e];
-        const float ex = g.ent_ex[e];
+        const int4 en = g.ent[e];
+        const int key = entry_key(en);
+        const float ex = entry_ex(en);
         float2 acc = make_float2(0.f, 0.f);
         for (int t = 0; t < g.w; ++t) {
             const float wt = es_kernel_fast(((float)t - ex) * g.inv_h, g.beta_l2);
             cfma(acc, wt, sm[cell_slot(0, N, (key + t) & Gm)]);
         }
-        const float wy = g.ent_wy[e];
-        Pb[(size_t)g.ent_s[e] * g.AM + g.ent_p[e]] = cscale(acc, wy);
+        Pb[(size_t)entry_s(en) * g.AM + entry_p(en)] = cscale(acc, entry_wy(en));
     }
 }
 
@@ -102,19 +106,28 @@ __global__ void __launch_bounds__(512) k_fwd_row(const float2 *__restrict__ T, f
 #define DET_RESID 2
 #define DET_OBJ 4
 
-__global__ void __launch_bounds__(256) k_fwd_det(const float2 *__restrict__ P, float *__restrict__ y,
+// Detector-row transforms: the generic mixed-radix Stockham (BLUE = false) or
+// Bluestein through power-of-two FFTs (BLUE = true); buffer index helper.
+template <bool BLUE>
+__device__ __forceinline__ int didx(int i) { return BLUE ? spad(i) : i; }
+
+template <bool BLUE>
+__global__ void __launch_bounds__(512) k_fwd_det(const float2 *__restrict__ P, float *__restrict__ y,
                           const float *__restrict__ bsino, const float *__restrict__ wsino,
                           float *__restrict__ resid, double *__restrict__ partials,
                           const KArgs g, int mode) {
-    extern __shared__ float2 sm[];  // [D] bufA, [D] bufB, [D] tw, [rad0] root
+    // mixed radix: [D] bufA, [D] bufB, [D] tw, [rad0] root; Bluestein: [spad(L)] buffer
+    extern __shared__ float2 sm[];
     __shared__ double red[32];
     const int D = g.D, Mh = g.Mh, A = g.A;
     const int a0 = 2 * blockIdx.x, b = blockIdx.y;
     const bool has1 = (a0 + 1) < A;
     float2 *bufA = sm, *bufB = sm + D, *tw = sm + 2 * D, *root0 = sm + 3 * D;
-    const int R0 = g.rp.rad[0], per0 = D / R0;
-    for (int k = threadIdx.x; k < D; k += blockDim.x) tw[k] = g.twD[k];
-    for (int k = threadIdx.x; k < R0; k += blockDim.x) root0[k] = g.twD[k * per0];
+    if (!BLUE) {
+        const int R0 = g.rp.rad[0], per0 = D / R0;
+        for (int k = threadIdx.x; k < D; k += blockDim.x) tw[k] = g.twD[k];
+        for (int k = threadIdx.x; k < R0; k += blockDim.x) root0[k] = g.twD[k * per0];
+    }
     const float2 *Pb = P + (size_t)b * g.w * g.AM;
     for (int m = threadIdx.x; m < Mh; m += blockDim.x) {
         float2 c0 = make_float2(0.f, 0.f), c1 = make_float2(0.f, 0.f);
@@ -128,14 +141,20 @@ __global__ void __launch_bounds__(256) k_fwd_det(const float2 *__restrict__ P, f
         const float sg = (m & 1) ? -1.f : 1.f;
         float2 X0 = cscale(c0, sg), X1 = cscale(c1, sg);
         if (2 * m == D) { X0.y = 0.f; X1.y = 0.f; }
-        bufA[m] = make_float2(X0.x - X1.y, X0.y + X1.x);
-        if (m > 0 && 2 * m < D) bufA[D - m] = make_float2(X0.x + X1.y, X1.x - X0.y);
+        bufA[didx<BLUE>(m)] = make_float2(X0.x - X1.y, X0.y + X1.x);
+        if (m > 0 && 2 * m < D) bufA[didx<BLUE>(D - m)] = make_float2(X0.x + X1.y, X1.x - X0.y);
     }
     __syncthreads();
-    const float2 *res = fft_mixed<+1>(bufA, bufB, g.rp, tw, root0);
+    const float2 *res;
+    if (BLUE) {
+        bluestein<+1>(sm, D, g.L, g.log2L, g.chirp, g.bhat, g.twL);
+        res = sm;
+    } else {
+        res = fft_mixed<+1>(bufA, bufB, g.rp, tw, root0);
+    }
     float objv = 0.f;
     for (int i = threadIdx.x; i < D; i += blockDim.x) {
-        const float2 z = res[i];
+        const float2 z = res[didx<BLUE>(i)];
         const float yv[2] = {z.x * g.invD, z.y * g.invD};
         for (int h = 0; h < 2; ++h) {
             if (h == 1 && !has1) break;
@@ -157,25 +176,34 @@ __global__ void __launch_bounds__(256) k_fwd_det(const float2 *__restrict__ P, f
 }
 
 // ------------------------------------------------------------ adjoint ------
-__global__ void __launch_bounds__(256) k_adj_det(const float *__restrict__ ysino, float2 *__restrict__ V,
+template <bool BLUE>
+__global__ void __launch_bounds__(512) k_adj_det(const float *__restrict__ ysino, float2 *__restrict__ V,
                           const KArgs g) {
     extern __shared__ float2 sm[];
     const int D = g.D, Mh = g.Mh, A = g.A;
     const int a0 = 2 * blockIdx.x, b = blockIdx.y;
     const bool has1 = (a0 + 1) < A;
     float2 *bufA = sm, *bufB = sm + D, *tw = sm + 2 * D, *root0 = sm + 3 * D;
-    const int R0 = g.rp.rad[0], per0 = D / R0;
-    for (int k = threadIdx.x; k < D; k += blockDim.x) tw[k] = g.twD[k];
-    for (int k = threadIdx.x; k < R0; k += blockDim.x) root0[k] = g.twD[k * per0];
+    if (!BLUE) {
+        const int R0 = g.rp.rad[0], per0 = D / R0;
+        for (int k = threadIdx.x; k < D; k += blockDim.x) tw[k] = g.twD[k];
+        for (int k = threadIdx.x; k < R0; k += blockDim.x) root0[k] = g.twD[k * per0];
+    }
     const float *y0 = ysino + ((size_t)b * A + a0) * D;
     for (int i = threadIdx.x; i < D; i += blockDim.x)
-        bufA[i] = make_float2(y0[i], has1 ? y0[D + i] : 0.f);
+        bufA[didx<BLUE>(i)] = make_float2(y0[i], has1 ? y0[D + i] : 0.f);
     __syncthreads();
-    const float2 *Z = fft_mixed<-1>(bufA, bufB, g.rp, tw, root0);
+    const float2 *Z;
+    if (BLUE) {
+        bluestein<-1>(sm, D, g.L, g.log2L, g.chirp, g.bhat, g.twL);
+        Z = sm;
+    } else {
+        Z = fft_mixed<-1>(bufA, bufB, g.rp, tw, root0);
+    }
     float2 *Vb = V + (size_t)b * g.w * g.AM;
     for (int m = threadIdx.x; m < Mh; m += blockDim.x) {
-        const float2 zp = Z[m];
-        const float2 zm = cconj(Z[m == 0 ? 0 : D - m]);
+        const float2 zp = Z[didx<BLUE>(m)];
+        const float2 zm = cconj(Z[didx<BLUE>(m == 0 ? 0 : D - m)]);
         // Y_a0 = (zp + zm)/2, Y_a1 = (zp - zm)/(2i); weight mu_m nu_m (-1)^m / D
         const float mn = (m == 0 || 2 * m == D) ? 1.f : 2.f;
         const float sc = ((m & 1) ? -mn : mn) * 0.5f * g.invD;
@@ -192,75 +220,105 @@ __global__ void __launch_bounds__(256) k_adj_det(const float *__restrict__ ysino
 
 // Spreading of one grid row, atomic-free.  The row's (point, tap) entries are
 // sorted by jx0 (the key), so entries with one key form a run.  Entries are
-// taken in chunks: every thread stages one entry's u = phi_y * V[p] and
-// gx - jx0 in shared memory and the run table of the chunk is built.  Then,
-// in w phases by (key - kmin) mod w, one thread per (key, tap t) sums
-// u * phi(t - (gx - jx0)) over the key's run and adds it to cell key + t:
-// keys of one phase are at least w apart, so no two threads touch the same
-// cell.  Keys whose window could wrap (mod G) onto a low key's window are
-// added last by one thread.  Every cell's summation order is fixed, so the
-// result is bit-reproducible.
+// taken in chunks: every thread stages one entry's u = phi_y * V[p], gx - jx0
+// and key in shared memory, and a block-wide scan lists the run starts.
+// Consecutive runs have increasing keys, so runs j and j + w have keys at
+// least w apart: in phase ph (runs j = ph mod w) no two runs' windows
+// key..key+w-1 overlap, and one thread per (run, tap t) sums u * phi(t -
+// (gx - jx0)) over its run and adds it to cell key + t without conflicts.
+// Runs whose window could wrap (mod G) onto the first runs' windows are added
+// last by one thread.  Every cell's summation order is fixed, so the result is
+// bit-reproducible.
 __global__ void __launch_bounds__(512) k_adj_row(const float2 *__restrict__ V, float2 *__restrict__ U,
                           const KArgs g) {
     extern __shared__ float2 sm[];
+    __shared__ int wsum[32];
+    __shared__ int s_nr, s_nmain;
     const int N = g.N, G = g.G, w = g.w, r = blockIdx.x, b = blockIdx.y;
-    const int nkeys = g.kmax - g.kmin + 1;
     const int hsz = spad_size(2 * N);
-    float2 *cu = sm + hsz;                                     // [SPREAD_CHUNK]
-    float *cex = reinterpret_cast<float *>(cu + SPREAD_CHUNK);   // [SPREAD_CHUNK]
-    short *rstart = reinterpret_cast<short *>(cex + SPREAD_CHUNK);  // [nkeys]
-    short *rlen = rstart + nkeys;                              // [nkeys]
+    float2 *tws = sm + hsz;                                        // [N] twiddles
+    float2 *cu = tws + N;                                          // [SPREAD_CHUNK]
+    float *cex = reinterpret_cast<float *>(cu + SPREAD_CHUNK);     // [SPREAD_CHUNK]
+    short *ckey = reinterpret_cast<short *>(cex + SPREAD_CHUNK);   // [SPREAD_CHUNK]
+    short *rpos = ckey + SPREAD_CHUNK;                             // [SPREAD_CHUNK + 1]
     const int e0 = g.row_off[r], e1 = g.row_off[r + 1];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = (blockDim.x + 31) >> 5;
     for (int c = threadIdx.x; c < hsz; c += blockDim.x) sm[c] = make_float2(0.f, 0.f);
+    for (int i = threadIdx.x; i < N; i += blockDim.x) tws[i] = g.twN[i];
     const float2 *Vb = V + (size_t)b * g.w * g.AM;
-    const int nlow = nkeys < G - w + 1 ? nkeys : G - w + 1;
+    // keys with key - kmin >= klow may wrap onto the lowest keys' windows
+    const int klow = g.kmin + G - w + 1;
     for (int c0 = e0; c0 < e1; c0 += SPREAD_CHUNK) {
         const int n = (e1 - c0) < SPREAD_CHUNK ? (e1 - c0) : SPREAD_CHUNK;
-        for (int k = threadIdx.x; k < nkeys; k += blockDim.x) rlen[k] = 0;
         for (int i = threadIdx.x; i < n; i += blockDim.x) {
             const int e = c0 + i;
-            cu[i] = cscale(Vb[g.ent_p[e]], g.ent_wy[e]);
-            cex[i] = g.ent_ex[e];
+            const int4 en = g.ent[e];
+            cu[i] = cscale(Vb[entry_p(en)], entry_wy(en));
+            cex[i] = entry_ex(en);
+            ckey[i] = (short)entry_key(en);
         }
         __syncthreads();
-        for (int i = threadIdx.x; i < n; i += blockDim.x) {
-            const int key = g.ent_key[c0 + i];
-            if (i == 0 || g.ent_key[c0 + i - 1] != key) rstart[key - g.kmin] = (short)i;
+        // run starts: block-wide exclusive scan over contiguous per-thread segments
+        const int per = (n + blockDim.x - 1) / blockDim.x;
+        const int i0 = threadIdx.x * per, i1 = min(n, i0 + per);
+        int cnt = 0;
+        for (int i = i0; i < i1; ++i) cnt += (i == 0 || ckey[i] != ckey[i - 1]);
+        int incl = cnt;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        if (lane == 31) wsum[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            int v = lane < nwarps ? wsum[lane] : 0;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int u = __shfl_up_sync(0xffffffffu, v, o);
+                if (lane >= o) v += u;
+            }
+            wsum[lane] = v;
         }
         __syncthreads();
-        for (int i = threadIdx.x; i < n; i += blockDim.x) {
-            const int key = g.ent_key[c0 + i];
-            if (i == n - 1 || g.ent_key[c0 + i + 1] != key)
-                rlen[key - g.kmin] = (short)(i + 1 - rstart[key - g.kmin]);
+        int pos = (warp > 0 ? wsum[warp - 1] : 0) + incl - cnt;
+        for (int i = i0; i < i1; ++i)
+            if (i == 0 || ckey[i] != ckey[i - 1]) rpos[pos++] = (short)i;
+        if (threadIdx.x == 0) {
+            const int nr = wsum[nwarps - 1];
+            rpos[nr] = (short)n;
+            s_nr = nr;
         }
         __syncthreads();
+        if (threadIdx.x == 0) {
+            int nm = s_nr;
+            while (nm > 0 && ckey[rpos[nm - 1]] >= klow) --nm;
+            s_nmain = nm;
+        }
+        __syncthreads();
+        const int nr = s_nr, nmain = s_nmain;
         for (int ph = 0; ph < w; ++ph) {
-            const int nk = (nlow - ph + w - 1) / w;
-            for (int item = threadIdx.x; item < nk * w; item += blockDim.x) {
-                const int j = item / w, t = item - j * w;
-                const int ki = ph + j * w;
-                const int len = rlen[ki];
-                if (len == 0) continue;
-                const int st = rstart[ki];
+            const int nm = (nmain - ph + w - 1) / w;
+            for (int item = threadIdx.x; item < nm * 8; item += blockDim.x) {
+                const int t = item & 7;
+                if (t >= w) continue;
+                const int j = ph + (item >> 3) * w;
+                const int st = rpos[j], en = rpos[j + 1];
                 float2 acc = make_float2(0.f, 0.f);
-                for (int e = st; e < st + len; ++e)
+                for (int e = st; e < en; ++e)
                     cfma(acc, es_kernel_fast(((float)t - cex[e]) * g.inv_h, g.beta_l2), cu[e]);
-                const int c = (g.kmin + ki + t) & (G - 1);
+                const int c = (ckey[st] + t) & (G - 1);
                 float2 &hc = sm[cell_slot(0, N, c)];
                 hc = cadd(hc, acc);
             }
             __syncthreads();
         }
         if (threadIdx.x == 0) {
-            for (int ki = nlow; ki < nkeys; ++ki) {
-                const int len = rlen[ki];
-                if (len == 0) continue;
-                const int st = rstart[ki];
+            for (int j = nmain; j < nr; ++j) {
+                const int st = rpos[j], en = rpos[j + 1];
                 for (int t = 0; t < w; ++t) {
                     float2 acc = make_float2(0.f, 0.f);
-                    for (int e = st; e < st + len; ++e)
+                    for (int e = st; e < en; ++e)
                         cfma(acc, es_kernel_fast(((float)t - cex[e]) * g.inv_h, g.beta_l2), cu[e]);
-                    const int c = (g.kmin + ki + t) & (G - 1);
+                    const int c = (ckey[st] + t) & (G - 1);
                     float2 &hc = sm[cell_slot(0, N, c)];
                     hc = cadd(hc, acc);
                 }
@@ -268,7 +326,7 @@ __global__ void __launch_bounds__(512) k_adj_row(const float2 *__restrict__ V, f
         }
         __syncthreads();
     }
-    fft_pow2<+1>(sm, N, g.log2N, 2, g.twN);
+    fft_pow2<+1>(sm, N, g.log2N, 2, tws);
     float2 *Ur = U + ((size_t)b * g.R + r) * N;
     for (int ix = threadIdx.x; ix < N; ix += blockDim.x) {
         const int q = (ix - N / 2) & (N - 1);
@@ -278,10 +336,12 @@ __global__ void __launch_bounds__(512) k_adj_row(const float2 *__restrict__ V, f
 
 __global__ void __launch_bounds__(512) k_adj_col(const float2 *__restrict__ U, float *__restrict__ x,
                           const KArgs g, int CP) {
-    extern __shared__ float2 sm[];  // [CP][2][N]
+    extern __shared__ float2 sm[];  // [CP][2][N] padded, then [N] twiddles
     const int N = g.N, G = g.G, b = blockIdx.y;
     const int x0base = blockIdx.x * CP * 2;
     const float2 *Ub = U + (size_t)b * g.R * N;
+    float2 *tws = sm + spad_size(2 * CP * N);
+    for (int i = threadIdx.x; i < N; i += blockDim.x) tws[i] = g.twN[i];
     const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
     for (int idx = threadIdx.x; idx < G * CP; idx += blockDim.x) {
         const int pp = idx % CP, jy = idx / CP;
@@ -299,7 +359,7 @@ __global__ void __launch_bounds__(512) k_adj_col(const float2 *__restrict__ U, f
         sm[cell_slot(pp * 2 * N, N, jy)] = make_float2(h0x - h1y, h0y + h1x);
     }
     __syncthreads();
-    fft_pow2<+1>(sm, N, g.log2N, 2 * CP, g.twN);
+    fft_pow2<+1>(sm, N, g.log2N, 2 * CP, tws);
     float *xb = x + (size_t)b * N * N;
     for (int idx = threadIdx.x; idx < N * CP; idx += blockDim.x) {
         const int pp = idx % CP, iy = idx / CP;
@@ -330,7 +390,10 @@ int launch_radon_fwd_chunk(tc_plan *p, const float *x, float *y, int nb,
     if (y) mode |= DET_WRITE_Y;
     if (resid) mode |= DET_RESID;
     if (resid && obj_acc) mode |= DET_OBJ;
-    TC_PROFILED(TCK_FWD_DET, s, k_fwd_det<<<gd, p->threads_det, p->smem_det, s>>>(p->pv, y, b, w, resid, p->partials, g, mode));
+    if (g.blue)
+        TC_PROFILED(TCK_FWD_DET, s, k_fwd_det<true><<<gd, p->threads_det, p->smem_det, s>>>(p->pv, y, b, w, resid, p->partials, g, mode));
+    else
+        TC_PROFILED(TCK_FWD_DET, s, k_fwd_det<false><<<gd, p->threads_det, p->smem_det, s>>>(p->pv, y, b, w, resid, p->partials, g, mode));
     TC_LAUNCHED("k_fwd_det");
     if (mode & DET_OBJ) {
         int rc = launch_reduce_finalize(p->partials, gd.x * gd.y, obj_acc, 1, 1.0, s);
@@ -343,7 +406,10 @@ int launch_radon_adj_chunk(tc_plan *p, const float *y, float *x, int nb,
                            cudaStream_t s) {
     const KArgs &g = p->k;
     dim3 gd((g.A + 1) / 2, nb);
-    TC_PROFILED(TCK_ADJ_DET, s, k_adj_det<<<gd, p->threads_det, p->smem_det, s>>>(y, p->pv, g));
+    if (g.blue)
+        TC_PROFILED(TCK_ADJ_DET, s, k_adj_det<true><<<gd, p->threads_det, p->smem_det, s>>>(y, p->pv, g));
+    else
+        TC_PROFILED(TCK_ADJ_DET, s, k_adj_det<false><<<gd, p->threads_det, p->smem_det, s>>>(y, p->pv, g));
     TC_LAUNCHED("k_adj_det");
     dim3 gr(g.R, nb);
     TC_PROFILED(TCK_ADJ_ROW, s, k_adj_row<<<gr, p->threads_row, p->smem_row_adj, s>>>(p->pv, p->tu, g));
@@ -360,7 +426,9 @@ int radon_configure_kernels(tc_plan *p) {
     TC_CUDA(cudaFuncSetAttribute(k_adj_col, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem_col));
     TC_CUDA(cudaFuncSetAttribute(k_fwd_row, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem_row_fwd));
     TC_CUDA(cudaFuncSetAttribute(k_adj_row, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem_row_adj));
-    TC_CUDA(cudaFuncSetAttribute(k_fwd_det, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem_det));
-    TC_CUDA(cudaFuncSetAttribute(k_adj_det, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem_det));
+    TC_CUDA(cudaFuncSetAttribute(k_fwd_det<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem_det));
+    TC_CUDA(cudaFuncSetAttribute(k_adj_det<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem_det));
+    TC_CUDA(cudaFuncSetAttribute(k_fwd_det<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem_det));
+    TC_CUDA(cudaFuncSetAttribute(k_adj_det<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem_det));
     return TC_OK;
 }
