@@ -31,7 +31,8 @@ struct KArgs {
     float beta_l2;     // beta * log2(e)
     float invD;
     const float *dea;          // [N] 1 / psi(i - N/2)  (from FP64)
-    const float2 *twN;         // [N] exp(-2 pi i k / N)
+    const float2 *twN;         // per-stage twiddle tables of the N-point FFT (ntwN entries)
+    int ntwN;
     const float2 *twG;         // [N] exp(-2 pi i (k - N/2) / G)
     const float2 *twD;         // [D] exp(-2 pi i k / D)
     const int *row_off;        // [R + 1] first entry of each grid row
@@ -43,7 +44,7 @@ struct KArgs {
     int blue, L, log2L;
     const float2 *chirp;       // [D] exp(-i pi (n^2 mod 2D) / D)
     const float2 *bhat;        // [L] FFT_L of the conjugate chirp (wrapped), times 1/L
-    const float2 *twL;         // [L] exp(-2 pi i k / L)
+    const float2 *twL;         // per-stage twiddle tables of the L-point FFT
 };
 
 struct tc_plan {

@@ -112,31 +112,52 @@ __device__ __forceinline__ void dft_reg(float2 *v) {
     }
 }
 
-// One in-place Stockham stage of radix R over cnt transforms of length n
-// (padded indexing).  Every thread loads its IT butterflies, the block
-// synchronises, then all store.
+// Transform stride (in padded elements) for cnt transforms of length n kept
+// back to back: the padded length rounded up to 8 (mod 16), so element i of
+// consecutive transforms falls in different bank halves.
+__host__ __device__ __forceinline__ int fft_tstride(int n) {
+    const int m = spad_size(n);
+    return m + ((24 - (m & 15)) & 15);
+}
+
+// Per-stage twiddle tables of a length-n FFT (n = 2^log2n), concatenated for
+// the stages after the first: stage (Ns, R) holds W_n^(q k n / (Ns R)) at
+// [(q - 1) * Ns + k], q = 1..R-1, k = 0..Ns-1, so the lanes of a warp (k
+// consecutive) read consecutive words.  Total entries: fft_twiddle_count(n).
+__host__ __device__ __forceinline__ int fft_twiddle_count(int log2n) {
+    int logNs = 0, total = 0;
+    while (log2n - logNs > 0) {
+        const int lr = (log2n - logNs >= 4) ? 4 : (log2n - logNs);
+        if (logNs > 0) total += ((1 << lr) - 1) << logNs;
+        logNs += lr;
+    }
+    return total;
+}
+
+// One in-place Stockham stage of radix R over cnt transforms (stride ts).
+// Every thread loads its IT butterflies, the block synchronises, then all
+// store.
 template <int SIGN, int R, int LOGR, int IT>
-__device__ __forceinline__ void stockham_stage(float2 *s, int log2n, int cnt, int Ns, int logNs,
-                                               const float2 *__restrict__ tw) {
+__device__ __forceinline__ void stockham_stage(float2 *s, int log2n, int cnt, int ts, int Ns, int logNs,
+                                               const float2 *__restrict__ tws) {
     const int nt = blockDim.x, tid = threadIdx.x;
     const int logper = log2n - LOGR, per = 1 << logper;
     const int total = cnt << logper;
-    const int twshift = log2n - logNs - LOGR;  // twiddle stride n / (Ns R)
     float2 v[IT][R];
 #pragma unroll
     for (int i = 0; i < IT; ++i) {
         const int it = tid + i * nt;
         if (it < total) {
             const int tr = it >> logper, j = it & (per - 1), k = j & (Ns - 1);
-            const int base = (tr << log2n) + j;
-            v[i][0] = s[spad(base)];
+            float2 *src = s + tr * ts;
+            v[i][0] = src[spad(j)];
             if (logNs == 0) {  // first stage: every twiddle is 1
 #pragma unroll
-                for (int q = 1; q < R; ++q) v[i][q] = s[spad(base + q * per)];
+                for (int q = 1; q < R; ++q) v[i][q] = src[spad(j + q * per)];
             } else {
 #pragma unroll
                 for (int q = 1; q < R; ++q)
-                    v[i][q] = cmul(s[spad(base + q * per)], tw_get<SIGN>(tw, (q * k) << twshift));
+                    v[i][q] = cmul(src[spad(j + q * per)], tw_get<SIGN>(tws, ((q - 1) << logNs) + k));
             }
         }
     }
@@ -147,28 +168,31 @@ __device__ __forceinline__ void stockham_stage(float2 *s, int log2n, int cnt, in
         if (it < total) {
             const int tr = it >> logper, j = it & (per - 1), k = j & (Ns - 1);
             dft_reg<SIGN, R>(v[i]);
-            const int base = (tr << log2n) + ((j >> logNs) << (logNs + LOGR)) + k;
+            float2 *dst = s + tr * ts;
+            const int base = ((j >> logNs) << (logNs + LOGR)) + k;
 #pragma unroll
-            for (int q = 0; q < R; ++q) s[spad(base + q * Ns)] = v[i][q];
+            for (int q = 0; q < R; ++q) dst[spad(base + q * Ns)] = v[i][q];
         }
     }
     __syncthreads();
 }
 
-// In-place FFT of cnt back-to-back length-n transforms (n = 2^log2n) in the
-// padded shared buffer s: radix-16 stages, then one radix-8/4/2 stage.
-// Requires blockDim.x >= cnt * n / 16.
+// In-place FFT of cnt length-n transforms (n = 2^log2n) in the padded shared
+// buffer s, transform t at s + t * ts: radix-16 stages, then one radix-8/4/2
+// stage.  tw: the per-stage twiddle tables (fft_twiddle_count(log2n)
+// entries).  Requires blockDim.x >= cnt * n / 16.
 template <int SIGN>
-__device__ void fft_pow2(float2 *s, int n, int log2n, int cnt, const float2 *__restrict__ tw) {
-    int logNs = 0;
+__device__ void fft_pow2(float2 *s, int n, int log2n, int cnt, int ts, const float2 *__restrict__ tw) {
+    int logNs = 0, toff = 0;
     while (log2n - logNs >= 4) {
-        stockham_stage<SIGN, 16, 4, 1>(s, log2n, cnt, 1 << logNs, logNs, tw);
+        stockham_stage<SIGN, 16, 4, 1>(s, log2n, cnt, ts, 1 << logNs, logNs, tw + toff);
+        if (logNs > 0) toff += 15 << logNs;
         logNs += 4;
     }
     const int rem = log2n - logNs;
-    if (rem == 3) stockham_stage<SIGN, 8, 3, 2>(s, log2n, cnt, 1 << logNs, logNs, tw);
-    else if (rem == 2) stockham_stage<SIGN, 4, 2, 4>(s, log2n, cnt, 1 << logNs, logNs, tw);
-    else if (rem == 1) stockham_stage<SIGN, 2, 1, 8>(s, log2n, cnt, 1 << logNs, logNs, tw);
+    if (rem == 3) stockham_stage<SIGN, 8, 3, 2>(s, log2n, cnt, ts, 1 << logNs, logNs, tw + toff);
+    else if (rem == 2) stockham_stage<SIGN, 4, 2, 4>(s, log2n, cnt, ts, 1 << logNs, logNs, tw + toff);
+    else if (rem == 1) stockham_stage<SIGN, 2, 1, 8>(s, log2n, cnt, ts, 1 << logNs, logNs, tw + toff);
 }
 
 // Out-of-place mixed-radix Stockham; returns the buffer holding the result.
@@ -244,10 +268,10 @@ __device__ void bluestein(float2 *s, int D, int L, int log2L, const float2 *__re
         s[spad(n)] = a;
     }
     __syncthreads();
-    fft_pow2<-1>(s, L, log2L, 1, twL);
+    fft_pow2<-1>(s, L, log2L, 1, 0, twL);
     for (int n = threadIdx.x; n < L; n += blockDim.x) s[spad(n)] = cmul(s[spad(n)], bhat[n]);
     __syncthreads();
-    fft_pow2<+1>(s, L, log2L, 1, twL);
+    fft_pow2<+1>(s, L, log2L, 1, 0, twL);
     for (int k = threadIdx.x; k < D; k += blockDim.x) {
         float2 v = cmul(s[spad(k)], chirp[k]);
         if (SIGN > 0) v.y = -v.y;

@@ -78,6 +78,17 @@ __global__ void __launch_bounds__(PRIOR_THREADS) k_prior(const float *__restrict
         }
         fpl[0][h] = inb ? f[(size_t)y * N + x] : 0.f;
     }
+    // pair validity is the same at every z: bit u of mup / bit q of mpl says the
+    // pair towards (dx, dy) is inside the volume and needed by an interior voxel
+    unsigned mup = 0, mpl = 0;
+#pragma unroll
+    for (int u = 0; u < 9; ++u) {
+        const int dx = u % 3 - 1, dy = u / 3 - 1;
+        if (inb && ring_in(dx, dy) && (interior || is_interior(dx, dy))) mup |= 1u << u;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        if (inb && ring_in(pdx[q], pdy[q]) && (interior || is_interior(pdx[q], pdy[q]))) mpl |= 1u << q;
     // register prefetch: the plane the next step stores (3D: z + 2, 2D: z + 1)
     const size_t off = (size_t)y * N + x;
     float f_nx = (inb && B > 1) ? f[NN + off] : 0.f;
@@ -97,26 +108,27 @@ __global__ void __launch_bounds__(PRIOR_THREADS) k_prior(const float *__restrict
         float hs = 0.f;
         if (ring) {
             const float fm = fpl[cur][h];
+            const unsigned mu = up ? mup : 0u;
 #pragma unroll
             for (int u = 0; u < 9; ++u) {
                 const int dx = u % 3 - 1, dy = u / 3 - 1;
                 float e = 0.f;
-                if (up && inb && ring_in(dx, dy) && (interior || is_interior(dx, dy))) {
+                if (mu & (1u << u)) {
                     float rho, rp;
                     qggmrf(fm - fpl[nxt][h + dy * PRX + dx], a, rho, rp);
                     e = rp;
-                    if (interior) hs = fmaf((dx == 0 && dy == 0) ? a.w1 : ((dx == 0 || dy == 0) ? a.w2 : a.w3), rho, hs);
+                    hs = fmaf((dx == 0 && dy == 0) ? a.w1 : ((dx == 0 || dy == 0) ? a.w2 : a.w3), rho, hs);
                 }
                 Eu[cur][u][h] = e;
             }
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 float e = 0.f;
-                if (inb && ring_in(pdx[q], pdy[q]) && (interior || is_interior(pdx[q], pdy[q]))) {
+                if (mpl & (1u << q)) {
                     float rho, rp;
                     qggmrf(fm - fpl[cur][h + pdy[q] * PRX + pdx[q]], a, rho, rp);
                     e = rp;
-                    if (interior) hs = fmaf(pw[q], rho, hs);
+                    hs = fmaf(pw[q], rho, hs);
                 }
                 Ep[q][h] = e;
             }

@@ -124,6 +124,27 @@ void fft64(std::vector<double> &re, std::vector<double> &im) {
     }
 }
 
+// Per-stage twiddle tables of a length-2^log2n FFT in the layout fft_pow2
+// reads: for each stage after the first, W^(q k n / (Ns R)) at [(q-1) Ns + k].
+std::vector<float2> stage_twiddles(int log2n) {
+    const int n = 1 << log2n;
+    std::vector<float2> out;
+    int logNs = 0;
+    while (log2n - logNs > 0) {
+        const int lr = std::min(4, log2n - logNs);
+        const int R = 1 << lr, Ns = 1 << logNs;
+        if (logNs > 0)
+            for (int q = 1; q < R; ++q)
+                for (int k = 0; k < Ns; ++k) {
+                    const long long e = (long long)q * k * (n / (Ns * R));
+                    const double a = -2.0 * kPi * (double)e / (double)n;
+                    out.push_back(make_float2((float)std::cos(a), (float)std::sin(a)));
+                }
+        logNs += lr;
+    }
+    return out;
+}
+
 // Largest prime factor of n.
 int largest_prime(int n) {
     int lp = 1;
@@ -331,19 +352,22 @@ int tc_plan_build(const tc_geom *geom, int max_batch, tc_plan **out) {
             fft64(br, bi);
             bhat.resize(L);
             for (int i = 0; i < L; ++i) bhat[i] = make_float2((float)(br[i] / L), (float)(bi[i] / L));
-            twL.resize(L);
-            for (int i = 0; i < L; ++i) {
-                const double a = -2.0 * kPi * i / L;
-                twL[i] = make_float2((float)std::cos(a), (float)std::sin(a));
+            twL = stage_twiddles(lg);
+            if ((int)twL.size() != fft_twiddle_count(lg)) {
+                tc_plan_free(p);
+                return TC_ERR_UNSUPPORTED;
             }
         }
     }
 
     // twiddles
-    std::vector<float2> twN(N), twG(N), twD(D);
+    std::vector<float2> twN = stage_twiddles(k.log2N), twG(N), twD(D);
+    k.ntwN = (int)twN.size();
+    if (k.ntwN != fft_twiddle_count(k.log2N)) {
+        tc_plan_free(p);
+        return TC_ERR_UNSUPPORTED;
+    }
     for (int i = 0; i < N; ++i) {
-        const double a1 = -2.0 * kPi * i / N;
-        twN[i] = make_float2((float)std::cos(a1), (float)std::sin(a1));
         const double a2 = -2.0 * kPi * (i - N / 2) / G;
         twG[i] = make_float2((float)std::cos(a2), (float)std::sin(a2));
     }
@@ -389,8 +413,8 @@ int tc_plan_build(const tc_geom *geom, int max_batch, tc_plan **out) {
     p->threads_col = std::max(64, 2 * cp * N / 16);
     p->threads_row = std::max(128, N / 8);
     p->threads_det = k.blue ? std::max(256, k.L / 16) : 256;
-    p->smem_col = (size_t)(spad_size(cp * 2 * N) + N) * sizeof(float2);
-    p->smem_row_fwd = (size_t)(spad_size(2 * N) + N) * sizeof(float2);
+    p->smem_col = (size_t)(2 * cp * fft_tstride(N) + k.ntwN) * sizeof(float2);
+    p->smem_row_fwd = (size_t)(2 * fft_tstride(N) + k.ntwN) * sizeof(float2);
     p->smem_row_adj = p->smem_row_fwd + (size_t)SPREAD_CHUNK * (sizeof(float2) + sizeof(float)) +
                       (size_t)(2 * SPREAD_CHUNK + 2) * sizeof(short);
     p->smem_det = k.blue ? (size_t)spad_size(k.L) * sizeof(float2)

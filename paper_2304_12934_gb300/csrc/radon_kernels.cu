@@ -26,21 +26,21 @@
 
 namespace {
 
-// Padded shared-memory slot of cell c of a G-row stored as [even | odd] halves
-// starting at element `base`.
-__device__ __forceinline__ int cell_slot(int base, int N, int c) {
-    return spad(base + (c & 1) * N + (c >> 1));
+// Shared-memory slot of cell c of a G-row kept as two N-point transforms
+// [even cells | odd cells], the even one being transform t0 (stride ts).
+__device__ __forceinline__ int cell_slot(int t0, int ts, int c) {
+    return (t0 + (c & 1)) * ts + spad(c >> 1);
 }
 
 // ------------------------------------------------------------ forward ------
 __global__ void __launch_bounds__(512) k_fwd_col(const float *__restrict__ x, float2 *__restrict__ T,
                           const KArgs g, int CP) {
-    extern __shared__ float2 sm[];  // [CP][2][N] padded, then [N] twiddles
-    const int N = g.N, b = blockIdx.y;
+    extern __shared__ float2 sm[];  // 2CP transforms (stride ts), then the twiddle tables
+    const int N = g.N, b = blockIdx.y, ts = fft_tstride(N);
     const int x0base = blockIdx.x * CP * 2;
     const float *xs = x + (size_t)b * N * N;
-    float2 *tws = sm + spad_size(2 * CP * N);
-    for (int i = threadIdx.x; i < N; i += blockDim.x) tws[i] = g.twN[i];
+    float2 *tws = sm + 2 * CP * ts;
+    for (int i = threadIdx.x; i < g.ntwN; i += blockDim.x) tws[i] = g.twN[i];
     for (int idx = threadIdx.x; idx < N * CP; idx += blockDim.x) {
         const int pp = idx % CP, iy = idx / CP;
         const int xc = x0base + 2 * pp;
@@ -48,18 +48,18 @@ __global__ void __launch_bounds__(512) k_fwd_col(const float *__restrict__ x, fl
         const float dy = g.dea[iy];
         const float2 z = make_float2(f.x * g.dea[xc] * dy, f.y * g.dea[xc + 1] * dy);
         const int q = (iy - N / 2) & (N - 1);
-        sm[spad((pp * 2) * N + q)] = z;
-        sm[spad((pp * 2 + 1) * N + q)] = cmul(z, g.twG[iy]);
+        sm[(pp * 2) * ts + spad(q)] = z;
+        sm[(pp * 2 + 1) * ts + spad(q)] = cmul(z, g.twG[iy]);
     }
     __syncthreads();
-    fft_pow2<-1>(sm, N, g.log2N, 2 * CP, tws);
+    fft_pow2<-1>(sm, N, g.log2N, 2 * CP, ts, tws);
     float2 *Tb = T + (size_t)b * g.R * N;
     const int Gm = g.G - 1;
     for (int idx = threadIdx.x; idx < g.R * CP; idx += blockDim.x) {
         const int pp = idx % CP, r = idx / CP;
         const int jy = g.jmin + r;
-        const float2 zp = sm[cell_slot(pp * 2 * N, N, jy & Gm)];
-        const float2 zm = cconj(sm[cell_slot(pp * 2 * N, N, (-jy) & Gm)]);
+        const float2 zp = sm[cell_slot(pp * 2, ts, jy & Gm)];
+        const float2 zm = cconj(sm[cell_slot(pp * 2, ts, (-jy) & Gm)]);
         const float2 d = csub(zp, zm);
         float4 o;
         o.x = 0.5f * (zp.x + zm.x);
@@ -72,19 +72,19 @@ __global__ void __launch_bounds__(512) k_fwd_col(const float *__restrict__ x, fl
 
 __global__ void __launch_bounds__(512) k_fwd_row(const float2 *__restrict__ T, float2 *__restrict__ P,
                           const KArgs g) {
-    extern __shared__ float2 sm[];  // [2][N] padded, then [N] twiddles
-    const int N = g.N, r = blockIdx.x, b = blockIdx.y;
+    extern __shared__ float2 sm[];  // 2 transforms (stride ts), then the twiddle tables
+    const int N = g.N, r = blockIdx.x, b = blockIdx.y, ts = fft_tstride(N);
     const float2 *Tr = T + ((size_t)b * g.R + r) * N;
-    float2 *tws = sm + spad_size(2 * N);
-    for (int i = threadIdx.x; i < N; i += blockDim.x) tws[i] = g.twN[i];
+    float2 *tws = sm + 2 * ts;
+    for (int i = threadIdx.x; i < g.ntwN; i += blockDim.x) tws[i] = g.twN[i];
     for (int ix = threadIdx.x; ix < N; ix += blockDim.x) {
         const float2 v = Tr[ix];
         const int q = (ix - N / 2) & (N - 1);
         sm[spad(q)] = v;
-        sm[spad(N + q)] = cmul(v, g.twG[ix]);
+        sm[ts + spad(q)] = cmul(v, g.twG[ix]);
     }
     __syncthreads();
-    fft_pow2<-1>(sm, N, g.log2N, 2, tws);
+    fft_pow2<-1>(sm, N, g.log2N, 2, ts, tws);
     float2 *Pb = P + (size_t)b * g.w * g.AM;
     const int e1 = g.row_off[r + 1];
     const int Gm = g.G - 1;
@@ -95,7 +95,7 @@ __global__ void __launch_bounds__(512) k_fwd_row(const float2 *__restrict__ T, f
         float2 acc = make_float2(0.f, 0.f);
         for (int t = 0; t < g.w; ++t) {
             const float wt = es_kernel_fast(((float)t - ex) * g.inv_h, g.beta_l2);
-            cfma(acc, wt, sm[cell_slot(0, N, (key + t) & Gm)]);
+            cfma(acc, wt, sm[cell_slot(0, ts, (key + t) & Gm)]);
         }
         Pb[(size_t)entry_s(en) * g.AM + entry_p(en)] = cscale(acc, entry_wy(en));
     }
@@ -235,16 +235,16 @@ __global__ void __launch_bounds__(512) k_adj_row(const float2 *__restrict__ V, f
     __shared__ int wsum[32];
     __shared__ int s_nr, s_nmain;
     const int N = g.N, G = g.G, w = g.w, r = blockIdx.x, b = blockIdx.y;
-    const int hsz = spad_size(2 * N);
-    float2 *tws = sm + hsz;                                        // [N] twiddles
-    float2 *cu = tws + N;                                          // [SPREAD_CHUNK]
+    const int ts = fft_tstride(N), hsz = 2 * ts;                  // grid row: 2 transforms
+    float2 *tws = sm + hsz;                                        // twiddle tables
+    float2 *cu = tws + g.ntwN;                                     // [SPREAD_CHUNK]
     float *cex = reinterpret_cast<float *>(cu + SPREAD_CHUNK);     // [SPREAD_CHUNK]
     short *ckey = reinterpret_cast<short *>(cex + SPREAD_CHUNK);   // [SPREAD_CHUNK]
     short *rpos = ckey + SPREAD_CHUNK;                             // [SPREAD_CHUNK + 1]
     const int e0 = g.row_off[r], e1 = g.row_off[r + 1];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = (blockDim.x + 31) >> 5;
     for (int c = threadIdx.x; c < hsz; c += blockDim.x) sm[c] = make_float2(0.f, 0.f);
-    for (int i = threadIdx.x; i < N; i += blockDim.x) tws[i] = g.twN[i];
+    for (int i = threadIdx.x; i < g.ntwN; i += blockDim.x) tws[i] = g.twN[i];
     const float2 *Vb = V + (size_t)b * g.w * g.AM;
     // keys with key - kmin >= klow may wrap onto the lowest keys' windows
     const int klow = g.kmin + G - w + 1;
@@ -306,7 +306,7 @@ __global__ void __launch_bounds__(512) k_adj_row(const float2 *__restrict__ V, f
                 for (int e = st; e < en; ++e)
                     cfma(acc, es_kernel_fast(((float)t - cex[e]) * g.inv_h, g.beta_l2), cu[e]);
                 const int c = (ckey[st] + t) & (G - 1);
-                float2 &hc = sm[cell_slot(0, N, c)];
+                float2 &hc = sm[cell_slot(0, ts, c)];
                 hc = cadd(hc, acc);
             }
             __syncthreads();
@@ -319,29 +319,29 @@ __global__ void __launch_bounds__(512) k_adj_row(const float2 *__restrict__ V, f
                     for (int e = st; e < en; ++e)
                         cfma(acc, es_kernel_fast(((float)t - cex[e]) * g.inv_h, g.beta_l2), cu[e]);
                     const int c = (ckey[st] + t) & (G - 1);
-                    float2 &hc = sm[cell_slot(0, N, c)];
+                    float2 &hc = sm[cell_slot(0, ts, c)];
                     hc = cadd(hc, acc);
                 }
             }
         }
         __syncthreads();
     }
-    fft_pow2<+1>(sm, N, g.log2N, 2, tws);
+    fft_pow2<+1>(sm, N, g.log2N, 2, ts, tws);
     float2 *Ur = U + ((size_t)b * g.R + r) * N;
     for (int ix = threadIdx.x; ix < N; ix += blockDim.x) {
         const int q = (ix - N / 2) & (N - 1);
-        Ur[ix] = cadd(sm[spad(q)], cmul(sm[spad(N + q)], cconj(g.twG[ix])));
+        Ur[ix] = cadd(sm[spad(q)], cmul(sm[ts + spad(q)], cconj(g.twG[ix])));
     }
 }
 
 __global__ void __launch_bounds__(512) k_adj_col(const float2 *__restrict__ U, float *__restrict__ x,
                           const KArgs g, int CP) {
-    extern __shared__ float2 sm[];  // [CP][2][N] padded, then [N] twiddles
-    const int N = g.N, G = g.G, b = blockIdx.y;
+    extern __shared__ float2 sm[];  // 2CP transforms (stride ts), then the twiddle tables
+    const int N = g.N, G = g.G, b = blockIdx.y, ts = fft_tstride(N);
     const int x0base = blockIdx.x * CP * 2;
     const float2 *Ub = U + (size_t)b * g.R * N;
-    float2 *tws = sm + spad_size(2 * CP * N);
-    for (int i = threadIdx.x; i < N; i += blockDim.x) tws[i] = g.twN[i];
+    float2 *tws = sm + 2 * CP * ts;
+    for (int i = threadIdx.x; i < g.ntwN; i += blockDim.x) tws[i] = g.twN[i];
     const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
     for (int idx = threadIdx.x; idx < G * CP; idx += blockDim.x) {
         const int pp = idx % CP, jy = idx / CP;
@@ -356,17 +356,17 @@ __global__ void __launch_bounds__(512) k_adj_col(const float2 *__restrict__ U, f
         // Hermitian parts of the two columns, packed as H0 + i H1
         const float h0x = 0.5f * (up.x + un.x), h0y = 0.5f * (up.y - un.y);
         const float h1x = 0.5f * (up.z + un.z), h1y = 0.5f * (up.w - un.w);
-        sm[cell_slot(pp * 2 * N, N, jy)] = make_float2(h0x - h1y, h0y + h1x);
+        sm[cell_slot(pp * 2, ts, jy)] = make_float2(h0x - h1y, h0y + h1x);
     }
     __syncthreads();
-    fft_pow2<+1>(sm, N, g.log2N, 2 * CP, tws);
+    fft_pow2<+1>(sm, N, g.log2N, 2 * CP, ts, tws);
     float *xb = x + (size_t)b * N * N;
     for (int idx = threadIdx.x; idx < N * CP; idx += blockDim.x) {
         const int pp = idx % CP, iy = idx / CP;
         const int xc = x0base + 2 * pp;
         const int q = (iy - N / 2) & (N - 1);
-        const float2 v = cadd(sm[spad(pp * 2 * N + q)],
-                              cmul(sm[spad(pp * 2 * N + N + q)], cconj(g.twG[iy])));
+        const float2 v = cadd(sm[(pp * 2) * ts + spad(q)],
+                              cmul(sm[(pp * 2 + 1) * ts + spad(q)], cconj(g.twG[iy])));
         const float dy = g.dea[iy];
         *reinterpret_cast<float2 *>(xb + (size_t)iy * N + xc) =
             make_float2(v.x * g.dea[xc] * dy, v.y * g.dea[xc + 1] * dy);
