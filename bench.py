@@ -61,6 +61,23 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(value: float, device=None) -> float:
+    """Largest value over all ranks (the job's time is its slowest rank's)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_seed(rank: int) -> int:
+    """Each rank solves its own replica volume, seeded by its rank."""
+    from paper_2304_12934_gb300 import synth
+    return synth.BASE_SEED + 1000 * rank
+
+
 # ------------------------------------------------------------- clocks ------
 class ClockSampler:
     """nvidia-smi SM clock / throttle-reason samples during the timed region."""
@@ -239,7 +256,7 @@ def run_ours(args):
     theta = np.arange(A) * (math.pi / A)
 
     # ---- inputs (untimed): replica volume per rank, seeded by rank
-    seed = synth.BASE_SEED + 1000 * rank
+    seed = replica_seed(rank)
     p_true = synth.ellipsoid_sinogram_torch(N, B, theta, D, dev, scale=1.0 / N, seed=seed)
     b, wgt = synth.poisson_measurement_torch(p_true, 1e4, seed + 1)
     del p_true
@@ -279,11 +296,7 @@ def run_ours(args):
     gpu_launches = api.launch_count() - launches0
     if ws > 1:
         dist.barrier()
-    ms = e0.elapsed_time(e1)
-    t = torch.tensor([ms], device=dev, dtype=torch.float64)
-    if ws > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms = float(t.item())
+    ms = max_over_ranks(e0.elapsed_time(e1), dev)
     ms_per_step = ms / args.steps
     value = ws * B * args.steps / (ms / 1e3)
 
@@ -342,11 +355,7 @@ def run_ours(args):
         t0 = time.perf_counter()
         for _ in range(args.steps):
             api.mbir_solve_host(plan, bh, wh, xh, 1, step, prior, state=st_e, dev=devbuf)
-        t_e2e = time.perf_counter() - t0
-        tt = torch.tensor([t_e2e], device=dev, dtype=torch.float64)
-        if ws > 1:
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_e2e = float(tt.item())
+        t_e2e = max_over_ranks(time.perf_counter() - t0, dev)
         e2e = {"value": ws * B * args.steps / t_e2e, "unit": UNIT,
                "h2d_bytes_per_step": int(bh.numel() * 4 + wh.numel() * 4 + xh.numel() * 4),
                "d2h_bytes_per_step": int(xh.numel() * 4),
