@@ -47,7 +47,8 @@ int check_ptrs(std::initializer_list<const void *> req, std::initializer_list<co
 
 // grad = A^T W (A x - b) + lambda grad H(x); scal[SC_DATA], scal[SC_PRIOR] set.
 int grad_impl(tc_plan *p, const float *x, const float *b, const float *w,
-              const tc_prior *prior, float *grad, int batch, cudaStream_t s) {
+              const tc_prior *prior, float *grad, int batch, cudaStream_t s,
+              bool want_prior_value = true) {
     TC_CUDA(cudaMemsetAsync(p->scal + SC_DATA, 0, 2 * sizeof(double), s));
     const size_t ni = img_elems(p), ns = sino_elems(p);
     for (int c0 = 0; c0 < batch; c0 += p->max_batch) {
@@ -59,7 +60,8 @@ int grad_impl(tc_plan *p, const float *x, const float *b, const float *w,
         if (rc) return rc;
     }
     if (prior && prior->lambda != 0.0) {
-        int rc = launch_prior_grad(p, x, grad, batch, prior, p->scal + SC_PRIOR, s);
+        int rc = launch_prior_grad(p, x, grad, batch, prior,
+                                   want_prior_value ? p->scal + SC_PRIOR : nullptr, s);
         if (rc) return rc;
     }
     return TC_OK;
@@ -216,7 +218,8 @@ int mbir_solve(tc_plan *p, const float *b, const float *w, float *x, int batch,
             return rc;
     }
     for (int it = 0; it < opts->n_iter; ++it) {
-        if ((rc = grad_impl(p, st->z, b, w, prior, st->g, batch, s))) return rc;
+        // the prior's value H is only reported for the last gradient point
+        if ((rc = grad_impl(p, st->z, b, w, prior, st->g, batch, s, it == opts->n_iter - 1))) return rc;
         if ((rc = launch_dots_gzx_gg(p, st->g, st->z, x, n, s))) return rc;
         if ((rc = launch_solver_scalar(p, opts->restart, s))) return rc;
         if ((rc = launch_update(p, x, st->z, st->g, n, s))) return rc;

@@ -17,15 +17,33 @@ struct PriorArgs {
     float w1, w2, w3;             // weights at distance 1, sqrt 2, sqrt 3
 };
 
-// rho(d) = u^2 / (c + |u|^(2-p)), u = d / sigma, and its derivative in d
-// (fast approximate log2 / exp2 / reciprocal: ~1e-7 relative error).
-__device__ __forceinline__ void qggmrf(float d, const PriorArgs &a, float &rho, float &rhop) {
+// Hardware approximations (one instruction each, denormals flushed to zero):
+// relative errors ~1e-7, far inside the prior's FP32 tolerance.
+__device__ __forceinline__ float lg2_approx(float x) {
+    float r;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float ex2_approx(float x) {
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// rho(d) = u^2 / (c + |u|^(2-p)), u = d / sigma, and its derivative in d.
+// |u|^(2-p) = 2^((2-p) log2|u|); at d = 0, log2 gives -inf and the power 0.
+__device__ __forceinline__ float qggmrf_rhop(float d, const PriorArgs &a, float &inv_out, float &u_out) {
     const float u = d * a.inv_sigma;
-    const float au = fabsf(u);
-    const float q = au > 0.f ? exp2f(a.qexp * __log2f(au)) : 0.f;
-    const float inv = __fdividef(1.0f, a.c + q);
-    rho = u * u * inv;
-    rhop = u * a.inv_sigma * fmaf(a.p, q, 2.0f * a.c) * inv * inv;
+    const float q = ex2_approx(a.qexp * lg2_approx(fabsf(u)));
+    const float inv = rcp_approx(a.c + q);
+    inv_out = inv;
+    u_out = u;
+    return u * a.inv_sigma * fmaf(a.p, q, 2.0f * a.c) * inv * inv;
 }
 
 // qGGMRF prior on a volume [B][N][N] (slices consecutive along z).
@@ -33,20 +51,27 @@ __device__ __forceinline__ void qggmrf(float d, const PriorArgs &a, float &rho, 
 // (tile + 1-voxel halo) of two f planes in shared memory.  Each unordered
 // neighbour pair is evaluated once, at its lower voxel, along the 13 forward
 // directions (9 towards z+1, 4 in-plane); both voxels read the pair's rho'
-// from shared memory (the z+1 pairs are kept one step for the voxel above).
-// dims = 2 skips the z pairs and uses the 8-neighbour weights.
+// from shared memory (the z+1 pairs are kept for the voxel above).
+// Buffers: the z+1 pair values rotate over three slots and the in-plane ones
+// over two, so a step's writes never touch what the previous step's gradient
+// phase still reads; with the plane double buffer this needs two barriers per
+// z step.  dims = 2 skips the z pairs and uses the 8-neighbour weights.
+// WANT_H also accumulates H (otherwise only the gradient is produced).
 #define PTX 32
 #define PTY 12
 #define PRX (PTX + 2)
 #define PRY (PTY + 2)
 #define PRS (PRX * PRY)
 #define PRIOR_THREADS 480
+#define PRIOR_SMEM_FLOATS (2 * PRS + 3 * 9 * PRS + 2 * 4 * PRS)
 
+template <bool WANT_H>
 __global__ void __launch_bounds__(PRIOR_THREADS) k_prior(const float *__restrict__ f, float *__restrict__ g,
                                                           double *__restrict__ partials, const PriorArgs a) {
-    __shared__ float fpl[2][PRS];
-    __shared__ float Eu[2][9][PRS];
-    __shared__ float Ep[4][PRS];
+    extern __shared__ float psm[];
+    float *fpl = psm;                 // [2][PRS]
+    float *Eu = fpl + 2 * PRS;        // [3][9][PRS]
+    float *Ep = Eu + 3 * 9 * PRS;     // [2][4][PRS]
     __shared__ double red[32];
     const int N = a.N, B = a.B;
     const size_t NN = (size_t)N * N;
@@ -71,13 +96,6 @@ __global__ void __launch_bounds__(PRIOR_THREADS) k_prior(const float *__restrict
         return nx >= 1 && nx <= PTX && ny >= 1 && ny <= PTY && x + dx < N && y + dy < N &&
                x + dx >= 0 && y + dy >= 0;
     };
-    if (ring) {
-        for (int u = 0; u < 9; ++u) {
-            Eu[0][u][h] = 0.f;
-            Eu[1][u][h] = 0.f;
-        }
-        fpl[0][h] = inb ? f[(size_t)y * N + x] : 0.f;
-    }
     // pair validity is the same at every z: bit u of mup / bit q of mpl says the
     // pair towards (dx, dy) is inside the volume and needed by an interior voxel
     unsigned mup = 0, mpl = 0;
@@ -89,72 +107,82 @@ __global__ void __launch_bounds__(PRIOR_THREADS) k_prior(const float *__restrict
 #pragma unroll
     for (int q = 0; q < 4; ++q)
         if (inb && ring_in(pdx[q], pdy[q]) && (interior || is_interior(pdx[q], pdy[q]))) mpl |= 1u << q;
+    if (ring) {
+        for (int u = 0; u < 9; ++u)
+            for (int sl = 0; sl < 3; ++sl) Eu[(sl * 9 + u) * PRS + h] = 0.f;
+        fpl[h] = inb ? f[(size_t)y * N + x] : 0.f;
+    }
     // register prefetch: the plane the next step stores (3D: z + 2, 2D: z + 1)
     const size_t off = (size_t)y * N + x;
     float f_nx = (inb && B > 1) ? f[NN + off] : 0.f;
     double hacc = 0.0;
     for (int z = 0; z < B; ++z) {
         const int cur = z & 1, nxt = cur ^ 1;
+        const int s3 = z % 3, p3 = (z + 2) % 3;  // this step's / previous step's z+1 slots
         const bool up = three && z + 1 < B;
         const int pz = three ? z + 2 : z + 1;
         const float f_pf = (inb && pz < B) ? f[(size_t)pz * NN + off] : 0.f;
         const size_t i = (size_t)z * NN + off;
         const float g_old = interior ? g[i] : 0.f;
         if (ring) {
-            if (up) fpl[nxt][h] = f_nx;                 // 3D: plane z + 1
-            else if (!three && z > 0) fpl[cur][h] = f_nx;  // 2D: slices are independent
+            if (up) fpl[nxt * PRS + h] = f_nx;                 // 3D: plane z + 1
+            else if (!three && z > 0) fpl[cur * PRS + h] = f_nx;  // 2D: slices are independent
         }
         __syncthreads();
         float hs = 0.f;
         if (ring) {
-            const float fm = fpl[cur][h];
+            const float fm = fpl[cur * PRS + h];
             const unsigned mu = up ? mup : 0u;
+            float *eu = Eu + (s3 * 9) * PRS + h;
 #pragma unroll
             for (int u = 0; u < 9; ++u) {
                 const int dx = u % 3 - 1, dy = u / 3 - 1;
                 float e = 0.f;
                 if (mu & (1u << u)) {
-                    float rho, rp;
-                    qggmrf(fm - fpl[nxt][h + dy * PRX + dx], a, rho, rp);
-                    e = rp;
-                    hs = fmaf((dx == 0 && dy == 0) ? a.w1 : ((dx == 0 || dy == 0) ? a.w2 : a.w3), rho, hs);
+                    float inv, uu;
+                    e = qggmrf_rhop(fm - fpl[nxt * PRS + h + dy * PRX + dx], a, inv, uu);
+                    if (WANT_H)
+                        hs = fmaf((dx == 0 && dy == 0) ? a.w1 : ((dx == 0 || dy == 0) ? a.w2 : a.w3), uu * uu * inv, hs);
                 }
-                Eu[cur][u][h] = e;
+                eu[u * PRS] = e;
             }
+            float *ep = Ep + (cur * 4) * PRS + h;
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 float e = 0.f;
                 if (mpl & (1u << q)) {
-                    float rho, rp;
-                    qggmrf(fm - fpl[cur][h + pdy[q] * PRX + pdx[q]], a, rho, rp);
-                    e = rp;
-                    hs = fmaf(pw[q], rho, hs);
+                    float inv, uu;
+                    e = qggmrf_rhop(fm - fpl[cur * PRS + h + pdy[q] * PRX + pdx[q]], a, inv, uu);
+                    if (WANT_H) hs = fmaf(pw[q], uu * uu * inv, hs);
                 }
-                Ep[q][h] = e;
+                ep[q * PRS] = e;
             }
         }
         __syncthreads();
         if (interior) {
             float gs = 0.f;
             if (three) {
+                const float *ec = Eu + (s3 * 9) * PRS + h, *epv = Eu + (p3 * 9) * PRS + h;
 #pragma unroll
                 for (int u = 0; u < 9; ++u) {
                     const int dx = u % 3 - 1, dy = u / 3 - 1;
                     const float wu = (dx == 0 && dy == 0) ? a.w1 : ((dx == 0 || dy == 0) ? a.w2 : a.w3);
-                    gs = fmaf(wu, Eu[cur][u][h] - Eu[nxt][u][h - dy * PRX - dx], gs);
+                    gs = fmaf(wu, ec[u * PRS] - epv[u * PRS - dy * PRX - dx], gs);
                 }
             }
+            const float *ep = Ep + (cur * 4) * PRS + h;
 #pragma unroll
             for (int q = 0; q < 4; ++q)
-                gs = fmaf(pw[q], Ep[q][h] - Ep[q][h - pdy[q] * PRX - pdx[q]], gs);
+                gs = fmaf(pw[q], ep[q * PRS] - ep[q * PRS - pdy[q] * PRX - pdx[q]], gs);
             g[i] = fmaf(a.two_lambda, gs, g_old);
-            hacc += 2.0 * (double)hs;
+            if (WANT_H) hacc += 2.0 * (double)hs;
         }
-        __syncthreads();
         f_nx = f_pf;
     }
-    const double tot = block_sum_f64(hacc, red);
-    if (threadIdx.x == 0) partials[blockIdx.y * gridDim.x + blockIdx.x] = tot;
+    if (WANT_H) {
+        const double tot = block_sum_f64(hacc, red);
+        if (threadIdx.x == 0) partials[blockIdx.y * gridDim.x + blockIdx.x] = tot;
+    }
 }
 
 __global__ void k_reduce_finalize(const double *__restrict__ partials, int n,
@@ -298,8 +326,11 @@ int launch_prior_grad(tc_plan *p, const float *x, float *g, int nb,
     const int blocks = grid.x * grid.y;
     if (blocks > p->slot) return TC_ERR_UNSUPPORTED;
     double *part = p->partials + (size_t)1 * p->slot;
-    TC_PROFILED(TCK_PRIOR, s,
-                k_prior<<<grid, PRIOR_THREADS, 0, s>>>(x, g, part, a));
+    const size_t smem = PRIOR_SMEM_FLOATS * sizeof(float);
+    if (h_acc)
+        TC_PROFILED(TCK_PRIOR, s, k_prior<true><<<grid, PRIOR_THREADS, smem, s>>>(x, g, part, a));
+    else
+        TC_PROFILED(TCK_PRIOR, s, k_prior<false><<<grid, PRIOR_THREADS, smem, s>>>(x, g, part, a));
     TC_LAUNCHED("k_prior");
     if (h_acc) return launch_reduce_finalize(part, blocks, h_acc, 0, pr->lambda, s);
     return TC_OK;
@@ -403,8 +434,20 @@ int launch_prior_kernel_into(const float *x, float *g, int n, int nb, const tc_p
     dim3 grid((n + PTX - 1) / PTX, (n + PTY - 1) / PTY);
     const int blocks = grid.x * grid.y;
     if (blocks > max_partials) return TC_ERR_INVALID_ARG;
-    TC_PROFILED(TCK_PRIOR, s, k_prior<<<grid, PRIOR_THREADS, 0, s>>>(x, g, partials, a));
+    const size_t smem = PRIOR_SMEM_FLOATS * sizeof(float);
+    if (h_out)
+        TC_PROFILED(TCK_PRIOR, s, k_prior<true><<<grid, PRIOR_THREADS, smem, s>>>(x, g, partials, a));
+    else
+        TC_PROFILED(TCK_PRIOR, s, k_prior<false><<<grid, PRIOR_THREADS, smem, s>>>(x, g, partials, a));
     TC_LAUNCHED("k_prior");
     if (h_out) return launch_reduce_finalize(partials, blocks, h_out, 0, pr->lambda, s);
+    return TC_OK;
+}
+
+// Opt the prior kernel into its dynamic shared memory (once per process).
+int prior_configure_kernels() {
+    const int smem = (int)(PRIOR_SMEM_FLOATS * sizeof(float));
+    TC_CUDA(cudaFuncSetAttribute(k_prior<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    TC_CUDA(cudaFuncSetAttribute(k_prior<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     return TC_OK;
 }

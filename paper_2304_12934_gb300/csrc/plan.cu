@@ -21,6 +21,7 @@
 #include "fft.cuh"
 
 int radon_configure_kernels(tc_plan *p);
+int prior_configure_kernels();
 
 namespace {
 
@@ -439,7 +440,7 @@ int tc_plan_build(const tc_geom *geom, int max_batch, tc_plan **out) {
     }
     TC_CUDA(cudaMemset(p->scal, 0, SC_COUNT * sizeof(double)));
     p->bytes = bytes;
-    if ((rc = radon_configure_kernels(p))) {
+    if ((rc = radon_configure_kernels(p)) || (rc = prior_configure_kernels())) {
         tc_plan_free(p);
         return rc;
     }

@@ -22,6 +22,7 @@ static __device__ __align__(256) double g_noalloc_partials[TC_NOALLOC_PARTIALS];
 int launch_prior_kernel_into(const float *x, float *g, int n, int nb, const tc_prior *pr,
                              double *partials, int max_partials, double *h_out,
                              cudaStream_t s);
+int prior_configure_kernels();
 
 namespace {
 
@@ -39,6 +40,8 @@ int noalloc_scratch(double **out) {
     if (!g_addr[dev]) {
         void *ptr = nullptr;
         TC_CUDA(cudaGetSymbolAddress(&ptr, g_noalloc_partials));
+        const int rc = prior_configure_kernels();
+        if (rc) return rc;
         g_addr[dev] = static_cast<double *>(ptr);
     }
     *out = g_addr[dev];
