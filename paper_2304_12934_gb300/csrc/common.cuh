@@ -37,6 +37,10 @@ struct KArgs {
     const float2 *twD;         // [D] exp(-2 pi i k / D)
     const int *row_off;        // [R + 1] first entry of each grid row
     const int4 *ent;           // [E] packed Entry records (see entry_* accessors)
+    // spreading records: one per (row, entry chunk, touched cell); see plan.cu
+    const int2 *rec;           // x: (signed cell - kmin) | seam << 15; y: lo | hi << 16
+    const int *rec_off;        // [R][2 nch + 1] record ranges (regular, seam) per row and chunk
+    int nch;                   // chunks per row (max over rows)
     const unsigned char *angle_flip; // [A] 1: theta was in [pi, 2 pi), data conjugated
     RadixPlan rp;              // factorisation of D
     // Bluestein (chirp-z) detector DFT, used when D has a large prime factor:
@@ -56,6 +60,8 @@ struct tc_plan {
     float2 *twN, *twG, *twD;
     int *row_off;
     int4 *ent;
+    int2 *rec;
+    int *rec_off;
     unsigned char *angle_flip;
     float2 *chirp, *bhat, *twL;
     long long n_entries;
@@ -115,7 +121,7 @@ __device__ __forceinline__ float es_kernel_fast(float z, float beta_l2) {
 }
 
 // Entries of one grid row staged per chunk by the spreading kernel.
-#define SPREAD_CHUNK 1024
+#define SPREAD_CHUNK 1536
 
 // Block-wide FP64 sum of one float per thread; thread 0 gets the total.
 __device__ __forceinline__ double block_sum_f64(double d, double *red) {

@@ -189,7 +189,7 @@ int alloc_dev(void **dst, size_t nb, long long &bytes) {
 
 void tc_plan_free(tc_plan *p) {
     if (!p) return;
-    void *ptrs[] = {p->dea64, p->dea, p->twN, p->twG, p->twD, p->row_off, p->ent,
+    void *ptrs[] = {p->dea64, p->dea, p->twN, p->twG, p->twD, p->row_off, p->ent, p->rec, p->rec_off,
                     p->tu, p->pv, p->sr, p->partials, p->scal, p->angle_flip,
                     p->chirp, p->bhat, p->twL};
     for (void *q : ptrs)
@@ -324,6 +324,68 @@ int tc_plan_build(const tc_geom *geom, int max_batch, tc_plan **out) {
     }
     p->n_entries = (long long)E;
 
+    // Spreading records.  Within each row the entries are cut into chunks of
+    // SPREAD_CHUNK; for every chunk and every signed cell cs touched by one of
+    // its entries (cs in [key, key + w - 1]), the entries that touch cs are
+    // those with key in [cs - w + 1, cs]: a contiguous range [lo, hi) of the
+    // key-sorted chunk.  A record (cs, lo, hi) lets one thread compute the
+    // chunk's whole contribution to cell cs mod G.  When two signed cells of a
+    // chunk share a physical cell (the spectrum edge wraps, cs and cs + G), the
+    // later record is flagged "seam" and added serially.
+    std::vector<int2> recs;
+    int nch = 1;
+    for (int r = 0; r < R; ++r) nch = std::max(nch, (cnt[r + 1] - cnt[r] + SPREAD_CHUNK - 1) / SPREAD_CHUNK);
+    // per row: [start_0, seam_0, start_1, seam_1, ..., start_nch]; the seam
+    // records of chunk k are [seam_k, start_{k+1}), after its regular ones
+    std::vector<int> roff((size_t)R * (2 * nch + 1), 0);
+    {
+        std::vector<int> last_use(G, -1);
+        std::vector<int2> seams;
+        int stamp = 0;
+        for (int r = 0; r < R; ++r) {
+            const int e0 = cnt[r], e1 = cnt[r + 1];
+            for (int kc = 0; kc <= nch; ++kc) {
+                int *ro = &roff[(size_t)r * (2 * nch + 1)];
+                ro[2 * kc] = (int)recs.size();
+                if (kc == nch) continue;
+                ro[2 * kc + 1] = (int)recs.size();
+                const int c0 = e0 + kc * SPREAD_CHUNK;
+                if (c0 >= e1) continue;
+                seams.clear();
+                const int n = std::min(SPREAD_CHUNK, e1 - c0);
+                ++stamp;
+                // signed cells touched, in increasing order: walk the sorted keys
+                int lo = 0, hi = 0;
+                int cs = ents[c0].key;
+                const int cs_end = ents[c0 + n - 1].key + w - 1;
+                while (cs <= cs_end) {
+                    while (lo < n && ents[c0 + lo].key < cs - w + 1) ++lo;
+                    while (hi < n && ents[c0 + hi].key <= cs) ++hi;
+                    if (hi > lo) {
+                        const int cp = cs & (G - 1);
+                        const int seam = last_use[cp] == stamp ? 1 : 0;
+                        last_use[cp] = stamp;
+                        int2 rc;
+                        rc.x = (cs - kmin) | (seam << 15);
+                        rc.y = lo | (hi << 16);
+                        (seam ? seams : recs).push_back(rc);
+                        ++cs;
+                    } else {
+                        // no entry touches cs: jump to the next key's window
+                        cs = (lo < n) ? std::max(cs + 1, ents[c0 + lo].key) : cs_end + 1;
+                    }
+                }
+                ro[2 * kc + 1] = (int)recs.size();
+                recs.insert(recs.end(), seams.begin(), seams.end());
+            }
+        }
+        if ((long long)kmax + w - 1 - kmin >= (1 << 15)) {
+            tc_plan_free(p);
+            return TC_ERR_UNSUPPORTED;
+        }
+    }
+    k.nch = nch;
+
     // Bluestein tables when D has a large prime factor (and L stays <= 8192)
     std::vector<float2> chirp, bhat, twL;
     {
@@ -391,6 +453,8 @@ int tc_plan_build(const tc_geom *geom, int max_batch, tc_plan **out) {
     UP(p->twD, twD);
     UP(p->row_off, cnt);
     UP(p->ent, epk);
+    UP(p->rec, recs);
+    UP(p->rec_off, roff);
     UP(p->angle_flip, flip);
     UP(p->chirp, chirp);
     UP(p->bhat, bhat);
@@ -402,6 +466,8 @@ int tc_plan_build(const tc_geom *geom, int max_batch, tc_plan **out) {
     k.twD = p->twD;
     k.row_off = p->row_off;
     k.ent = p->ent;
+    k.rec = p->rec;
+    k.rec_off = p->rec_off;
     k.angle_flip = p->angle_flip;
     k.chirp = p->chirp;
     k.bhat = p->bhat;
@@ -416,8 +482,7 @@ int tc_plan_build(const tc_geom *geom, int max_batch, tc_plan **out) {
     p->threads_det = k.blue ? std::max(256, k.L / 16) : 256;
     p->smem_col = (size_t)(2 * cp * fft_tstride(N) + k.ntwN) * sizeof(float2);
     p->smem_row_fwd = (size_t)(2 * fft_tstride(N) + k.ntwN) * sizeof(float2);
-    p->smem_row_adj = p->smem_row_fwd + (size_t)SPREAD_CHUNK * (sizeof(float2) + sizeof(float)) +
-                      (size_t)(2 * SPREAD_CHUNK + 2) * sizeof(short);
+    p->smem_row_adj = p->smem_row_fwd + (size_t)SPREAD_CHUNK * (sizeof(float2) + sizeof(float) + sizeof(short));
     p->smem_det = k.blue ? (size_t)spad_size(k.L) * sizeof(float2)
                          : (size_t)(3 * D + k.rp.rad[0]) * sizeof(float2);
     if (p->threads_col > 1024 || p->threads_row > 1024 || p->smem_det > 200 * 1024 ||

@@ -219,109 +219,60 @@ __global__ void __launch_bounds__(512) k_adj_det(const float *__restrict__ ysino
 }
 
 // Spreading of one grid row, atomic-free.  The row's (point, tap) entries are
-// sorted by jx0 (the key), so entries with one key form a run.  Entries are
-// taken in chunks: every thread stages one entry's u = phi_y * V[p], gx - jx0
-// and key in shared memory, and a block-wide scan lists the run starts.
-// Consecutive runs have increasing keys, so runs j and j + w have keys at
-// least w apart: in phase ph (runs j = ph mod w) no two runs' windows
-// key..key+w-1 overlap, and one thread per (run, tap t) sums u * phi(t -
-// (gx - jx0)) over its run and adds it to cell key + t without conflicts.
-// Runs whose window could wrap (mod G) onto the first runs' windows are added
-// last by one thread.  Every cell's summation order is fixed, so the result is
-// bit-reproducible.
+// sorted by jx0 (the key) and taken in chunks: every thread stages one
+// entry's u = phi_y * V[p], gx - jx0 and key in shared memory.  The plan holds
+// one record per touched cell of the chunk, naming the contiguous range of
+// entries whose footprint covers that cell (keys in [cell - w + 1, cell]);
+// one thread per record sums u * phi(cell - key - (gx - jx0)) over its range
+// and adds it to its cell.  Within a chunk every physical cell has one record
+// (the few wrap-around duplicates at the spectrum edge are flagged and added
+// serially), so no two threads touch a cell and every cell's summation order
+// is fixed: atomic-free and bit-reproducible.
 __global__ void __launch_bounds__(512) k_adj_row(const float2 *__restrict__ V, float2 *__restrict__ U,
                           const KArgs g) {
     extern __shared__ float2 sm[];
-    __shared__ int wsum[32];
-    __shared__ int s_nr, s_nmain;
-    const int N = g.N, G = g.G, w = g.w, r = blockIdx.x, b = blockIdx.y;
+    const int N = g.N, G = g.G, r = blockIdx.x, b = blockIdx.y;
     const int ts = fft_tstride(N), hsz = 2 * ts;                  // grid row: 2 transforms
     float2 *tws = sm + hsz;                                        // twiddle tables
     float2 *cu = tws + g.ntwN;                                     // [SPREAD_CHUNK]
     float *cex = reinterpret_cast<float *>(cu + SPREAD_CHUNK);     // [SPREAD_CHUNK]
     short *ckey = reinterpret_cast<short *>(cex + SPREAD_CHUNK);   // [SPREAD_CHUNK]
-    short *rpos = ckey + SPREAD_CHUNK;                             // [SPREAD_CHUNK + 1]
     const int e0 = g.row_off[r], e1 = g.row_off[r + 1];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = (blockDim.x + 31) >> 5;
     for (int c = threadIdx.x; c < hsz; c += blockDim.x) sm[c] = make_float2(0.f, 0.f);
     for (int i = threadIdx.x; i < g.ntwN; i += blockDim.x) tws[i] = g.twN[i];
     const float2 *Vb = V + (size_t)b * g.w * g.AM;
-    // keys with key - kmin >= klow may wrap onto the lowest keys' windows
-    const int klow = g.kmin + G - w + 1;
-    for (int c0 = e0; c0 < e1; c0 += SPREAD_CHUNK) {
+    const int *roff = g.rec_off + (size_t)r * (2 * g.nch + 1);
+    for (int kc = 0, c0 = e0; c0 < e1; ++kc, c0 += SPREAD_CHUNK) {
         const int n = (e1 - c0) < SPREAD_CHUNK ? (e1 - c0) : SPREAD_CHUNK;
         for (int i = threadIdx.x; i < n; i += blockDim.x) {
-            const int e = c0 + i;
-            const int4 en = g.ent[e];
+            const int4 en = g.ent[c0 + i];
             cu[i] = cscale(Vb[entry_p(en)], entry_wy(en));
             cex[i] = entry_ex(en);
             ckey[i] = (short)entry_key(en);
         }
         __syncthreads();
-        // run starts: block-wide exclusive scan over contiguous per-thread segments
-        const int per = (n + blockDim.x - 1) / blockDim.x;
-        const int i0 = threadIdx.x * per, i1 = min(n, i0 + per);
-        int cnt = 0;
-        for (int i = i0; i < i1; ++i) cnt += (i == 0 || ckey[i] != ckey[i - 1]);
-        int incl = cnt;
-        for (int o = 1; o < 32; o <<= 1) {
-            const int v = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += v;
-        }
-        if (lane == 31) wsum[warp] = incl;
-        __syncthreads();
-        if (warp == 0) {
-            int v = lane < nwarps ? wsum[lane] : 0;
-            for (int o = 1; o < 32; o <<= 1) {
-                const int u = __shfl_up_sync(0xffffffffu, v, o);
-                if (lane >= o) v += u;
-            }
-            wsum[lane] = v;
-        }
-        __syncthreads();
-        int pos = (warp > 0 ? wsum[warp - 1] : 0) + incl - cnt;
-        for (int i = i0; i < i1; ++i)
-            if (i == 0 || ckey[i] != ckey[i - 1]) rpos[pos++] = (short)i;
-        if (threadIdx.x == 0) {
-            const int nr = wsum[nwarps - 1];
-            rpos[nr] = (short)n;
-            s_nr = nr;
+        const int rb = roff[2 * kc], rs = roff[2 * kc + 1], re = roff[2 * kc + 2];
+        for (int q = rb + threadIdx.x; q < rs; q += blockDim.x) {
+            const int2 rc = g.rec[q];
+            const int cs = (rc.x & 0x7fff) + g.kmin;
+            const int lo = rc.y & 0xffff, hi = rc.y >> 16;
+            float2 acc = make_float2(0.f, 0.f);
+            for (int i = lo; i < hi; ++i)
+                cfma(acc, es_kernel_fast(((float)(cs - ckey[i]) - cex[i]) * g.inv_h, g.beta_l2), cu[i]);
+            float2 &hc = sm[cell_slot(0, ts, cs & (G - 1))];
+            hc = cadd(hc, acc);
         }
         __syncthreads();
         if (threadIdx.x == 0) {
-            int nm = s_nr;
-            while (nm > 0 && ckey[rpos[nm - 1]] >= klow) --nm;
-            s_nmain = nm;
-        }
-        __syncthreads();
-        const int nr = s_nr, nmain = s_nmain;
-        for (int ph = 0; ph < w; ++ph) {
-            const int nm = (nmain - ph + w - 1) / w;
-            for (int item = threadIdx.x; item < nm * 8; item += blockDim.x) {
-                const int t = item & 7;
-                if (t >= w) continue;
-                const int j = ph + (item >> 3) * w;
-                const int st = rpos[j], en = rpos[j + 1];
+            for (int q = rs; q < re; ++q) {  // seam records, in order
+                const int2 rc = g.rec[q];
+                const int cs = (rc.x & 0x7fff) + g.kmin;
+                const int lo = rc.y & 0xffff, hi = rc.y >> 16;
                 float2 acc = make_float2(0.f, 0.f);
-                for (int e = st; e < en; ++e)
-                    cfma(acc, es_kernel_fast(((float)t - cex[e]) * g.inv_h, g.beta_l2), cu[e]);
-                const int c = (ckey[st] + t) & (G - 1);
-                float2 &hc = sm[cell_slot(0, ts, c)];
+                for (int i = lo; i < hi; ++i)
+                    cfma(acc, es_kernel_fast(((float)(cs - ckey[i]) - cex[i]) * g.inv_h, g.beta_l2), cu[i]);
+                float2 &hc = sm[cell_slot(0, ts, cs & (G - 1))];
                 hc = cadd(hc, acc);
-            }
-            __syncthreads();
-        }
-        if (threadIdx.x == 0) {
-            for (int j = nmain; j < nr; ++j) {
-                const int st = rpos[j], en = rpos[j + 1];
-                for (int t = 0; t < w; ++t) {
-                    float2 acc = make_float2(0.f, 0.f);
-                    for (int e = st; e < en; ++e)
-                        cfma(acc, es_kernel_fast(((float)t - cex[e]) * g.inv_h, g.beta_l2), cu[e]);
-                    const int c = (ckey[st] + t) & (G - 1);
-                    float2 &hc = sm[cell_slot(0, ts, c)];
-                    hc = cadd(hc, acc);
-                }
             }
         }
         __syncthreads();
