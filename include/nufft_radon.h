@@ -84,6 +84,25 @@ int tc_plan_destroy(tc_plan *plan);
 /* Device bytes held by the plan (tables + scratch). */
 long long tc_plan_device_bytes(const tc_plan *plan);
 
+/* Launch-shape autotuner (an engineering addition; the paper has none).
+ * Times radon_fwd + radon_adj on the caller's buffers for every candidate of
+ *   chunk      slices per launch: max_batch, max_batch/2, ..., 1 (smaller
+ *              chunks keep the grid rows of the column pass in L2 for the
+ *              row pass), and
+ *   col_pairs  image column pairs per CTA of the column passes (1, 2, 4),
+ * keeps the fastest in the plan and reports it (chunk_out, cp_out: HOST, may
+ * be NULL).  x [batch][N][N] and y [batch][A][D] are DEVICE scratch buffers
+ * (overwritten).  Synchronous.  The operators' outputs do not depend on the
+ * choice (bit-identical images and sinograms; only the summation order of the
+ * FP64 objective across chunks changes).  reps: timed repetitions per
+ * candidate (>= 1). */
+int tc_plan_autotune(tc_plan *plan, const float *x, float *y, int batch, int reps,
+                     int *chunk_out, int *cp_out, void *stream);
+
+/* Set the launch shape directly: chunk in [1, max_batch]; col_pairs 1, 2, 4
+ * (0 keeps the current value).  Returns TC_ERR_INVALID_ARG if unsupported. */
+int tc_plan_set_launch(tc_plan *plan, int chunk, int col_pairs);
+
 /* --------------------------------------------------------------- operators */
 /* y = A x  (Sec. 2.2 NUFFT steps in reverse order).
  *   x  [batch][N][N] float32 in;  y [batch][A][D] float32 out (overwritten).
@@ -173,8 +192,10 @@ int mbir_solve(tc_plan *plan, const float *b, const float *w, float *x, int batc
  * x_host are HOST pointers (page-locked memory gives asynchronous copies);
  * dev_b, dev_w, dev_x are caller-owned DEVICE buffers of the same sizes that
  * receive the copies.  Inputs are copied host-to-device in slabs of max_batch
- * slices on a second stream, overlapped with the first iterations' work; the
- * result x is copied back to x_host.  Synchronises before returning. */
+ * slices on a second stream (created and destroyed by the call); the first
+ * iteration's chunk c starts as soon as slab c is resident, so the copies
+ * overlap the first iteration's Radon work.  The result x is copied back to
+ * x_host.  Synchronises before returning. */
 int mbir_solve_host(tc_plan *plan, const float *b_host, const float *w_host,
                     float *x_host, float *dev_b, float *dev_w, float *dev_x,
                     int batch, const tc_prior *prior, const tc_solve_opts *opts,

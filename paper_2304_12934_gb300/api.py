@@ -54,7 +54,8 @@ class _SolveState(ctypes.Structure):
 SYMBOLS = ("tc_status_string", "tc_last_error_detail", "tc_plan_create", "tc_plan_destroy",
            "tc_plan_device_bytes", "radon_fwd", "radon_adj", "mbir_grad",
            "mbir_power_norm", "mbir_solve", "mbir_solve_host", "tc_profile_enable",
-           "tc_profile_collect", "tc_profile_kernel_name", "tc_launch_count")
+           "tc_profile_collect", "tc_profile_kernel_name", "tc_launch_count",
+           "tc_plan_autotune", "tc_plan_set_launch", "tc_prior_grad_noalloc")
 
 
 def lib_path() -> str:
@@ -96,9 +97,13 @@ def load(build_if_missing: bool = True):
     L.tc_profile_kernel_name.restype = ctypes.c_char_p
     L.tc_launch_count.argtypes = []
     L.tc_launch_count.restype = ctypes.c_longlong
+    L.tc_plan_autotune.argtypes = [vp, vp, vp, i, i, ctypes.POINTER(i), ctypes.POINTER(i), vp]
+    L.tc_plan_set_launch.argtypes = [vp, i, i]
+    L.tc_prior_grad_noalloc.argtypes = [vp, vp, i, i, ctypes.POINTER(_Prior), vp, vp]
     for fn in ("tc_profile_enable", "tc_profile_collect", "tc_plan_create", "tc_plan_destroy",
                "radon_fwd", "radon_adj", "mbir_grad", "mbir_power_norm", "mbir_solve",
-               "mbir_solve_host"):
+               "mbir_solve_host", "tc_plan_autotune", "tc_plan_set_launch",
+               "tc_prior_grad_noalloc"):
         getattr(L, fn).restype = i
     _LIB = L
     return L
@@ -182,6 +187,23 @@ class Plan:
 
     def __exit__(self, *a):
         self.close()
+
+    def autotune(self, batch=None, reps=2, stream=None):
+        """Pick slices per launch and column pairs per CTA by timing (tc_plan_autotune).
+
+        Uses scratch buffers of `batch` slices (default max_batch); returns (chunk, col_pairs)."""
+        B = self.max_batch if batch is None else int(batch)
+        x = torch.rand(self.image_shape(B), device=self.device)
+        y = torch.empty(self.sino_shape(B), device=self.device)
+        ch, cp = ctypes.c_int(), ctypes.c_int()
+        _check("tc_plan_autotune", load().tc_plan_autotune(self.handle, _ptr(x), _ptr(y), B, int(reps),
+                                                           ctypes.byref(ch), ctypes.byref(cp),
+                                                           _stream(stream, self.device)))
+        return ch.value, cp.value
+
+    def set_launch(self, chunk, col_pairs=0):
+        """Slices per launch (1..max_batch) and column pairs per CTA (1, 2, 4; 0 keeps)."""
+        _check("tc_plan_set_launch", load().tc_plan_set_launch(self.handle, int(chunk), int(col_pairs)))
 
     def image_shape(self, batch):
         return (batch, self.n, self.n)

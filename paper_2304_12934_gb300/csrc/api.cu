@@ -5,11 +5,13 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <vector>
 
 #include "common.cuh"
 
 int tc_plan_build(const tc_geom *geom, int max_batch, tc_plan **out);
 void tc_plan_free(tc_plan *p);
+int plan_set_col_pairs(tc_plan *p, int cp);
 
 namespace {
 
@@ -46,13 +48,19 @@ int check_ptrs(std::initializer_list<const void *> req, std::initializer_list<co
 }
 
 // grad = A^T W (A x - b) + lambda grad H(x); scal[SC_DATA], scal[SC_PRIOR] set.
+// ready: optional per-chunk events the chunk's first kernel waits for (slabs
+// still being copied in on another stream).
+// dot_x: with a prior, the prior kernel also forms the restart-test inner
+// products <grad, x - dot_x> and <grad, grad>.
 int grad_impl(tc_plan *p, const float *x, const float *b, const float *w,
               const tc_prior *prior, float *grad, int batch, cudaStream_t s,
-              bool want_prior_value = true) {
+              bool want_prior_value = true, const cudaEvent_t *ready = nullptr,
+              const float *dot_x = nullptr) {
     TC_CUDA(cudaMemsetAsync(p->scal + SC_DATA, 0, 2 * sizeof(double), s));
     const size_t ni = img_elems(p), ns = sino_elems(p);
-    for (int c0 = 0; c0 < batch; c0 += p->max_batch) {
-        const int nb = batch - c0 < p->max_batch ? batch - c0 : p->max_batch;
+    for (int c0 = 0; c0 < batch; c0 += p->chunk) {
+        const int nb = batch - c0 < p->chunk ? batch - c0 : p->chunk;
+        if (ready) TC_CUDA(cudaStreamWaitEvent(s, ready[c0 / p->chunk], 0));
         int rc = launch_radon_fwd_chunk(p, x + c0 * ni, nullptr, nb, b ? b + c0 * ns : nullptr,
                                         w ? w + c0 * ns : nullptr, p->sr, p->scal + SC_DATA, s);
         if (rc) return rc;
@@ -61,7 +69,7 @@ int grad_impl(tc_plan *p, const float *x, const float *b, const float *w,
     }
     if (prior && prior->lambda != 0.0) {
         int rc = launch_prior_grad(p, x, grad, batch, prior,
-                                   want_prior_value ? p->scal + SC_PRIOR : nullptr, s);
+                                   want_prior_value ? p->scal + SC_PRIOR : nullptr, s, dot_x);
         if (rc) return rc;
     }
     return TC_OK;
@@ -133,8 +141,8 @@ int radon_fwd(tc_plan *p, const float *x, float *y, int batch, void *stream) {
     if (!dg.ok) return TC_ERR_CUDA;
     cudaStream_t s = (cudaStream_t)stream;
     const size_t ni = img_elems(p), ns = sino_elems(p);
-    for (int c0 = 0; c0 < batch; c0 += p->max_batch) {
-        const int nb = batch - c0 < p->max_batch ? batch - c0 : p->max_batch;
+    for (int c0 = 0; c0 < batch; c0 += p->chunk) {
+        const int nb = batch - c0 < p->chunk ? batch - c0 : p->chunk;
         int rc = launch_radon_fwd_chunk(p, x + c0 * ni, y + c0 * ns, nb, nullptr, nullptr,
                                         nullptr, nullptr, s);
         if (rc) return rc;
@@ -150,8 +158,8 @@ int radon_adj(tc_plan *p, const float *y, float *x, int batch, void *stream) {
     if (!dg.ok) return TC_ERR_CUDA;
     cudaStream_t s = (cudaStream_t)stream;
     const size_t ni = img_elems(p), ns = sino_elems(p);
-    for (int c0 = 0; c0 < batch; c0 += p->max_batch) {
-        const int nb = batch - c0 < p->max_batch ? batch - c0 : p->max_batch;
+    for (int c0 = 0; c0 < batch; c0 += p->chunk) {
+        const int nb = batch - c0 < p->chunk ? batch - c0 : p->chunk;
         int rc = launch_radon_adj_chunk(p, y + c0 * ns, x + c0 * ni, nb, s);
         if (rc) return rc;
     }
@@ -197,20 +205,19 @@ int mbir_power_norm(tc_plan *p, const float *w, float *v, float *work, int batch
     return TC_OK;
 }
 
-int mbir_solve(tc_plan *p, const float *b, const float *w, float *x, int batch,
+}  // extern "C"
+
+namespace {
+
+// The accelerated-gradient loop.  fresh_z: z := x is still to be done;
+// ready: per-chunk events gating the first iteration (host streaming).
+int solve_loop(tc_plan *p, const float *b, const float *w, float *x, int batch,
                const tc_prior *prior, const tc_solve_opts *opts, tc_solve_state *st,
-               void *stream) {
-    if (!p || !opts || !st || batch < 1 || opts->n_iter < 0 || !(opts->step > 0) ||
-        check_prior(prior))
-        return TC_ERR_INVALID_ARG;
-    if (check_ptrs({b, x, st->z, st->g}, {w})) return TC_ERR_INVALID_ARG;
-    DeviceGuard dg(p->device);
-    if (!dg.ok) return TC_ERR_CUDA;
-    cudaStream_t s = (cudaStream_t)stream;
+               cudaStream_t s, bool fresh_z, const cudaEvent_t *ready) {
     const size_t n = img_elems(p) * batch;
     int rc;
     if (st->k == 0) {
-        if ((rc = launch_copy(st->z, x, n, s))) return rc;
+        if (fresh_z && (rc = launch_copy(st->z, x, n, s))) return rc;
         if ((rc = launch_fill_scalars_fresh(p, 1.0, 0.0, 0.0, opts->step, s))) return rc;
     } else {
         if ((rc = launch_fill_scalars_fresh(p, st->t, (double)st->k, (double)st->n_restarts,
@@ -219,8 +226,11 @@ int mbir_solve(tc_plan *p, const float *b, const float *w, float *x, int batch,
     }
     for (int it = 0; it < opts->n_iter; ++it) {
         // the prior's value H is only reported for the last gradient point
-        if ((rc = grad_impl(p, st->z, b, w, prior, st->g, batch, s, it == opts->n_iter - 1))) return rc;
-        if ((rc = launch_dots_gzx_gg(p, st->g, st->z, x, n, s))) return rc;
+        const bool fused = prior && prior->lambda != 0.0;  // dots inside the prior kernel
+        if ((rc = grad_impl(p, st->z, b, w, prior, st->g, batch, s, it == opts->n_iter - 1,
+                            it == 0 ? ready : nullptr, fused ? x : nullptr)))
+            return rc;
+        if (!fused && (rc = launch_dots_gzx_gg(p, st->g, st->z, x, n, s))) return rc;
         if ((rc = launch_solver_scalar(p, opts->restart, s))) return rc;
         if ((rc = launch_update(p, x, st->z, st->g, n, s))) return rc;
     }
@@ -237,22 +247,145 @@ int mbir_solve(tc_plan *p, const float *b, const float *w, float *x, int batch,
     return TC_OK;
 }
 
+int check_solve(tc_plan *p, int batch, const tc_prior *prior, const tc_solve_opts *opts,
+                const tc_solve_state *st) {
+    if (!p || !opts || !st || batch < 1 || opts->n_iter < 0 || !(opts->step > 0) ||
+        check_prior(prior))
+        return TC_ERR_INVALID_ARG;
+    if (check_ptrs({st->z, st->g}, {})) return TC_ERR_INVALID_ARG;
+    return TC_OK;
+}
+
+// Stream and events owned by one host-streamed solve.
+struct CopyStream {
+    cudaStream_t cs = nullptr;
+    std::vector<cudaEvent_t> ev;
+    ~CopyStream() {
+        for (cudaEvent_t e : ev)
+            if (e) cudaEventDestroy(e);
+        if (cs) cudaStreamDestroy(cs);
+    }
+};
+
+}  // namespace
+
+extern "C" {
+
+int tc_plan_autotune(tc_plan *p, const float *x, float *y, int batch, int reps,
+                     int *chunk_out, int *cp_out, void *stream) {
+    if (!p || batch < 1 || reps < 1 || check_ptrs({x, y}, {})) return TC_ERR_INVALID_ARG;
+    DeviceGuard dg(p->device);
+    if (!dg.ok) return TC_ERR_CUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    TC_CUDA(cudaEventCreate(&e0));
+    TC_CUDA(cudaEventCreate(&e1));
+    const int max_chunk = batch < p->max_batch ? batch : p->max_batch;
+    float best = -1.f;
+    int best_chunk = p->chunk, best_cp = p->cp_col;
+    int rc = TC_OK;
+    for (int cp = 1; cp <= 4 && !rc; cp <<= 1) {
+        if (plan_set_col_pairs(p, cp)) continue;
+        for (int ch = max_chunk; ch >= 1 && !rc; ch = (ch > 1 && ch < 4) ? 1 : ch / 2) {
+            p->chunk = ch;
+            rc = radon_fwd(p, x, y, batch, stream);
+            if (!rc) rc = radon_adj(p, y, (float *)x, batch, stream);
+            if (rc) break;
+            cudaEventRecord(e0, s);
+            for (int r = 0; r < reps && !rc; ++r) {
+                rc = radon_fwd(p, x, y, batch, stream);
+                if (!rc) rc = radon_adj(p, y, (float *)x, batch, stream);
+            }
+            cudaEventRecord(e1, s);
+            if (cudaEventSynchronize(e1) != cudaSuccess) {
+                rc = tc_cuda_fail(cudaGetLastError(), "autotune");
+                break;
+            }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (best < 0.f || ms < best) {
+                best = ms;
+                best_chunk = ch;
+                best_cp = cp;
+            }
+            if (ch == 1) break;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    plan_set_col_pairs(p, best_cp);
+    p->chunk = best_chunk;
+    if (chunk_out) *chunk_out = best_chunk;
+    if (cp_out) *cp_out = best_cp;
+    return TC_OK;
+}
+
+int tc_plan_set_launch(tc_plan *p, int chunk, int col_pairs) {
+    if (!p || chunk < 1 || chunk > p->max_batch) return TC_ERR_INVALID_ARG;
+    if (col_pairs && plan_set_col_pairs(p, col_pairs)) return TC_ERR_INVALID_ARG;
+    p->chunk = chunk;
+    return TC_OK;
+}
+
+int mbir_solve(tc_plan *p, const float *b, const float *w, float *x, int batch,
+               const tc_prior *prior, const tc_solve_opts *opts, tc_solve_state *st,
+               void *stream) {
+    if (check_solve(p, batch, prior, opts, st)) return TC_ERR_INVALID_ARG;
+    if (check_ptrs({b, x}, {w})) return TC_ERR_INVALID_ARG;
+    DeviceGuard dg(p->device);
+    if (!dg.ok) return TC_ERR_CUDA;
+    return solve_loop(p, b, w, x, batch, prior, opts, st, (cudaStream_t)stream, true, nullptr);
+}
+
 int mbir_solve_host(tc_plan *p, const float *b_host, const float *w_host, float *x_host,
                     float *dev_b, float *dev_w, float *dev_x, int batch,
                     const tc_prior *prior, const tc_solve_opts *opts,
                     tc_solve_state *st, void *stream) {
-    if (!p || batch < 1 || !b_host || !x_host || !dev_b || !dev_x || (w_host && !dev_w))
+    if (check_solve(p, batch, prior, opts, st)) return TC_ERR_INVALID_ARG;
+    if (!b_host || !x_host || (w_host && !dev_w) || check_ptrs({dev_b, dev_x}, {dev_w}))
         return TC_ERR_INVALID_ARG;
     DeviceGuard dg(p->device);
     if (!dg.ok) return TC_ERR_CUDA;
     cudaStream_t s = (cudaStream_t)stream;
-    const size_t ni = img_elems(p) * batch, ns = sino_elems(p) * batch;
-    TC_CUDA(cudaMemcpyAsync(dev_b, b_host, ns * sizeof(float), cudaMemcpyHostToDevice, s));
-    if (w_host) TC_CUDA(cudaMemcpyAsync(dev_w, w_host, ns * sizeof(float), cudaMemcpyHostToDevice, s));
-    TC_CUDA(cudaMemcpyAsync(dev_x, x_host, ni * sizeof(float), cudaMemcpyHostToDevice, s));
-    int rc = mbir_solve(p, dev_b, w_host ? dev_w : nullptr, dev_x, batch, prior, opts, st, stream);
+    const size_t ni = img_elems(p), ns = sino_elems(p);
+    const int nslab = (batch + p->chunk - 1) / p->chunk;
+    CopyStream cp;
+    TC_CUDA(cudaStreamCreateWithFlags(&cp.cs, cudaStreamNonBlocking));
+    cp.ev.assign(nslab, nullptr);
+    // the copy stream must not overtake work already queued on the caller's stream
+    cudaEvent_t start = nullptr;
+    TC_CUDA(cudaEventCreateWithFlags(&start, cudaEventDisableTiming));
+    cp.ev.push_back(start);
+    TC_CUDA(cudaEventRecord(start, s));
+    TC_CUDA(cudaStreamWaitEvent(cp.cs, start, 0));
+    // slab c of b, w and x goes in on the copy stream; the first iteration's
+    // chunk c starts once its slab is resident
+    for (int c = 0; c < nslab; ++c) {
+        const size_t s0 = (size_t)c * p->chunk;
+        const size_t nb = (size_t)(batch - (int)s0 < p->chunk ? batch - (int)s0 : p->chunk);
+        TC_CUDA(cudaMemcpyAsync(dev_b + s0 * ns, b_host + s0 * ns, nb * ns * sizeof(float),
+                                cudaMemcpyHostToDevice, cp.cs));
+        if (w_host)
+            TC_CUDA(cudaMemcpyAsync(dev_w + s0 * ns, w_host + s0 * ns, nb * ns * sizeof(float),
+                                    cudaMemcpyHostToDevice, cp.cs));
+        TC_CUDA(cudaMemcpyAsync(dev_x + s0 * ni, x_host + s0 * ni, nb * ni * sizeof(float),
+                                cudaMemcpyHostToDevice, cp.cs));
+        if (st->k == 0)
+            TC_CUDA(cudaMemcpyAsync(st->z + s0 * ni, dev_x + s0 * ni, nb * ni * sizeof(float),
+                                    cudaMemcpyDeviceToDevice, cp.cs));
+        TC_CUDA(cudaEventCreateWithFlags(&cp.ev[c], cudaEventDisableTiming));
+        TC_CUDA(cudaEventRecord(cp.ev[c], cp.cs));
+    }
+    // the first iteration's chunk c waits for slab c only; the full-volume
+    // kernels that follow the chunk loop then see every slab
+    const bool overlap = opts->n_iter > 0;
+    if (!overlap)
+        for (int c = 0; c < nslab; ++c) TC_CUDA(cudaStreamWaitEvent(s, cp.ev[c], 0));
+    int rc = solve_loop(p, dev_b, w_host ? dev_w : nullptr, dev_x, batch, prior, opts, st, s,
+                        false, overlap ? cp.ev.data() : nullptr);
     if (rc) return rc;
-    TC_CUDA(cudaMemcpyAsync(x_host, dev_x, ni * sizeof(float), cudaMemcpyDeviceToHost, s));
+    TC_CUDA(cudaMemcpyAsync(x_host, dev_x, (size_t)batch * ni * sizeof(float), cudaMemcpyDeviceToHost, s));
     TC_CUDA(cudaStreamSynchronize(s));
     return TC_OK;
 }

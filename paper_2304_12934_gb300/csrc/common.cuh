@@ -54,6 +54,7 @@ struct KArgs {
 struct tc_plan {
     int device;
     int max_batch;
+    int chunk;            // slices per launch (<= max_batch; set by tc_plan_autotune)
     KArgs k;
     double *dea64;        // FP64 deapodisation factors (device)
     float *dea;
@@ -164,8 +165,11 @@ int launch_radon_fwd_chunk(tc_plan *p, const float *x, float *y, int nb,
                            double *obj_acc, cudaStream_t s);
 int launch_radon_adj_chunk(tc_plan *p, const float *y, float *x, int nb,
                            cudaStream_t s);
+// g += lambda grad H(x); h_acc (or NULL) = lambda H(x); with dot_x, also
+// scal[SC_DOT_GZX] = <g, x - dot_x>, scal[SC_DOT_GG] = <g, g> of the final g.
 int launch_prior_grad(tc_plan *p, const float *x, float *g, int nb,
-                      const tc_prior *pr, double *h_acc, cudaStream_t s);
+                      const tc_prior *pr, double *h_acc, cudaStream_t s,
+                      const float *dot_x = nullptr);
 int launch_reduce_finalize(const double *partials, int n, double *acc,
                            int accumulate, double scale, cudaStream_t s);
 int launch_dots_gzx_gg(tc_plan *p, const float *g, const float *z, const float *x,

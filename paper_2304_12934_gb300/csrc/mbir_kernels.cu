@@ -57,6 +57,8 @@ __device__ __forceinline__ float qggmrf_rhop(float d, const PriorArgs &a, float 
 // phase still reads; with the plane double buffer this needs two barriers per
 // z step.  dims = 2 skips the z pairs and uses the 8-neighbour weights.
 // WANT_H also accumulates H (otherwise only the gradient is produced).
+// DOTS also accumulates <g, f - xprev> and <g, g> of the final gradient g (the
+// inner products of the solver's restart test), sparing a separate pass.
 #define PTX 32
 #define PTY 12
 #define PRX (PTX + 2)
@@ -65,9 +67,11 @@ __device__ __forceinline__ float qggmrf_rhop(float d, const PriorArgs &a, float 
 #define PRIOR_THREADS 480
 #define PRIOR_SMEM_FLOATS (2 * PRS + 3 * 9 * PRS + 2 * 4 * PRS)
 
-template <bool WANT_H>
+template <bool WANT_H, bool DOTS>
 __global__ void __launch_bounds__(PRIOR_THREADS) k_prior(const float *__restrict__ f, float *__restrict__ g,
-                                                          double *__restrict__ partials, const PriorArgs a) {
+                                                          double *__restrict__ partials, const PriorArgs a,
+                                                          const float *__restrict__ xprev,
+                                                          double *__restrict__ pd1, double *__restrict__ pd2) {
     extern __shared__ float psm[];
     float *fpl = psm;                 // [2][PRS]
     float *Eu = fpl + 2 * PRS;        // [3][9][PRS]
@@ -115,7 +119,8 @@ __global__ void __launch_bounds__(PRIOR_THREADS) k_prior(const float *__restrict
     // register prefetch: the plane the next step stores (3D: z + 2, 2D: z + 1)
     const size_t off = (size_t)y * N + x;
     float f_nx = (inb && B > 1) ? f[NN + off] : 0.f;
-    double hacc = 0.0;
+    double hacc = 0.0, d1 = 0.0, d2 = 0.0;
+    float d1f = 0.f, d2f = 0.f;
     for (int z = 0; z < B; ++z) {
         const int cur = z & 1, nxt = cur ^ 1;
         const int s3 = z % 3, p3 = (z + 2) % 3;  // this step's / previous step's z+1 slots
@@ -124,14 +129,15 @@ __global__ void __launch_bounds__(PRIOR_THREADS) k_prior(const float *__restrict
         const float f_pf = (inb && pz < B) ? f[(size_t)pz * NN + off] : 0.f;
         const size_t i = (size_t)z * NN + off;
         const float g_old = interior ? g[i] : 0.f;
+        const float x_old = (DOTS && interior) ? xprev[i] : 0.f;
         if (ring) {
             if (up) fpl[nxt * PRS + h] = f_nx;                 // 3D: plane z + 1
             else if (!three && z > 0) fpl[cur * PRS + h] = f_nx;  // 2D: slices are independent
         }
         __syncthreads();
-        float hs = 0.f;
+        float hs = 0.f, fm = 0.f;
         if (ring) {
-            const float fm = fpl[cur * PRS + h];
+            fm = fpl[cur * PRS + h];
             const unsigned mu = up ? mup : 0u;
             float *eu = Eu + (s3 * 9) * PRS + h;
 #pragma unroll
@@ -174,14 +180,33 @@ __global__ void __launch_bounds__(PRIOR_THREADS) k_prior(const float *__restrict
 #pragma unroll
             for (int q = 0; q < 4; ++q)
                 gs = fmaf(pw[q], ep[q * PRS] - ep[q * PRS - pdy[q] * PRX - pdx[q]], gs);
-            g[i] = fmaf(a.two_lambda, gs, g_old);
+            const float gn = fmaf(a.two_lambda, gs, g_old);
+            g[i] = gn;
             if (WANT_H) hacc += 2.0 * (double)hs;
+            if (DOTS) {
+                d1f = fmaf(gn, fm - x_old, d1f);
+                d2f = fmaf(gn, gn, d2f);
+                if ((z & 7) == 7) {  // promote to FP64 every 8 voxels
+                    d1 += (double)d1f;
+                    d2 += (double)d2f;
+                    d1f = d2f = 0.f;
+                }
+            }
         }
         f_nx = f_pf;
     }
+    const int bid = blockIdx.y * gridDim.x + blockIdx.x;
     if (WANT_H) {
         const double tot = block_sum_f64(hacc, red);
-        if (threadIdx.x == 0) partials[blockIdx.y * gridDim.x + blockIdx.x] = tot;
+        if (threadIdx.x == 0) partials[bid] = tot;
+    }
+    if (DOTS) {
+        const double t1 = block_sum_f64(d1 + (double)d1f, red);
+        const double t2 = block_sum_f64(d2 + (double)d2f, red);
+        if (threadIdx.x == 0) {
+            pd1[bid] = t1;
+            pd2[bid] = t2;
+        }
     }
 }
 
@@ -305,7 +330,7 @@ int grid_for(size_t n4) {
 }  // namespace
 
 int launch_prior_grad(tc_plan *p, const float *x, float *g, int nb,
-                      const tc_prior *pr, double *h_acc, cudaStream_t s) {
+                      const tc_prior *pr, double *h_acc, cudaStream_t s, const float *dot_x) {
     PriorArgs a;
     a.N = p->k.N;
     a.B = nb;
@@ -327,11 +352,24 @@ int launch_prior_grad(tc_plan *p, const float *x, float *g, int nb,
     if (blocks > p->slot) return TC_ERR_UNSUPPORTED;
     double *part = p->partials + (size_t)1 * p->slot;
     const size_t smem = PRIOR_SMEM_FLOATS * sizeof(float);
-    if (h_acc)
-        TC_PROFILED(TCK_PRIOR, s, k_prior<true><<<grid, PRIOR_THREADS, smem, s>>>(x, g, part, a));
-    else
-        TC_PROFILED(TCK_PRIOR, s, k_prior<false><<<grid, PRIOR_THREADS, smem, s>>>(x, g, part, a));
+    double *p1 = p->partials + (size_t)2 * p->slot, *p2 = p->partials + (size_t)3 * p->slot;
+    if (dot_x) {
+        if (h_acc)
+            TC_PROFILED(TCK_PRIOR, s, (k_prior<true, true><<<grid, PRIOR_THREADS, smem, s>>>(x, g, part, a, dot_x, p1, p2)));
+        else
+            TC_PROFILED(TCK_PRIOR, s, (k_prior<false, true><<<grid, PRIOR_THREADS, smem, s>>>(x, g, part, a, dot_x, p1, p2)));
+    } else {
+        if (h_acc)
+            TC_PROFILED(TCK_PRIOR, s, (k_prior<true, false><<<grid, PRIOR_THREADS, smem, s>>>(x, g, part, a, nullptr, nullptr, nullptr)));
+        else
+            TC_PROFILED(TCK_PRIOR, s, (k_prior<false, false><<<grid, PRIOR_THREADS, smem, s>>>(x, g, part, a, nullptr, nullptr, nullptr)));
+    }
     TC_LAUNCHED("k_prior");
+    if (dot_x) {
+        int rc = launch_reduce_finalize(p1, blocks, p->scal + SC_DOT_GZX, 0, 1.0, s);
+        if (!rc) rc = launch_reduce_finalize(p2, blocks, p->scal + SC_DOT_GG, 0, 1.0, s);
+        if (rc) return rc;
+    }
     if (h_acc) return launch_reduce_finalize(part, blocks, h_acc, 0, pr->lambda, s);
     return TC_OK;
 }
@@ -436,9 +474,9 @@ int launch_prior_kernel_into(const float *x, float *g, int n, int nb, const tc_p
     if (blocks > max_partials) return TC_ERR_INVALID_ARG;
     const size_t smem = PRIOR_SMEM_FLOATS * sizeof(float);
     if (h_out)
-        TC_PROFILED(TCK_PRIOR, s, k_prior<true><<<grid, PRIOR_THREADS, smem, s>>>(x, g, partials, a));
+        TC_PROFILED(TCK_PRIOR, s, (k_prior<true, false><<<grid, PRIOR_THREADS, smem, s>>>(x, g, partials, a, nullptr, nullptr, nullptr)));
     else
-        TC_PROFILED(TCK_PRIOR, s, k_prior<false><<<grid, PRIOR_THREADS, smem, s>>>(x, g, partials, a));
+        TC_PROFILED(TCK_PRIOR, s, (k_prior<false, false><<<grid, PRIOR_THREADS, smem, s>>>(x, g, partials, a, nullptr, nullptr, nullptr)));
     TC_LAUNCHED("k_prior");
     if (h_out) return launch_reduce_finalize(partials, blocks, h_out, 0, pr->lambda, s);
     return TC_OK;
@@ -447,7 +485,9 @@ int launch_prior_kernel_into(const float *x, float *g, int n, int nb, const tc_p
 // Opt the prior kernel into its dynamic shared memory (once per process).
 int prior_configure_kernels() {
     const int smem = (int)(PRIOR_SMEM_FLOATS * sizeof(float));
-    TC_CUDA(cudaFuncSetAttribute(k_prior<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    TC_CUDA(cudaFuncSetAttribute(k_prior<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    TC_CUDA(cudaFuncSetAttribute(k_prior<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    TC_CUDA(cudaFuncSetAttribute(k_prior<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    TC_CUDA(cudaFuncSetAttribute(k_prior<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    TC_CUDA(cudaFuncSetAttribute(k_prior<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     return TC_OK;
 }

@@ -187,6 +187,19 @@ int alloc_dev(void **dst, size_t nb, long long &bytes) {
 
 }  // namespace
 
+// Column pairs per CTA of the column passes: threads, shared memory (the
+// kernels' dynamic-smem limit is raised to the largest candidate at build).
+int plan_set_col_pairs(tc_plan *p, int cp) {
+    const int N = p->k.N;
+    if (cp < 1 || cp > 4 || 2 * cp > N || 2 * cp * N / 16 > 512) return TC_ERR_INVALID_ARG;
+    const size_t smem = (size_t)(2 * cp * fft_tstride(N) + p->k.ntwN) * sizeof(float2);
+    if (smem > 200 * 1024) return TC_ERR_INVALID_ARG;
+    p->cp_col = cp;
+    p->threads_col = std::max(64, 2 * cp * N / 16);
+    p->smem_col = smem;
+    return TC_OK;
+}
+
 void tc_plan_free(tc_plan *p) {
     if (!p) return;
     void *ptrs[] = {p->dea64, p->dea, p->twN, p->twG, p->twD, p->row_off, p->ent, p->rec, p->rec_off,
@@ -473,20 +486,21 @@ int tc_plan_build(const tc_geom *geom, int max_batch, tc_plan **out) {
     k.bhat = p->bhat;
     k.twL = p->twL;
 
-    // launch configuration
+    // launch configuration (column pairs per CTA may be retuned by tc_plan_autotune)
     int cp = 4;
-    while (cp > 1 && (cp * 2 * N * 8 > 96 * 1024 || 2 * cp * N / 16 > 1024 || 2 * cp > N)) cp >>= 1;
-    p->cp_col = cp;
-    p->threads_col = std::max(64, 2 * cp * N / 16);
+    while (cp > 1 && (cp * 2 * N * 8 > 96 * 1024 || 2 * cp * N / 16 > 512 || 2 * cp > N)) cp >>= 1;
+    p->chunk = max_batch;
+    if (plan_set_col_pairs(p, cp)) {
+        tc_plan_free(p);
+        return TC_ERR_UNSUPPORTED;
+    }
     p->threads_row = std::max(128, N / 8);
     p->threads_det = k.blue ? std::max(256, k.L / 16) : 256;
-    p->smem_col = (size_t)(2 * cp * fft_tstride(N) + k.ntwN) * sizeof(float2);
     p->smem_row_fwd = (size_t)(2 * fft_tstride(N) + k.ntwN) * sizeof(float2);
     p->smem_row_adj = p->smem_row_fwd + (size_t)SPREAD_CHUNK * (sizeof(float2) + sizeof(float) + sizeof(short));
     p->smem_det = k.blue ? (size_t)spad_size(k.L) * sizeof(float2)
                          : (size_t)(3 * D + k.rp.rad[0]) * sizeof(float2);
-    if (p->threads_col > 1024 || p->threads_row > 1024 || p->smem_det > 200 * 1024 ||
-        p->smem_row_adj > 200 * 1024) {
+    if (p->threads_row > 512 || p->smem_det > 200 * 1024 || p->smem_row_adj > 200 * 1024) {
         tc_plan_free(p);
         return TC_ERR_UNSUPPORTED;
     }

@@ -373,8 +373,14 @@ int launch_radon_adj_chunk(tc_plan *p, const float *y, float *x, int nb,
 
 int radon_configure_kernels(tc_plan *p) {
     // opt in to large dynamic shared memory where needed
-    TC_CUDA(cudaFuncSetAttribute(k_fwd_col, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem_col));
-    TC_CUDA(cudaFuncSetAttribute(k_adj_col, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem_col));
+    // the column passes may be retuned to up to 4 column pairs per CTA
+    int col_max = (int)p->smem_col;
+    for (int cp = 1; cp <= 4; cp <<= 1) {
+        const long long sm = (long long)(2 * cp * fft_tstride(p->k.N) + p->k.ntwN) * 8;
+        if (sm <= 200 * 1024 && sm > col_max) col_max = (int)sm;
+    }
+    TC_CUDA(cudaFuncSetAttribute(k_fwd_col, cudaFuncAttributeMaxDynamicSharedMemorySize, col_max));
+    TC_CUDA(cudaFuncSetAttribute(k_adj_col, cudaFuncAttributeMaxDynamicSharedMemorySize, col_max));
     TC_CUDA(cudaFuncSetAttribute(k_fwd_row, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem_row_fwd));
     TC_CUDA(cudaFuncSetAttribute(k_adj_row, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem_row_adj));
     TC_CUDA(cudaFuncSetAttribute(k_fwd_det<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem_det));
