@@ -123,7 +123,8 @@ __host__ __device__ __forceinline__ int fft_tstride(int n) {
 // Per-stage twiddle tables of a length-n FFT (n = 2^log2n), concatenated for
 // the stages after the first: stage (Ns, R) holds W_n^(q k n / (Ns R)) at
 // [(q - 1) * Ns + k], q = 1..R-1, k = 0..Ns-1, so the lanes of a warp (k
-// consecutive) read consecutive words.  Total entries: fft_twiddle_count(n).
+// consecutive) read consecutive words (coalesced global / L1 reads).  Total
+// entries: fft_twiddle_count(n).
 __host__ __device__ __forceinline__ int fft_twiddle_count(int log2n) {
     int logNs = 0, total = 0;
     while (log2n - logNs > 0) {

@@ -482,12 +482,22 @@ int launch_prior_kernel_into(const float *x, float *g, int n, int nb, const tc_p
     return TC_OK;
 }
 
-// Opt the prior kernel into its dynamic shared memory (once per process).
+// Opt the prior kernel into its dynamic shared memory (raise only: the limit
+// is a process-wide attribute of the kernel).
+template <class F>
+int raise_prior_smem(F *fn, int smem) {
+    cudaFuncAttributes at;
+    TC_CUDA(cudaFuncGetAttributes(&at, fn));
+    if (at.maxDynamicSharedSizeBytes < smem)
+        TC_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    return TC_OK;
+}
+
 int prior_configure_kernels() {
     const int smem = (int)(PRIOR_SMEM_FLOATS * sizeof(float));
-    TC_CUDA(cudaFuncSetAttribute(k_prior<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    TC_CUDA(cudaFuncSetAttribute(k_prior<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    TC_CUDA(cudaFuncSetAttribute(k_prior<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    TC_CUDA(cudaFuncSetAttribute(k_prior<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    int rc;
+    if ((rc = raise_prior_smem(k_prior<true, false>, smem)) || (rc = raise_prior_smem(k_prior<false, false>, smem)) ||
+        (rc = raise_prior_smem(k_prior<true, true>, smem)) || (rc = raise_prior_smem(k_prior<false, true>, smem)))
+        return rc;
     return TC_OK;
 }

@@ -192,7 +192,7 @@ int alloc_dev(void **dst, size_t nb, long long &bytes) {
 int plan_set_col_pairs(tc_plan *p, int cp) {
     const int N = p->k.N;
     if (cp < 1 || cp > 4 || 2 * cp > N || 2 * cp * N / 16 > 512) return TC_ERR_INVALID_ARG;
-    const size_t smem = (size_t)(2 * cp * fft_tstride(N) + p->k.ntwN) * sizeof(float2);
+    const size_t smem = (size_t)(2 * cp * fft_tstride(N)) * sizeof(float2);
     if (smem > 200 * 1024) return TC_ERR_INVALID_ARG;
     p->cp_col = cp;
     p->threads_col = std::max(64, 2 * cp * N / 16);
@@ -496,7 +496,7 @@ int tc_plan_build(const tc_geom *geom, int max_batch, tc_plan **out) {
     }
     p->threads_row = std::max(128, N / 8);
     p->threads_det = k.blue ? std::max(256, k.L / 16) : 256;
-    p->smem_row_fwd = (size_t)(2 * fft_tstride(N) + k.ntwN) * sizeof(float2);
+    p->smem_row_fwd = (size_t)(2 * fft_tstride(N)) * sizeof(float2);
     p->smem_row_adj = p->smem_row_fwd + (size_t)SPREAD_CHUNK * (sizeof(float2) + sizeof(float) + sizeof(short));
     p->smem_det = k.blue ? (size_t)spad_size(k.L) * sizeof(float2)
                          : (size_t)(3 * D + k.rp.rad[0]) * sizeof(float2);

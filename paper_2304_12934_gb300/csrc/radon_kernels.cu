@@ -35,12 +35,10 @@ __device__ __forceinline__ int cell_slot(int t0, int ts, int c) {
 // ------------------------------------------------------------ forward ------
 __global__ void __launch_bounds__(512) k_fwd_col(const float *__restrict__ x, float2 *__restrict__ T,
                           const KArgs g, int CP) {
-    extern __shared__ float2 sm[];  // 2CP transforms (stride ts), then the twiddle tables
+    extern __shared__ float2 sm[];  // 2CP transforms (stride ts)
     const int N = g.N, b = blockIdx.y, ts = fft_tstride(N);
     const int x0base = blockIdx.x * CP * 2;
     const float *xs = x + (size_t)b * N * N;
-    float2 *tws = sm + 2 * CP * ts;
-    for (int i = threadIdx.x; i < g.ntwN; i += blockDim.x) tws[i] = g.twN[i];
     for (int idx = threadIdx.x; idx < N * CP; idx += blockDim.x) {
         const int pp = idx % CP, iy = idx / CP;
         const int xc = x0base + 2 * pp;
@@ -52,7 +50,7 @@ __global__ void __launch_bounds__(512) k_fwd_col(const float *__restrict__ x, fl
         sm[(pp * 2 + 1) * ts + spad(q)] = cmul(z, g.twG[iy]);
     }
     __syncthreads();
-    fft_pow2<-1>(sm, N, g.log2N, 2 * CP, ts, tws);
+    fft_pow2<-1>(sm, N, g.log2N, 2 * CP, ts, g.twN);
     float2 *Tb = T + (size_t)b * g.R * N;
     const int Gm = g.G - 1;
     for (int idx = threadIdx.x; idx < g.R * CP; idx += blockDim.x) {
@@ -72,11 +70,9 @@ __global__ void __launch_bounds__(512) k_fwd_col(const float *__restrict__ x, fl
 
 __global__ void __launch_bounds__(512) k_fwd_row(const float2 *__restrict__ T, float2 *__restrict__ P,
                           const KArgs g) {
-    extern __shared__ float2 sm[];  // 2 transforms (stride ts), then the twiddle tables
+    extern __shared__ float2 sm[];  // 2 transforms (stride ts)
     const int N = g.N, r = blockIdx.x, b = blockIdx.y, ts = fft_tstride(N);
     const float2 *Tr = T + ((size_t)b * g.R + r) * N;
-    float2 *tws = sm + 2 * ts;
-    for (int i = threadIdx.x; i < g.ntwN; i += blockDim.x) tws[i] = g.twN[i];
     for (int ix = threadIdx.x; ix < N; ix += blockDim.x) {
         const float2 v = Tr[ix];
         const int q = (ix - N / 2) & (N - 1);
@@ -84,7 +80,7 @@ __global__ void __launch_bounds__(512) k_fwd_row(const float2 *__restrict__ T, f
         sm[ts + spad(q)] = cmul(v, g.twG[ix]);
     }
     __syncthreads();
-    fft_pow2<-1>(sm, N, g.log2N, 2, ts, tws);
+    fft_pow2<-1>(sm, N, g.log2N, 2, ts, g.twN);
     float2 *Pb = P + (size_t)b * g.w * g.AM;
     const int e1 = g.row_off[r + 1];
     const int Gm = g.G - 1;
@@ -233,13 +229,11 @@ __global__ void __launch_bounds__(512) k_adj_row(const float2 *__restrict__ V, f
     extern __shared__ float2 sm[];
     const int N = g.N, G = g.G, r = blockIdx.x, b = blockIdx.y;
     const int ts = fft_tstride(N), hsz = 2 * ts;                  // grid row: 2 transforms
-    float2 *tws = sm + hsz;                                        // twiddle tables
-    float2 *cu = tws + g.ntwN;                                     // [SPREAD_CHUNK]
+    float2 *cu = sm + hsz;                                         // [SPREAD_CHUNK]
     float *cex = reinterpret_cast<float *>(cu + SPREAD_CHUNK);     // [SPREAD_CHUNK]
     short *ckey = reinterpret_cast<short *>(cex + SPREAD_CHUNK);   // [SPREAD_CHUNK]
     const int e0 = g.row_off[r], e1 = g.row_off[r + 1];
     for (int c = threadIdx.x; c < hsz; c += blockDim.x) sm[c] = make_float2(0.f, 0.f);
-    for (int i = threadIdx.x; i < g.ntwN; i += blockDim.x) tws[i] = g.twN[i];
     const float2 *Vb = V + (size_t)b * g.w * g.AM;
     const int *roff = g.rec_off + (size_t)r * (2 * g.nch + 1);
     for (int kc = 0, c0 = e0; c0 < e1; ++kc, c0 += SPREAD_CHUNK) {
@@ -277,7 +271,7 @@ __global__ void __launch_bounds__(512) k_adj_row(const float2 *__restrict__ V, f
         }
         __syncthreads();
     }
-    fft_pow2<+1>(sm, N, g.log2N, 2, ts, tws);
+    fft_pow2<+1>(sm, N, g.log2N, 2, ts, g.twN);
     float2 *Ur = U + ((size_t)b * g.R + r) * N;
     for (int ix = threadIdx.x; ix < N; ix += blockDim.x) {
         const int q = (ix - N / 2) & (N - 1);
@@ -287,12 +281,10 @@ __global__ void __launch_bounds__(512) k_adj_row(const float2 *__restrict__ V, f
 
 __global__ void __launch_bounds__(512) k_adj_col(const float2 *__restrict__ U, float *__restrict__ x,
                           const KArgs g, int CP) {
-    extern __shared__ float2 sm[];  // 2CP transforms (stride ts), then the twiddle tables
+    extern __shared__ float2 sm[];  // 2CP transforms (stride ts)
     const int N = g.N, G = g.G, b = blockIdx.y, ts = fft_tstride(N);
     const int x0base = blockIdx.x * CP * 2;
     const float2 *Ub = U + (size_t)b * g.R * N;
-    float2 *tws = sm + 2 * CP * ts;
-    for (int i = threadIdx.x; i < g.ntwN; i += blockDim.x) tws[i] = g.twN[i];
     const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
     for (int idx = threadIdx.x; idx < G * CP; idx += blockDim.x) {
         const int pp = idx % CP, jy = idx / CP;
@@ -310,7 +302,7 @@ __global__ void __launch_bounds__(512) k_adj_col(const float2 *__restrict__ U, f
         sm[cell_slot(pp * 2, ts, jy)] = make_float2(h0x - h1y, h0y + h1x);
     }
     __syncthreads();
-    fft_pow2<+1>(sm, N, g.log2N, 2 * CP, ts, tws);
+    fft_pow2<+1>(sm, N, g.log2N, 2 * CP, ts, g.twN);
     float *xb = x + (size_t)b * N * N;
     for (int idx = threadIdx.x; idx < N * CP; idx += blockDim.x) {
         const int pp = idx % CP, iy = idx / CP;
@@ -371,21 +363,32 @@ int launch_radon_adj_chunk(tc_plan *p, const float *y, float *x, int nb,
     return TC_OK;
 }
 
+// The dynamic shared-memory limit is an attribute of the kernel (process
+// wide, per device), shared by every plan: only ever raise it.
+template <class F>
+int raise_smem_limit(F *fn, size_t bytes) {
+    cudaFuncAttributes at;
+    TC_CUDA(cudaFuncGetAttributes(&at, fn));
+    if ((size_t)at.maxDynamicSharedSizeBytes < bytes)
+        TC_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    return TC_OK;
+}
+
 int radon_configure_kernels(tc_plan *p) {
-    // opt in to large dynamic shared memory where needed
     // the column passes may be retuned to up to 4 column pairs per CTA
-    int col_max = (int)p->smem_col;
+    size_t col_max = p->smem_col;
     for (int cp = 1; cp <= 4; cp <<= 1) {
-        const long long sm = (long long)(2 * cp * fft_tstride(p->k.N) + p->k.ntwN) * 8;
-        if (sm <= 200 * 1024 && sm > col_max) col_max = (int)sm;
+        const size_t sm = (size_t)(2 * cp * fft_tstride(p->k.N)) * 8;
+        if (sm <= 200 * 1024 && sm > col_max) col_max = sm;
     }
-    TC_CUDA(cudaFuncSetAttribute(k_fwd_col, cudaFuncAttributeMaxDynamicSharedMemorySize, col_max));
-    TC_CUDA(cudaFuncSetAttribute(k_adj_col, cudaFuncAttributeMaxDynamicSharedMemorySize, col_max));
-    TC_CUDA(cudaFuncSetAttribute(k_fwd_row, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem_row_fwd));
-    TC_CUDA(cudaFuncSetAttribute(k_adj_row, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem_row_adj));
-    TC_CUDA(cudaFuncSetAttribute(k_fwd_det<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem_det));
-    TC_CUDA(cudaFuncSetAttribute(k_adj_det<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem_det));
-    TC_CUDA(cudaFuncSetAttribute(k_fwd_det<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem_det));
-    TC_CUDA(cudaFuncSetAttribute(k_adj_det<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem_det));
+    int rc;
+    if ((rc = raise_smem_limit(k_fwd_col, col_max)) || (rc = raise_smem_limit(k_adj_col, col_max)) ||
+        (rc = raise_smem_limit(k_fwd_row, p->smem_row_fwd)) ||
+        (rc = raise_smem_limit(k_adj_row, p->smem_row_adj)) ||
+        (rc = raise_smem_limit(k_fwd_det<true>, p->smem_det)) ||
+        (rc = raise_smem_limit(k_adj_det<true>, p->smem_det)) ||
+        (rc = raise_smem_limit(k_fwd_det<false>, p->smem_det)) ||
+        (rc = raise_smem_limit(k_adj_det<false>, p->smem_det)))
+        return rc;
     return TC_OK;
 }
