@@ -388,6 +388,10 @@ int tc_plan_build(const tc_geom *geom, int max_batch, tc_plan **out) {
                         cs = (lo < n) ? std::max(cs + 1, ents[c0 + lo].key) : cs_end + 1;
                     }
                 }
+                // longest ranges first: the threads that take them start early
+                std::stable_sort(recs.begin() + ro[2 * kc], recs.end(), [](const int2 &u, const int2 &v) {
+                    return ((u.y >> 16) - (u.y & 0xffff)) > ((v.y >> 16) - (v.y & 0xffff));
+                });
                 ro[2 * kc + 1] = (int)recs.size();
                 recs.insert(recs.end(), seams.begin(), seams.end());
             }
