@@ -62,16 +62,17 @@ def lib():
         dp = ctypes.POINTER(ctypes.c_double)
         ip = ctypes.POINTER(ctypes.c_int)
         i = ctypes.c_int
+        d = ctypes.c_double
         L.oracle_radon_fwd.argtypes = [i, i, i, dp, dp, dp]
         L.oracle_radon_adj.argtypes = [i, i, i, dp, dp, dp]
-        L.oracle_radon_fwd_batch.argtypes = [i, i, i, i, dp, dp, dp]
-        L.oracle_radon_adj_batch.argtypes = [i, i, i, i, dp, dp, dp]
-        L.oracle_radon_fwd_at.argtypes = [i, i, i, dp, dp, i, ip, ip, dp]
-        L.oracle_radon_adj_at.argtypes = [i, i, i, dp, dp, i, ip, dp]
+        L.oracle_radon_fwd_batch.argtypes = [i, i, i, i, dp, d, dp, dp]
+        L.oracle_radon_adj_batch.argtypes = [i, i, i, i, dp, d, dp, dp]
+        L.oracle_radon_fwd_at_shift.argtypes = [i, i, i, dp, d, dp, i, ip, ip, dp]
+        L.oracle_radon_adj_at_shift.argtypes = [i, i, i, dp, d, dp, i, ip, dp]
         L.oracle_dirichlet.argtypes = [i, ctypes.c_double]
         L.oracle_dirichlet.restype = ctypes.c_double
         for fn in ("oracle_radon_fwd", "oracle_radon_adj", "oracle_radon_fwd_batch",
-                   "oracle_radon_adj_batch", "oracle_radon_fwd_at", "oracle_radon_adj_at"):
+                   "oracle_radon_adj_batch", "oracle_radon_fwd_at_shift", "oracle_radon_adj_at_shift"):
             getattr(L, fn).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -96,8 +97,9 @@ def _theta(theta, n_angles):
     return th
 
 
-def radon_fwd(f: np.ndarray, n_angles: int, n_det: int, theta=None) -> np.ndarray:
-    """y = A f for f of shape [N,N] or [B,N,N]; returns [A,D] or [B,A,D]."""
+def radon_fwd(f: np.ndarray, n_angles: int, n_det: int, theta=None, delta: float = 0.0) -> np.ndarray:
+    """y = A f for f of shape [N,N] or [B,N,N]; returns [A,D] or [B,A,D].
+    delta: rotation-axis offset (detector coordinate of the axis minus D/2)."""
     f = np.ascontiguousarray(f, np.float64)
     squeeze = f.ndim == 2
     if squeeze:
@@ -106,13 +108,13 @@ def radon_fwd(f: np.ndarray, n_angles: int, n_det: int, theta=None) -> np.ndarra
     assert N == N2
     th = _theta(theta, n_angles)
     y = np.zeros((B, n_angles, n_det), np.float64)
-    rc = lib().oracle_radon_fwd_batch(B, N, n_angles, n_det, _dp(th), _dp(f), _dp(y))
+    rc = lib().oracle_radon_fwd_batch(B, N, n_angles, n_det, _dp(th), float(delta), _dp(f), _dp(y))
     if rc:
         raise ValueError(f"oracle_radon_fwd failed: {rc}")
     return y[0] if squeeze else y
 
 
-def radon_adj(y: np.ndarray, n: int, theta=None) -> np.ndarray:
+def radon_adj(y: np.ndarray, n: int, theta=None, delta: float = 0.0) -> np.ndarray:
     """x = A^T y for y of shape [A,D] or [B,A,D]; returns [N,N] or [B,N,N]."""
     y = np.ascontiguousarray(y, np.float64)
     squeeze = y.ndim == 2
@@ -121,13 +123,13 @@ def radon_adj(y: np.ndarray, n: int, theta=None) -> np.ndarray:
     B, A, D = y.shape
     th = _theta(theta, A)
     x = np.zeros((B, n, n), np.float64)
-    rc = lib().oracle_radon_adj_batch(B, n, A, D, _dp(th), _dp(y), _dp(x))
+    rc = lib().oracle_radon_adj_batch(B, n, A, D, _dp(th), float(delta), _dp(y), _dp(x))
     if rc:
         raise ValueError(f"oracle_radon_adj failed: {rc}")
     return x[0] if squeeze else x
 
 
-def radon_fwd_at(f, n_angles, n_det, a_idx, i_idx, theta=None) -> np.ndarray:
+def radon_fwd_at(f, n_angles, n_det, a_idx, i_idx, theta=None, delta: float = 0.0) -> np.ndarray:
     """Sampled entries y(a_k, i_k) of A f (single slice), Dirichlet closed form."""
     f = np.ascontiguousarray(f, np.float64)
     N = f.shape[0]
@@ -135,21 +137,22 @@ def radon_fwd_at(f, n_angles, n_det, a_idx, i_idx, theta=None) -> np.ndarray:
     a_idx = np.ascontiguousarray(a_idx, np.int32)
     i_idx = np.ascontiguousarray(i_idx, np.int32)
     out = np.zeros(a_idx.shape[0], np.float64)
-    rc = lib().oracle_radon_fwd_at(N, n_angles, n_det, _dp(th), _dp(f), out.shape[0],
-                                   _ip(a_idx), _ip(i_idx), _dp(out))
+    rc = lib().oracle_radon_fwd_at_shift(N, n_angles, n_det, _dp(th), float(delta), _dp(f),
+                                         out.shape[0], _ip(a_idx), _ip(i_idx), _dp(out))
     if rc:
         raise ValueError(f"oracle_radon_fwd_at failed: {rc}")
     return out
 
 
-def radon_adj_at(y, n, pix_idx, theta=None) -> np.ndarray:
+def radon_adj_at(y, n, pix_idx, theta=None, delta: float = 0.0) -> np.ndarray:
     """Sampled pixels x(pix_k) of A^T y (single slice), Dirichlet closed form."""
     y = np.ascontiguousarray(y, np.float64)
     A, D = y.shape
     th = _theta(theta, A)
     pix_idx = np.ascontiguousarray(pix_idx, np.int32)
     out = np.zeros(pix_idx.shape[0], np.float64)
-    rc = lib().oracle_radon_adj_at(n, A, D, _dp(th), _dp(y), out.shape[0], _ip(pix_idx), _dp(out))
+    rc = lib().oracle_radon_adj_at_shift(n, A, D, _dp(th), float(delta), _dp(y), out.shape[0],
+                                         _ip(pix_idx), _dp(out))
     if rc:
         raise ValueError(f"oracle_radon_adj_at failed: {rc}")
     return out

@@ -68,9 +68,11 @@ int oracle_check_geometry(int N, int A, int D)
     return 0;
 }
 
-/* y[A][D] = A f, f[N][N]; exact two-stage NUDFT. */
-int oracle_radon_fwd(int N, int A, int D, const double *theta,
-                     const double *f, double *y)
+/* y[A][D] = A f, f[N][N]; exact two-stage NUDFT.  delta: rotation-axis
+ * offset, the projection of x_n lands at detector coordinate s_n + delta
+ * (Sec. 4.1, Fourier-shift correction of the axis). */
+int oracle_radon_fwd_shift(int N, int A, int D, const double *theta, double delta,
+                           const double *f, double *y)
 {
     if (oracle_check_geometry(N, A, D)) return -1;
     const int M = D + 1; /* m = -D/2 .. D/2 */
@@ -104,7 +106,14 @@ int oracle_radon_fwd(int N, int A, int D, const double *theta,
                 }
             }
         }
-        /* stage 2: y(a,i) = (1/D) Re sum_m nu_m c(a,m) exp(2 pi i m t_i / D) */
+        /* stage 2: y(a,i) = (1/D) Re sum_m nu_m c(a,m) exp(2 pi i m (t_i - delta) / D) */
+        for (int j = 0; j < M; ++j) {  /* c(a,m) *= exp(-2 pi i m delta / D) */
+            const double ph = -2.0 * PI * (j - D / 2) * delta / (double)D;
+            const double pr = cos(ph), pi = sin(ph);
+            const double nr = cre[j] * pr - cim[j] * pi;
+            cim[j] = cre[j] * pi + cim[j] * pr;
+            cre[j] = nr;
+        }
         for (int i = 0; i < D; ++i) {
             const int t = i - D / 2;
             double acc = 0.0;
@@ -124,8 +133,8 @@ int oracle_radon_fwd(int N, int A, int D, const double *theta,
 }
 
 /* x[N][N] = A^T y, y[A][D]; row DFT then exact back-summation. */
-int oracle_radon_adj(int N, int A, int D, const double *theta,
-                     const double *y, double *x)
+int oracle_radon_adj_shift(int N, int A, int D, const double *theta, double delta,
+                           const double *y, double *x)
 {
     if (oracle_check_geometry(N, A, D)) return -1;
     const int M = D + 1;
@@ -153,8 +162,11 @@ int oracle_radon_adj(int N, int A, int D, const double *theta,
                 sr += v * cr_t[k];
                 si += v * ci_t[k];
             }
-            gr[(size_t)a * M + j] = nu_m(m, D) * sr / (double)D;
-            gi[(size_t)a * M + j] = nu_m(m, D) * si / (double)D;
+            /* times exp(+2 pi i m delta / D): the transpose of the forward shift */
+            const double ph = 2.0 * PI * m * delta / (double)D;
+            const double pr = cos(ph), pim = sin(ph);
+            gr[(size_t)a * M + j] = nu_m(m, D) * (sr * pr - si * pim) / (double)D;
+            gi[(size_t)a * M + j] = nu_m(m, D) * (sr * pim + si * pr) / (double)D;
         }
     }
     /* x_n = Re sum_a sum_m g(a,m) exp(+2 pi i m s_n(a) / D) */
@@ -196,9 +208,9 @@ double oracle_dirichlet(int D, double u)
 }
 
 /* y(a_k, i_k) for K sampled sinogram entries, by the closed form. */
-int oracle_radon_fwd_at(int N, int A, int D, const double *theta,
-                        const double *f, int K, const int *a_idx,
-                        const int *i_idx, double *out)
+int oracle_radon_fwd_at_shift(int N, int A, int D, const double *theta, double delta,
+                              const double *f, int K, const int *a_idx,
+                              const int *i_idx, double *out)
 {
     if (oracle_check_geometry(N, A, D)) return -1;
     for (int k = 0; k < K; ++k)
@@ -207,7 +219,7 @@ int oracle_radon_fwd_at(int N, int A, int D, const double *theta,
 #pragma omp parallel for schedule(dynamic, 1)
     for (int k = 0; k < K; ++k) {
         const double ct = cos(theta[a_idx[k]]), st = sin(theta[a_idx[k]]);
-        const double t = i_idx[k] - D / 2;
+        const double t = i_idx[k] - D / 2 - delta;
         double acc = 0.0;
         for (int iy = 0; iy < N; ++iy)
             for (int ix = 0; ix < N; ++ix) {
@@ -222,9 +234,9 @@ int oracle_radon_fwd_at(int N, int A, int D, const double *theta,
 }
 
 /* x(pix_k) for K sampled pixels of A^T y, by the closed form. */
-int oracle_radon_adj_at(int N, int A, int D, const double *theta,
-                        const double *y, int K, const int *pix_idx,
-                        double *out)
+int oracle_radon_adj_at_shift(int N, int A, int D, const double *theta, double delta,
+                              const double *y, int K, const int *pix_idx,
+                              double *out)
 {
     if (oracle_check_geometry(N, A, D)) return -1;
     for (int k = 0; k < K; ++k)
@@ -236,31 +248,42 @@ int oracle_radon_adj_at(int N, int A, int D, const double *theta,
         for (int a = 0; a < A; ++a) {
             const double s = (ix - N / 2) * cos(theta[a]) + (iy - N / 2) * sin(theta[a]);
             for (int i = 0; i < D; ++i)
-                acc += y[(size_t)a * D + i] * oracle_dirichlet(D, (i - D / 2) - s);
+                acc += y[(size_t)a * D + i] * oracle_dirichlet(D, (i - D / 2) - delta - s);
         }
         out[k] = acc;
     }
     return 0;
 }
 
+/* Unshifted forms (rotation axis at the detector centre). */
+int oracle_radon_fwd(int N, int A, int D, const double *theta, const double *f, double *y)
+{
+    return oracle_radon_fwd_shift(N, A, D, theta, 0.0, f, y);
+}
+
+int oracle_radon_adj(int N, int A, int D, const double *theta, const double *y, double *x)
+{
+    return oracle_radon_adj_shift(N, A, D, theta, 0.0, y, x);
+}
+
 /* Batched forms over B slices (each slice is an independent 2D problem). */
-int oracle_radon_fwd_batch(int B, int N, int A, int D, const double *theta,
+int oracle_radon_fwd_batch(int B, int N, int A, int D, const double *theta, double delta,
                            const double *f, double *y)
 {
     for (int b = 0; b < B; ++b) {
-        int rc = oracle_radon_fwd(N, A, D, theta, f + (size_t)b * N * N,
-                                  y + (size_t)b * A * D);
+        int rc = oracle_radon_fwd_shift(N, A, D, theta, delta, f + (size_t)b * N * N,
+                                        y + (size_t)b * A * D);
         if (rc) return rc;
     }
     return 0;
 }
 
-int oracle_radon_adj_batch(int B, int N, int A, int D, const double *theta,
+int oracle_radon_adj_batch(int B, int N, int A, int D, const double *theta, double delta,
                            const double *y, double *x)
 {
     for (int b = 0; b < B; ++b) {
-        int rc = oracle_radon_adj(N, A, D, theta, y + (size_t)b * A * D,
-                                  x + (size_t)b * N * N);
+        int rc = oracle_radon_adj_shift(N, A, D, theta, delta, y + (size_t)b * A * D,
+                                        x + (size_t)b * N * N);
         if (rc) return rc;
     }
     return 0;

@@ -144,3 +144,37 @@ def test_ellipse_phantom_close_to_analytic_line_integrals():
 def test_rejects_odd_detector_width():
     with pytest.raises(ValueError):
         oracle.radon_fwd(np.zeros((8, 8)), 4, 11)
+
+
+@pytest.mark.parametrize("delta", [2.7, -5.25, 0.5])
+def test_rotation_axis_offset_moves_the_gaussian_projection(delta):
+    """With the axis at detector coordinate D/2 + delta, the projection of a
+    Gaussian is the analytic one shifted by +delta along t (Sec. 4.1)."""
+    N, A, D = 64, 10, 92
+    th = np.sort(RNG.uniform(0.0, math.pi, A))
+    cx, cy, s = 4.1, -6.3, 3.0
+    f = synth.gaussian_blob(N, cx, cy, s)
+    y = oracle.radon_fwd(f, A, D, th, delta=delta)
+    t = np.arange(D) - D // 2
+    tc = cx * np.cos(th) + cy * np.sin(th) + delta
+    ya = math.sqrt(2 * math.pi) * s * np.exp(-(t[None, :] - tc[:, None]) ** 2 / (2 * s * s))
+    assert np.abs(y - ya).max() <= 1e-10 * np.abs(ya).max()
+
+
+def test_shifted_operator_adjoint_and_sampled_forms():
+    N, A, D, delta = 32, 9, 46, 1.37
+    th = RNG.uniform(0.0, math.pi, A)
+    x = RNG.standard_normal((N, N))
+    y = RNG.standard_normal((A, D))
+    Ax = oracle.radon_fwd(x, A, D, th, delta=delta)
+    Aty = oracle.radon_adj(y, N, th, delta=delta)
+    assert abs(float(np.sum(Ax * y)) - float(np.sum(x * Aty))) <= 1e-11 * abs(float(np.sum(Ax * y)))
+    ai = RNG.integers(0, A, 20)
+    ii = RNG.integers(0, D, 20)
+    assert np.abs(oracle.radon_fwd_at(x, A, D, ai, ii, th, delta=delta) - Ax[ai, ii]).max() < 1e-11
+    pix = RNG.integers(0, N * N, 20)
+    assert np.abs(oracle.radon_adj_at(y, N, pix, th, delta=delta) - Aty.ravel()[pix]).max() < 1e-11
+    # an integer offset at theta = 0 shifts the column sums by exactly delta bins
+    y0 = oracle.radon_fwd(x, 1, D, np.array([0.0]), delta=3.0)[0]
+    off = (D - N) // 2 + 3
+    assert np.abs(y0[off:off + N] - x.sum(axis=0)).max() < 1e-11
