@@ -58,6 +58,14 @@ const char *tc_last_error_detail(void);
  *   oversample    sigma, the grid oversampling factor; must be 2
  *   kernel_width  w, spreading-kernel width in grid points (Sec. 2.2: w about
  *                 log10(1/eps)); 2 <= w <= 8; 7 gives ~1e-6 relative error
+ *   center_offset delta, rotation-axis offset in detector bins: the axis
+ *                 projects to detector coordinate D/2 + delta, so pixel x_n
+ *                 lands at t = s_n(theta) + delta.  Applied as the Fourier
+ *                 shift exp(-2 pi i m delta / D) of every projection's
+ *                 spectrum (Sec. 4.1, axis correction by the shift property);
+ *                 the adjoint applies the conjugate phase.  Finite and
+ *                 |delta| <= D/2, else TC_ERR_INVALID_ARG.  0 (a
+ *                 zero-initialised struct) means the axis at the centre.
  */
 typedef struct {
     int n;
@@ -66,6 +74,7 @@ typedef struct {
     const double *angles;
     int oversample;
     int kernel_width;
+    double center_offset;
 } tc_geom;
 
 typedef struct tc_plan tc_plan;

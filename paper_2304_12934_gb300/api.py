@@ -32,7 +32,7 @@ class TcError(RuntimeError):
 class _Geom(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int), ("n_angles", ctypes.c_int), ("n_det", ctypes.c_int),
                 ("angles", ctypes.POINTER(ctypes.c_double)), ("oversample", ctypes.c_int),
-                ("kernel_width", ctypes.c_int)]
+                ("kernel_width", ctypes.c_int), ("center_offset", ctypes.c_double)]
 
 
 class _Prior(ctypes.Structure):
@@ -142,10 +142,11 @@ class Plan:
     """Geometry + tables + scratch for max_batch slices per launch (tc_plan_create)."""
 
     def __init__(self, n, n_angles, n_det, angles=None, oversample=2, kernel_width=7,
-                 max_batch=1, device=None):
+                 max_batch=1, device=None, center_offset=0.0):
         L = load()
         self.n, self.n_angles, self.n_det = int(n), int(n_angles), int(n_det)
         self.kernel_width, self.max_batch = int(kernel_width), int(max_batch)
+        self.center_offset = float(center_offset)
         self.device = torch.device("cuda", torch.cuda.current_device()) if device is None \
             else torch.device(device)
         self._angles = None
@@ -155,7 +156,8 @@ class Plan:
             self._angles = np.ascontiguousarray(angles, dtype=np.float64)
             assert self._angles.shape == (self.n_angles,)
             aptr = self._angles.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
-        g = _Geom(self.n, self.n_angles, self.n_det, aptr, int(oversample), self.kernel_width)
+        g = _Geom(self.n, self.n_angles, self.n_det, aptr, int(oversample), self.kernel_width,
+                  self.center_offset)
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
             _check("tc_plan_create", L.tc_plan_create(ctypes.byref(g), self.max_batch, ctypes.byref(h)))

@@ -1,6 +1,7 @@
 // C ABI entry points (include/nufft_radon.h): argument checks, chunking of
 // batches larger than the plan's scratch, and the MBIR driver loops.  All
 // compute runs in the kernels of radon_kernels.cu and mbir_kernels.cu.
+#include <cmath>
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
@@ -118,6 +119,7 @@ int tc_plan_create(const tc_geom *geom, int max_batch, tc_plan **out) {
     if (N < 16 || N > 4096 || (N & (N - 1)) || A < 1 || D < 4 || D > 16384 || (D & 1) ||
         geom->oversample != 2 || w < 2 || w > 8 || max_batch < 1 || max_batch > 65535)
         return TC_ERR_INVALID_ARG;
+    if (!(std::fabs(geom->center_offset) <= 0.5 * D)) return TC_ERR_INVALID_ARG;  // also rejects NaN
     if ((long long)A * (D / 2 + 1) >= (1LL << 31) / 8) return TC_ERR_UNSUPPORTED;
     g_detail.clear();
     return tc_plan_build(geom, max_batch, out);

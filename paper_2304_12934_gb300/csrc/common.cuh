@@ -42,6 +42,7 @@ struct KArgs {
     const int *rec_off;        // [R][2 nch + 1] record ranges (regular, seam) per row and chunk
     int nch;                   // chunks per row (max over rows)
     const unsigned char *angle_flip; // [A] 1: theta was in [pi, 2 pi), data conjugated
+    const float2 *shiftD;      // [Mh] exp(-2 pi i m delta / D) (axis offset), or null for delta = 0
     RadixPlan rp;              // factorisation of D
     // Bluestein (chirp-z) detector DFT, used when D has a large prime factor:
     // length-L power-of-two FFTs, L >= 2D - 1
@@ -64,6 +65,7 @@ struct tc_plan {
     int2 *rec;
     int *rec_off;
     unsigned char *angle_flip;
+    float2 *shiftD;
     float2 *chirp, *bhat, *twL;
     long long n_entries;
     // scratch for max_batch slices

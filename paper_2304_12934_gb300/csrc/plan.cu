@@ -203,7 +203,7 @@ int plan_set_col_pairs(tc_plan *p, int cp) {
 void tc_plan_free(tc_plan *p) {
     if (!p) return;
     void *ptrs[] = {p->dea64, p->dea, p->twN, p->twG, p->twD, p->row_off, p->ent, p->rec, p->rec_off,
-                    p->tu, p->pv, p->sr, p->partials, p->scal, p->angle_flip,
+                    p->tu, p->pv, p->sr, p->partials, p->scal, p->angle_flip, p->shiftD,
                     p->chirp, p->bhat, p->twL};
     for (void *q : ptrs)
         if (q) cudaFree(q);
@@ -455,6 +455,17 @@ int tc_plan_build(const tc_geom *geom, int max_batch, tc_plan **out) {
         const double a3 = -2.0 * kPi * i / D;
         twD[i] = make_float2((float)std::cos(a3), (float)std::sin(a3));
     }
+    // rotation-axis offset: exp(-2 pi i m delta / D), the phase reduced in FP64
+    const double delta = geom->center_offset;
+    std::vector<float2> shiftD;
+    if (delta != 0.0) {
+        shiftD.resize(k.Mh);
+        for (int m = 0; m < k.Mh; ++m) {
+            double cyc = std::fmod((double)m * delta, (double)D) / D;
+            const double a4 = -2.0 * kPi * cyc;
+            shiftD[m] = make_float2((float)std::cos(a4), (float)std::sin(a4));
+        }
+    }
 
     long long bytes = 0;
     int rc = TC_OK;
@@ -473,6 +484,7 @@ int tc_plan_build(const tc_geom *geom, int max_batch, tc_plan **out) {
     UP(p->rec, recs);
     UP(p->rec_off, roff);
     UP(p->angle_flip, flip);
+    UP(p->shiftD, shiftD);
     UP(p->chirp, chirp);
     UP(p->bhat, bhat);
     UP(p->twL, twL);
@@ -486,6 +498,7 @@ int tc_plan_build(const tc_geom *geom, int max_batch, tc_plan **out) {
     k.rec = p->rec;
     k.rec_off = p->rec_off;
     k.angle_flip = p->angle_flip;
+    k.shiftD = p->shiftD;
     k.chirp = p->chirp;
     k.bhat = p->bhat;
     k.twL = p->twL;

@@ -134,6 +134,11 @@ __global__ void __launch_bounds__(512) k_fwd_det(const float2 *__restrict__ P, f
         }
         if (g.angle_flip[a0]) c0 = cconj(c0);
         if (has1 && g.angle_flip[a0 + 1]) c1 = cconj(c1);
+        if (g.shiftD) {  // axis offset: Fourier shift of the true-angle spectrum
+            const float2 e = g.shiftD[m];
+            c0 = cmul(c0, e);
+            c1 = cmul(c1, e);
+        }
         const float sg = (m & 1) ? -1.f : 1.f;
         float2 X0 = cscale(c0, sg), X1 = cscale(c1, sg);
         if (2 * m == D) { X0.y = 0.f; X1.y = 0.f; }
@@ -204,10 +209,14 @@ __global__ void __launch_bounds__(512) k_adj_det(const float *__restrict__ ysino
         const float mn = (m == 0 || 2 * m == D) ? 1.f : 2.f;
         const float sc = ((m & 1) ? -mn : mn) * 0.5f * g.invD;
         float2 v0 = make_float2(sc * (zp.x + zm.x), sc * (zp.y + zm.y));
+        float2 e = make_float2(1.f, 0.f);
+        if (g.shiftD) e = cconj(g.shiftD[m]);  // transpose of the axis-offset shift
+        v0 = cmul(v0, e);
         if (g.angle_flip[a0]) v0 = cconj(v0);
         Vb[(size_t)a0 * Mh + m] = v0;
         if (has1) {
             float2 v1 = make_float2(sc * (zp.y - zm.y), -sc * (zp.x - zm.x));
+            v1 = cmul(v1, e);
             if (g.angle_flip[a0 + 1]) v1 = cconj(v1);
             Vb[(size_t)(a0 + 1) * Mh + m] = v1;
         }

@@ -53,6 +53,10 @@ def test_invalid_geometry_rejected_on_host():
         g = api._Geom(n, a, d, ctypes.POINTER(ctypes.c_double)(), os_, w)
         assert L.tc_plan_create(ctypes.byref(g), 1, ctypes.byref(h)) == -1
         assert not h.value
+    for delta in (float("nan"), float("inf"), 10.5, -11.0):  # |delta| <= D/2 = 10
+        g = api._Geom(64, 10, 20, ctypes.POINTER(ctypes.c_double)(), 2, 7, delta)
+        assert L.tc_plan_create(ctypes.byref(g), 1, ctypes.byref(h)) == -1
+        assert not h.value
     assert L.radon_fwd(None, None, None, 1, None) == -1
     assert L.tc_plan_destroy(None) == 0
 

@@ -171,3 +171,33 @@ def test_full_size_sampled_entries(api, N, A, D):
         xs = oracle.radon_adj_at(yy[k].astype(np.float64), N, pix)
         xrms = float(np.sqrt(np.mean(x[k] ** 2)))
         assert np.abs(x[k].ravel()[pix] - xs).max() <= REL_TOL * xrms * 2
+
+
+@pytest.mark.parametrize("N,A,D,delta,kind", [
+    (64, 33, 92, 3.4, "random2pi"),     # mixed-radix detector DFT, flipped angles
+    (128, 90, 184, -11.75, None),       # D = 8 * 23: Bluestein
+    (32, 13, 46, 23.0, "random"),       # |delta| = D/2, the largest allowed
+])
+def test_rotation_axis_offset_matches_oracle(api, N, A, D, delta, kind):
+    """Axis offset delta (Sec. 4.1 Fourier shift): forward and adjoint against
+    the oracle's shifted operator, and the adjoint identity of the GPU pair."""
+    th = _angles(kind, A, N + 5)
+    rng = np.random.default_rng(N + D)
+    f = synth.rasterize(N, synth.random_ellipses(N, synth.BASE_SEED + 3))[None]
+    yy = rng.standard_normal((1, A, D))
+    with api.Plan(N, A, D, angles=th, center_offset=delta) as plan:
+        y = api.radon_fwd(plan, t32(f)).double().cpu().numpy()
+        x = api.radon_adj(plan, t32(yy)).double().cpu().numpy()
+    thv = th if th is not None else oracle.default_angles(A)
+    f32 = f.astype(np.float32).astype(np.float64)
+    y32 = yy.astype(np.float32).astype(np.float64)
+    assert rel(y, oracle.radon_fwd(f32, A, D, thv, delta=delta)) <= REL_TOL
+    assert rel(x, oracle.radon_adj(y32, N, thv, delta=delta)) <= REL_TOL
+    lhs, rhs = float(np.sum(y * y32)), float(np.sum(f32 * x))
+    assert abs(lhs - rhs) <= 1e-5 * np.linalg.norm(y) * np.linalg.norm(y32)
+
+
+@pytest.mark.parametrize("delta", [float("nan"), 46.5, -1e9])
+def test_rotation_axis_offset_out_of_range_is_rejected(api, delta):
+    with pytest.raises(api.TcError):
+        api.Plan(32, 8, 92, center_offset=delta)
