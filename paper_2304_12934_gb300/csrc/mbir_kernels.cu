@@ -5,6 +5,8 @@
 // Vectors are FP32; every reduction accumulates at most a few FP32 products
 // per thread before promoting to FP64, then sums per-block FP64 partials in a
 // fixed order, so results are bit-reproducible run to run.
+#include <cmath>
+
 #include "common.cuh"
 #include "profile.cuh"
 
@@ -12,9 +14,11 @@ namespace {
 
 struct PriorArgs {
     int N, B, dims;
-    float p, inv_sigma, c, qexp;  // qexp = 2 - p
-    float two_lambda;
-    float w1, w2, w3;             // weights at distance 1, sqrt 2, sqrt 3
+    float p, c, qexp;  // qexp = 2 - p
+    float lk;          // qexp * log2(1 / sigma)
+    float two_c;       // 2 c
+    float gscale;      // 2 lambda / sigma^2: scale of the gradient sum
+    float w1, w2, w3;  // weights at distance 1, sqrt 2, sqrt 3
 };
 
 // Hardware approximations (one instruction each, denormals flushed to zero):
@@ -35,15 +39,17 @@ __device__ __forceinline__ float rcp_approx(float x) {
     return r;
 }
 
-// rho(d) = u^2 / (c + |u|^(2-p)), u = d / sigma, and its derivative in d.
-// |u|^(2-p) = 2^((2-p) log2|u|); at d = 0, log2 gives -inf and the power 0.
-__device__ __forceinline__ float qggmrf_rhop(float d, const PriorArgs &a, float &inv_out, float &u_out) {
-    const float u = d * a.inv_sigma;
-    const float q = ex2_approx(a.qexp * lg2_approx(fabsf(u)));
+// rho(d) = u^2 / (c + |u|^(2-p)), u = d / sigma (Eq. reg3), differentiated by
+// hand:  rho'(d) = (d / sigma^2) (p |u|^(2-p) + 2c) / (c + |u|^(2-p))^2.
+// Returns sigma^2 rho'(d) (the constant is applied once per voxel) and
+// inv = 1 / (c + |u|^(2-p)), from which sigma^2 rho(d) = d^2 inv.
+// |u|^(2-p) = 2^((2-p) log2|d| + (2-p) log2(1/sigma)); at d = 0, log2 gives
+// -inf and the power 0.
+__device__ __forceinline__ float qggmrf_e(float d, const PriorArgs &a, float &inv_out) {
+    const float q = ex2_approx(fmaf(a.qexp, lg2_approx(fabsf(d)), a.lk));
     const float inv = rcp_approx(a.c + q);
     inv_out = inv;
-    u_out = u;
-    return u * a.inv_sigma * fmaf(a.p, q, 2.0f * a.c) * inv * inv;
+    return d * fmaf(a.p, q, a.two_c) * (inv * inv);
 }
 
 // qGGMRF prior on a volume [B][N][N] (slices consecutive along z).
@@ -56,16 +62,62 @@ __device__ __forceinline__ float qggmrf_rhop(float d, const PriorArgs &a, float 
 // over two, so a step's writes never touch what the previous step's gradient
 // phase still reads; with the plane double buffer this needs two barriers per
 // z step.  dims = 2 skips the z pairs and uses the 8-neighbour weights.
+// A CTA whose ring lies inside the volume evaluates every direction at every
+// ring cell without per-pair tests (the pairs that leave the ring are never
+// read); CTAs at the volume border test each pair against the border rule.
 // WANT_H also accumulates H (otherwise only the gradient is produced).
 // DOTS also accumulates <g, f - xprev> and <g, g> of the final gradient g (the
 // inner products of the solver's restart test), sparing a separate pass.
+// Per-thread sums run in FP32 over 8 z steps, then over 8 such groups, then in
+// FP64 (the FP64 pipe of this part is narrow), always in the same order.
 #define PTX 32
 #define PTY 12
 #define PRX (PTX + 2)
 #define PRY (PTY + 2)
 #define PRS (PRX * PRY)
 #define PRIOR_THREADS 480
-#define PRIOR_SMEM_FLOATS (2 * PRS + 3 * 9 * PRS + 2 * 4 * PRS)
+#define PRIOR_FPAD 36  // front pad: unmasked halo reads reach PRX + 1 cells before a plane
+#define PRIOR_SMEM_FLOATS (PRIOR_FPAD + 2 * PRS + 3 * 9 * PRS + 2 * 4 * PRS)
+
+// z+1 pairs of one ring cell: fc / fn point at the cell in planes z and z+1,
+// eu at its slot of the current z+1 buffer.
+template <bool MASKED, bool WANT_H>
+__device__ __forceinline__ void prior_up_pairs(const float *fn, float fm, float *eu, unsigned mu,
+                                               const PriorArgs &a, float &hs) {
+#pragma unroll
+    for (int u = 0; u < 9; ++u) {
+        const int dx = u % 3 - 1, dy = u / 3 - 1;
+        float e = 0.f;
+        if (!MASKED || (mu & (1u << u))) {
+            float inv;
+            const float d = fm - fn[dy * PRX + dx];
+            e = qggmrf_e(d, a, inv);
+            if (WANT_H)
+                hs = fmaf((dx == 0 && dy == 0) ? a.w1 : ((dx == 0 || dy == 0) ? a.w2 : a.w3), d * d * inv, hs);
+        }
+        eu[u * PRS] = e;
+    }
+}
+
+// in-plane forward directions (dx, dy): (1,0) (-1,1) (0,1) (1,1)
+__device__ __forceinline__ int pl_dx(int q) { return q == 0 ? 1 : (q == 1 ? -1 : (q == 2 ? 0 : 1)); }
+__device__ __forceinline__ int pl_dy(int q) { return q == 0 ? 0 : 1; }
+
+template <bool MASKED, bool WANT_H>
+__device__ __forceinline__ void prior_plane_pairs(const float *fc, float fm, float *ep, unsigned mp,
+                                                  const PriorArgs &a, float &hs) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        float e = 0.f;
+        if (!MASKED || (mp & (1u << q))) {
+            float inv;
+            const float d = fm - fc[pl_dy(q) * PRX + pl_dx(q)];
+            e = qggmrf_e(d, a, inv);
+            if (WANT_H) hs = fmaf((q & 1) ? a.w2 : a.w1, d * d * inv, hs);
+        }
+        ep[q * PRS] = e;
+    }
+}
 
 template <bool WANT_H, bool DOTS>
 __global__ void __launch_bounds__(PRIOR_THREADS) k_prior(const float *__restrict__ f, float *__restrict__ g,
@@ -73,7 +125,7 @@ __global__ void __launch_bounds__(PRIOR_THREADS) k_prior(const float *__restrict
                                                           const float *__restrict__ xprev,
                                                           double *__restrict__ pd1, double *__restrict__ pd2) {
     extern __shared__ float psm[];
-    float *fpl = psm;                 // [2][PRS]
+    float *fpl = psm + PRIOR_FPAD;    // [2][PRS]
     float *Eu = fpl + 2 * PRS;        // [3][9][PRS]
     float *Ep = Eu + 3 * 9 * PRS;     // [2][4][PRS]
     __shared__ double red[32];
@@ -81,14 +133,14 @@ __global__ void __launch_bounds__(PRIOR_THREADS) k_prior(const float *__restrict
     const size_t NN = (size_t)N * N;
     const int h = threadIdx.x;
     const int hx = h % PRX, hy = h / PRX;
-    const int x = blockIdx.x * PTX - 1 + hx, y = blockIdx.y * PTY - 1 + hy;
+    const int x0 = blockIdx.x * PTX - 1, y0 = blockIdx.y * PTY - 1;
+    const int x = x0 + hx, y = y0 + hy;
     const bool ring = h < PRS;
     const bool inb = ring && x >= 0 && x < N && y >= 0 && y < N;
     const bool interior = inb && hx >= 1 && hx <= PTX && hy >= 1 && hy <= PTY;
     const bool three = a.dims == 3;
-    // in-plane forward directions (dx, dy): (1,0) (-1,1) (0,1) (1,1)
-    const int pdx[4] = {1, -1, 0, 1}, pdy[4] = {0, 1, 1, 1};
-    const float pw[4] = {a.w1, a.w2, a.w1, a.w2};
+    // the whole ring inside the volume: no pair needs the border test
+    const bool full = x0 >= 0 && y0 >= 0 && x0 + PRX <= N && y0 + PRY <= N;
     auto ring_in = [&](int dx, int dy) {
         const int nx = hx + dx, ny = hy + dy;
         if (nx < 0 || nx >= PRX || ny < 0 || ny >= PRY) return false;
@@ -100,17 +152,20 @@ __global__ void __launch_bounds__(PRIOR_THREADS) k_prior(const float *__restrict
         return nx >= 1 && nx <= PTX && ny >= 1 && ny <= PTY && x + dx < N && y + dy < N &&
                x + dx >= 0 && y + dy >= 0;
     };
-    // pair validity is the same at every z: bit u of mup / bit q of mpl says the
-    // pair towards (dx, dy) is inside the volume and needed by an interior voxel
+    // border CTAs: bit u of mup / bit q of mpl says the pair towards (dx, dy)
+    // is inside the volume and needed by an interior voxel (the same at every z)
     unsigned mup = 0, mpl = 0;
+    if (!full) {
 #pragma unroll
-    for (int u = 0; u < 9; ++u) {
-        const int dx = u % 3 - 1, dy = u / 3 - 1;
-        if (inb && ring_in(dx, dy) && (interior || is_interior(dx, dy))) mup |= 1u << u;
+        for (int u = 0; u < 9; ++u) {
+            const int dx = u % 3 - 1, dy = u / 3 - 1;
+            if (inb && ring_in(dx, dy) && (interior || is_interior(dx, dy))) mup |= 1u << u;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if (inb && ring_in(pl_dx(q), pl_dy(q)) && (interior || is_interior(pl_dx(q), pl_dy(q))))
+                mpl |= 1u << q;
     }
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-        if (inb && ring_in(pdx[q], pdy[q]) && (interior || is_interior(pdx[q], pdy[q]))) mpl |= 1u << q;
     if (ring) {
         for (int u = 0; u < 9; ++u)
             for (int sl = 0; sl < 3; ++sl) Eu[(sl * 9 + u) * PRS + h] = 0.f;
@@ -119,11 +174,11 @@ __global__ void __launch_bounds__(PRIOR_THREADS) k_prior(const float *__restrict
     // register prefetch: the plane the next step stores (3D: z + 2, 2D: z + 1)
     const size_t off = (size_t)y * N + x;
     float f_nx = (inb && B > 1) ? f[NN + off] : 0.f;
+    float h8 = 0.f, h64 = 0.f, a8 = 0.f, a64 = 0.f, b8 = 0.f, b64 = 0.f;
     double hacc = 0.0, d1 = 0.0, d2 = 0.0;
-    float d1f = 0.f, d2f = 0.f;
+    int s3 = 0, p3 = 2;  // this step's / previous step's z+1 slot (z mod 3, (z + 2) mod 3)
     for (int z = 0; z < B; ++z) {
         const int cur = z & 1, nxt = cur ^ 1;
-        const int s3 = z % 3, p3 = (z + 2) % 3;  // this step's / previous step's z+1 slots
         const bool up = three && z + 1 < B;
         const int pz = three ? z + 2 : z + 1;
         const float f_pf = (inb && pz < B) ? f[(size_t)pz * NN + off] : 0.f;
@@ -137,32 +192,19 @@ __global__ void __launch_bounds__(PRIOR_THREADS) k_prior(const float *__restrict
         __syncthreads();
         float hs = 0.f, fm = 0.f;
         if (ring) {
-            fm = fpl[cur * PRS + h];
-            const unsigned mu = up ? mup : 0u;
+            const float *fc = fpl + cur * PRS + h;
+            fm = *fc;
             float *eu = Eu + (s3 * 9) * PRS + h;
+            if (up) {
+                if (full) prior_up_pairs<false, WANT_H>(fpl + nxt * PRS + h, fm, eu, 0u, a, hs);
+                else prior_up_pairs<true, WANT_H>(fpl + nxt * PRS + h, fm, eu, mup, a, hs);
+            } else if (three) {
 #pragma unroll
-            for (int u = 0; u < 9; ++u) {
-                const int dx = u % 3 - 1, dy = u / 3 - 1;
-                float e = 0.f;
-                if (mu & (1u << u)) {
-                    float inv, uu;
-                    e = qggmrf_rhop(fm - fpl[nxt * PRS + h + dy * PRX + dx], a, inv, uu);
-                    if (WANT_H)
-                        hs = fmaf((dx == 0 && dy == 0) ? a.w1 : ((dx == 0 || dy == 0) ? a.w2 : a.w3), uu * uu * inv, hs);
-                }
-                eu[u * PRS] = e;
+                for (int u = 0; u < 9; ++u) eu[u * PRS] = 0.f;
             }
             float *ep = Ep + (cur * 4) * PRS + h;
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                float e = 0.f;
-                if (mpl & (1u << q)) {
-                    float inv, uu;
-                    e = qggmrf_rhop(fm - fpl[cur * PRS + h + pdy[q] * PRX + pdx[q]], a, inv, uu);
-                    if (WANT_H) hs = fmaf(pw[q], uu * uu * inv, hs);
-                }
-                ep[q * PRS] = e;
-            }
+            if (full) prior_plane_pairs<false, WANT_H>(fc, fm, ep, 0u, a, hs);
+            else prior_plane_pairs<true, WANT_H>(fc, fm, ep, mpl, a, hs);
         }
         __syncthreads();
         if (interior) {
@@ -179,30 +221,39 @@ __global__ void __launch_bounds__(PRIOR_THREADS) k_prior(const float *__restrict
             const float *ep = Ep + (cur * 4) * PRS + h;
 #pragma unroll
             for (int q = 0; q < 4; ++q)
-                gs = fmaf(pw[q], ep[q * PRS] - ep[q * PRS - pdy[q] * PRX - pdx[q]], gs);
-            const float gn = fmaf(a.two_lambda, gs, g_old);
+                gs = fmaf((q & 1) ? a.w2 : a.w1, ep[q * PRS] - ep[q * PRS - pl_dy(q) * PRX - pl_dx(q)], gs);
+            const float gn = fmaf(a.gscale, gs, g_old);
             g[i] = gn;
-            if (WANT_H) hacc += 2.0 * (double)hs;
+            if (WANT_H) h8 += hs;
             if (DOTS) {
-                d1f = fmaf(gn, fm - x_old, d1f);
-                d2f = fmaf(gn, gn, d2f);
-                if ((z & 7) == 7) {  // promote to FP64 every 8 voxels
-                    d1 += (double)d1f;
-                    d2 += (double)d2f;
-                    d1f = d2f = 0.f;
+                a8 = fmaf(gn, fm - x_old, a8);
+                b8 = fmaf(gn, gn, b8);
+            }
+        }
+        if ((z & 7) == 7) {
+            h64 += h8; a64 += a8; b64 += b8;
+            h8 = a8 = b8 = 0.f;
+            if ((z & 63) == 63) {
+                if (WANT_H) hacc += (double)h64;
+                if (DOTS) {
+                    d1 += (double)a64;
+                    d2 += (double)b64;
                 }
+                h64 = a64 = b64 = 0.f;
             }
         }
         f_nx = f_pf;
+        p3 = s3;
+        s3 = s3 == 2 ? 0 : s3 + 1;
     }
     const int bid = blockIdx.y * gridDim.x + blockIdx.x;
     if (WANT_H) {
-        const double tot = block_sum_f64(hacc, red);
+        const double tot = block_sum_f64(hacc + ((double)h64 + (double)h8), red);
         if (threadIdx.x == 0) partials[bid] = tot;
     }
     if (DOTS) {
-        const double t1 = block_sum_f64(d1 + (double)d1f, red);
-        const double t2 = block_sum_f64(d2 + (double)d2f, red);
+        const double t1 = block_sum_f64(d1 + ((double)a64 + (double)a8), red);
+        const double t2 = block_sum_f64(d2 + ((double)b64 + (double)b8), red);
         if (threadIdx.x == 0) {
             pd1[bid] = t1;
             pd2[bid] = t2;
@@ -327,19 +378,17 @@ int grid_for(size_t n4) {
     return (int)(b < TC_RED_BLOCKS ? (b ? b : 1) : TC_RED_BLOCKS);
 }
 
-}  // namespace
-
-int launch_prior_grad(tc_plan *p, const float *x, float *g, int nb,
-                      const tc_prior *pr, double *h_acc, cudaStream_t s, const float *dot_x) {
+PriorArgs make_prior_args(int n, int nb, const tc_prior *pr) {
     PriorArgs a;
-    a.N = p->k.N;
+    a.N = n;
     a.B = nb;
     a.dims = pr->dims;
     a.p = (float)pr->p;
-    a.inv_sigma = (float)(1.0 / pr->sigma);
     a.c = (float)pr->c;
     a.qexp = (float)(2.0 - pr->p);
-    a.two_lambda = (float)(2.0 * pr->lambda);
+    a.lk = (float)((2.0 - pr->p) * std::log2(1.0 / pr->sigma));
+    a.two_c = (float)(2.0 * pr->c);
+    a.gscale = (float)(2.0 * pr->lambda / (pr->sigma * pr->sigma));
     // w_mn proportional to 1/distance, normalised over the full neighbourhood
     double z;
     if (pr->dims == 3) z = 6.0 + 12.0 / sqrt(2.0) + 8.0 / sqrt(3.0);
@@ -347,6 +396,18 @@ int launch_prior_grad(tc_plan *p, const float *x, float *g, int nb,
     a.w1 = (float)(1.0 / z);
     a.w2 = (float)(1.0 / (sqrt(2.0) * z));
     a.w3 = (float)(1.0 / (sqrt(3.0) * z));
+    return a;
+}
+
+// lambda H from the block partials of sum w d^2 inv over unordered pairs:
+// every pair enters H twice (ordered pairs) and rho = d^2 inv / sigma^2.
+double prior_value_scale(const tc_prior *pr) { return 2.0 * pr->lambda / (pr->sigma * pr->sigma); }
+
+}  // namespace
+
+int launch_prior_grad(tc_plan *p, const float *x, float *g, int nb,
+                      const tc_prior *pr, double *h_acc, cudaStream_t s, const float *dot_x) {
+    const PriorArgs a = make_prior_args(p->k.N, nb, pr);
     dim3 grid((a.N + PTX - 1) / PTX, (a.N + PTY - 1) / PTY);
     const int blocks = grid.x * grid.y;
     if (blocks > p->slot) return TC_ERR_UNSUPPORTED;
@@ -370,7 +431,7 @@ int launch_prior_grad(tc_plan *p, const float *x, float *g, int nb,
         if (!rc) rc = launch_reduce_finalize(p2, blocks, p->scal + SC_DOT_GG, 0, 1.0, s);
         if (rc) return rc;
     }
-    if (h_acc) return launch_reduce_finalize(part, blocks, h_acc, 0, pr->lambda, s);
+    if (h_acc) return launch_reduce_finalize(part, blocks, h_acc, 0, prior_value_scale(pr), s);
     return TC_OK;
 }
 
@@ -454,21 +515,7 @@ int launch_fill_scalars_fresh(tc_plan *p, double t, double k, double restarts,
 int launch_prior_kernel_into(const float *x, float *g, int n, int nb, const tc_prior *pr,
                              double *partials, int max_partials, double *h_out,
                              cudaStream_t s) {
-    PriorArgs a;
-    a.N = n;
-    a.B = nb;
-    a.dims = pr->dims;
-    a.p = (float)pr->p;
-    a.inv_sigma = (float)(1.0 / pr->sigma);
-    a.c = (float)pr->c;
-    a.qexp = (float)(2.0 - pr->p);
-    a.two_lambda = (float)(2.0 * pr->lambda);
-    double z;
-    if (pr->dims == 3) z = 6.0 + 12.0 / sqrt(2.0) + 8.0 / sqrt(3.0);
-    else z = 4.0 + 4.0 / sqrt(2.0);
-    a.w1 = (float)(1.0 / z);
-    a.w2 = (float)(1.0 / (sqrt(2.0) * z));
-    a.w3 = (float)(1.0 / (sqrt(3.0) * z));
+    const PriorArgs a = make_prior_args(n, nb, pr);
     dim3 grid((n + PTX - 1) / PTX, (n + PTY - 1) / PTY);
     const int blocks = grid.x * grid.y;
     if (blocks > max_partials) return TC_ERR_INVALID_ARG;
@@ -478,7 +525,7 @@ int launch_prior_kernel_into(const float *x, float *g, int n, int nb, const tc_p
     else
         TC_PROFILED(TCK_PRIOR, s, (k_prior<false, false><<<grid, PRIOR_THREADS, smem, s>>>(x, g, partials, a, nullptr, nullptr, nullptr)));
     TC_LAUNCHED("k_prior");
-    if (h_out) return launch_reduce_finalize(partials, blocks, h_out, 0, pr->lambda, s);
+    if (h_out) return launch_reduce_finalize(partials, blocks, h_out, 0, prior_value_scale(pr), s);
     return TC_OK;
 }
 

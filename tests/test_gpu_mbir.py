@@ -181,3 +181,29 @@ def test_host_streamed_solve_in_slabs_matches_device_solve(api):
         sh = api.mbir_solve_host(plan, bh, wh, xh, 4, step, prior)
     assert torch.equal(xh, x.cpu())
     assert sh.k == sd.k == 4 and sh.n_restarts == sd.n_restarts
+
+
+@pytest.mark.parametrize("dims", [3, 2])
+def test_prior_on_a_tall_volume_matches_oracle(api, dims):
+    """150 slices of 128^2: tiles inside the volume and at its border, and
+    z marches long enough for every level of the per-thread FP32 -> FP64
+    accumulation of H.  Zero data weights leave the prior term alone."""
+    g, h, go, ho = _tall_prior_case(api, dims)
+    assert rel(g, go) <= 1e-5
+    assert abs(h - ho) <= 1e-5 * ho
+
+
+def _tall_prior_case(api, dims):
+    B, n = 150, 128
+    rng = np.random.default_rng(77 + dims)
+    base = synth.rasterize(n, synth.random_ellipses(n, synth.BASE_SEED + 9))
+    f = np.repeat(base[None], B, axis=0) * np.linspace(0.5, 1.5, B)[:, None, None]
+    f[::7] += 0.05 * rng.standard_normal((len(f[::7]), n, n))   # flat regions and noisy slices
+    f = f.astype(np.float32).astype(np.float64)
+    b = np.zeros((B, 8, 184))
+    prior = api.Prior(lam=1e-3, dims=dims)
+    with api.Plan(n, 8, 184, max_batch=B) as plan:
+        g, obj = api.mbir_grad(plan, t32(f), t32(b), t32(np.zeros_like(b)), prior)
+    pd = dict(p=prior.p, sigma=prior.sigma, c=prior.c)
+    Hv, gh = oracle.prior_value_grad(f, dims, **pd)
+    return np64(g), float(obj.cpu().numpy()[1]), prior.lam * gh, prior.lam * Hv
