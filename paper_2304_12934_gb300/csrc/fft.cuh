@@ -31,9 +31,9 @@ __device__ __forceinline__ float2 mul_si(float2 v) {
 
 // Shared-memory index padding: one float2 of padding after every 16, so the
 // strided butterfly stores of the first stages hit distinct banks.
-__host__ __device__ __forceinline__ int spad(int i) { return i + (i >> 4); }
+__host__ __device__ constexpr int spad(int i) { return i + (i >> 4); }
 // float2 elements to allocate for m padded elements
-__host__ __device__ __forceinline__ int spad_size(int m) { return m + (m >> 4) + 1; }
+__host__ __device__ constexpr int spad_size(int m) { return m + (m >> 4) + 1; }
 
 // In-register DFTs of length 2, 4, 8, 16 (natural order in and out).
 template <int SIGN>
@@ -115,9 +115,8 @@ __device__ __forceinline__ void dft_reg(float2 *v) {
 // Transform stride (in padded elements) for cnt transforms of length n kept
 // back to back: the padded length rounded up to 8 (mod 16), so element i of
 // consecutive transforms falls in different bank halves.
-__host__ __device__ __forceinline__ int fft_tstride(int n) {
-    const int m = spad_size(n);
-    return m + ((24 - (m & 15)) & 15);
+__host__ __device__ constexpr int fft_tstride(int n) {
+    return spad_size(n) + ((24 - (spad_size(n) & 15)) & 15);
 }
 
 // Per-stage twiddle tables of a length-n FFT (n = 2^log2n), concatenated for
@@ -194,6 +193,82 @@ __device__ void fft_pow2(float2 *s, int n, int log2n, int cnt, int ts, const flo
     if (rem == 3) stockham_stage<SIGN, 8, 3, 2>(s, log2n, cnt, ts, 1 << logNs, logNs, tw + toff);
     else if (rem == 2) stockham_stage<SIGN, 4, 2, 4>(s, log2n, cnt, ts, 1 << logNs, logNs, tw + toff);
     else if (rem == 1) stockham_stage<SIGN, 2, 1, 8>(s, log2n, cnt, ts, 1 << logNs, logNs, tw + toff);
+}
+
+// ---------------------------------------------------------------------------
+// The same FFT with the length fixed at compile time (n = 2^LOGN): every
+// shared-memory and twiddle offset within a butterfly is a constant, so each
+// access is a single instruction on a per-thread base address.  The padded
+// index is linear in the butterfly leg q: spad(j + q per) = spad(j) +
+// q (per + per/16) when per is a multiple of 16, and spad(b + q Ns) = spad(b) +
+// q (Ns + Ns/16) for Ns a multiple of 16 (Ns = 1: spad(b) + q, b = R j).
+
+// offset of the twiddle table of the stage starting at Ns = 2^logns
+__host__ __device__ constexpr int fft_twiddle_offset(int logns) {
+    return logns <= 4 ? 0 : fft_twiddle_offset(logns - 4) + (15 << (logns - 4));
+}
+
+template <int SIGN, int LOGN, int LOGR, int LOGNS, int IT>
+__device__ __forceinline__ void stockham_stage_ct(float2 *s, int cnt, const float2 *__restrict__ tw) {
+    constexpr int R = 1 << LOGR, LOGPER = LOGN - LOGR, PER = 1 << LOGPER, NS = 1 << LOGNS;
+    constexpr int TS = fft_tstride(1 << LOGN);
+    constexpr int LSTRIDE = PER + PER / 16;
+    constexpr int SSTRIDE = NS == 1 ? 1 : NS + NS / 16;
+    static_assert(NS == 1 || NS % 16 == 0, "stage offsets assume Ns = 1 or a multiple of 16");
+    const float2 *tws = tw + fft_twiddle_offset(LOGNS);
+    const int nt = blockDim.x, tid = threadIdx.x, total = cnt << LOGPER;
+    float2 v[IT][R];
+#pragma unroll
+    for (int i = 0; i < IT; ++i) {
+        const int it = tid + i * nt;
+        if (it < total) {
+            const int tr = it >> LOGPER, j = it & (PER - 1);
+            const float2 *src = s + tr * TS;
+            if constexpr (PER % 16 == 0) {
+                const float2 *sj = src + spad(j);
+#pragma unroll
+                for (int q = 0; q < R; ++q) v[i][q] = sj[q * LSTRIDE];
+            } else {
+#pragma unroll
+                for (int q = 0; q < R; ++q) v[i][q] = src[spad(j + q * PER)];
+            }
+            if constexpr (LOGNS > 0) {
+                const float2 *tk = tws + (j & (NS - 1));
+#pragma unroll
+                for (int q = 1; q < R; ++q) v[i][q] = cmul(v[i][q], tw_get<SIGN>(tk, (q - 1) * NS));
+            }
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < IT; ++i) {
+        const int it = tid + i * nt;
+        if (it < total) {
+            const int tr = it >> LOGPER, j = it & (PER - 1);
+            dft_reg<SIGN, R>(v[i]);
+            const int base = ((j >> LOGNS) << (LOGNS + LOGR)) + (j & (NS - 1));
+            float2 *dst = s + tr * TS + spad(base);
+#pragma unroll
+            for (int q = 0; q < R; ++q) dst[q * SSTRIDE] = v[i][q];
+        }
+    }
+    __syncthreads();
+}
+
+// In-place FFT of cnt length-2^LOGN transforms at s + t * fft_tstride(n);
+// same stages, tables and requirement (blockDim.x >= cnt * n / 16) as fft_pow2.
+template <int SIGN, int LOGN, int LOGNS = 0>
+__device__ __forceinline__ void fft_ct(float2 *s, int cnt, const float2 *__restrict__ tw) {
+    if constexpr (LOGN - LOGNS >= 4) {
+        stockham_stage_ct<SIGN, LOGN, 4, LOGNS, 1>(s, cnt, tw);
+        fft_ct<SIGN, LOGN, LOGNS + 4>(s, cnt, tw);
+    } else if constexpr (LOGN - LOGNS == 3) {
+        stockham_stage_ct<SIGN, LOGN, 3, LOGNS, 2>(s, cnt, tw);
+    } else if constexpr (LOGN - LOGNS == 2) {
+        stockham_stage_ct<SIGN, LOGN, 2, LOGNS, 4>(s, cnt, tw);
+    } else if constexpr (LOGN - LOGNS == 1) {
+        stockham_stage_ct<SIGN, LOGN, 1, LOGNS, 8>(s, cnt, tw);
+    }
 }
 
 // Out-of-place mixed-radix Stockham; returns the buffer holding the result.

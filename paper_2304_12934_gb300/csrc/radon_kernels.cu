@@ -20,6 +20,8 @@
 //              inverse FFT_G along x evaluated at the N image columns
 //   col pass   Hermitian completion, inverse FFT_G along y at the N image
 //              rows for two columns at once, real part, deapodise
+#include <type_traits>
+
 #include "common.cuh"
 #include "profile.cuh"
 #include "fft.cuh"
@@ -28,15 +30,19 @@ namespace {
 
 // Shared-memory slot of cell c of a G-row kept as two N-point transforms
 // [even cells | odd cells], the even one being transform t0 (stride ts).
-__device__ __forceinline__ int cell_slot(int t0, int ts, int c) {
+__host__ __device__ constexpr int cell_slot(int t0, int ts, int c) {
     return (t0 + (c & 1)) * ts + spad(c >> 1);
 }
 
 // ------------------------------------------------------------ forward ------
+// The pass kernels take the image side as a template parameter (N = 2^LOGN),
+// so their FFTs and shared-memory layouts are fixed at compile time.
+template <int LOGN>
 __global__ void __launch_bounds__(512) k_fwd_col(const float *__restrict__ x, float2 *__restrict__ T,
                           const KArgs g, int CP) {
     extern __shared__ float2 sm[];  // 2CP transforms (stride ts)
-    const int N = g.N, b = blockIdx.y, ts = fft_tstride(N);
+    constexpr int N = 1 << LOGN, ts = fft_tstride(N);
+    const int b = blockIdx.y;
     const int x0base = blockIdx.x * CP * 2;
     const float *xs = x + (size_t)b * N * N;
     for (int idx = threadIdx.x; idx < N * CP; idx += blockDim.x) {
@@ -50,9 +56,9 @@ __global__ void __launch_bounds__(512) k_fwd_col(const float *__restrict__ x, fl
         sm[(pp * 2 + 1) * ts + spad(q)] = cmul(z, g.twG[iy]);
     }
     __syncthreads();
-    fft_pow2<-1>(sm, N, g.log2N, 2 * CP, ts, g.twN);
+    fft_ct<-1, LOGN>(sm, 2 * CP, g.twN);
     float2 *Tb = T + (size_t)b * g.R * N;
-    const int Gm = g.G - 1;
+    constexpr int Gm = 2 * N - 1;
     for (int idx = threadIdx.x; idx < g.R * CP; idx += blockDim.x) {
         const int pp = idx % CP, r = idx / CP;
         const int jy = g.jmin + r;
@@ -68,10 +74,12 @@ __global__ void __launch_bounds__(512) k_fwd_col(const float *__restrict__ x, fl
     }
 }
 
+template <int LOGN>
 __global__ void __launch_bounds__(512) k_fwd_row(const float2 *__restrict__ T, float2 *__restrict__ P,
                           const KArgs g) {
     extern __shared__ float2 sm[];  // 2 transforms (stride ts)
-    const int N = g.N, r = blockIdx.x, b = blockIdx.y, ts = fft_tstride(N);
+    constexpr int N = 1 << LOGN, ts = fft_tstride(N);
+    const int r = blockIdx.x, b = blockIdx.y;
     const float2 *Tr = T + ((size_t)b * g.R + r) * N;
     for (int ix = threadIdx.x; ix < N; ix += blockDim.x) {
         const float2 v = Tr[ix];
@@ -80,10 +88,10 @@ __global__ void __launch_bounds__(512) k_fwd_row(const float2 *__restrict__ T, f
         sm[ts + spad(q)] = cmul(v, g.twG[ix]);
     }
     __syncthreads();
-    fft_pow2<-1>(sm, N, g.log2N, 2, ts, g.twN);
+    fft_ct<-1, LOGN>(sm, 2, g.twN);
     float2 *Pb = P + (size_t)b * g.w * g.AM;
     const int e1 = g.row_off[r + 1];
-    const int Gm = g.G - 1;
+    constexpr int Gm = 2 * N - 1;
     for (int e = g.row_off[r] + threadIdx.x; e < e1; e += blockDim.x) {
         const int4 en = g.ent[e];
         const int key = entry_key(en);
@@ -233,11 +241,13 @@ __global__ void __launch_bounds__(512) k_adj_det(const float *__restrict__ ysino
 // (the few wrap-around duplicates at the spectrum edge are flagged and added
 // serially), so no two threads touch a cell and every cell's summation order
 // is fixed: atomic-free and bit-reproducible.
+template <int LOGN>
 __global__ void __launch_bounds__(512) k_adj_row(const float2 *__restrict__ V, float2 *__restrict__ U,
                           const KArgs g) {
     extern __shared__ float2 sm[];
-    const int N = g.N, G = g.G, r = blockIdx.x, b = blockIdx.y;
-    const int ts = fft_tstride(N), hsz = 2 * ts;                  // grid row: 2 transforms
+    constexpr int N = 1 << LOGN, G = 2 * N;
+    constexpr int ts = fft_tstride(N), hsz = 2 * ts;              // grid row: 2 transforms
+    const int r = blockIdx.x, b = blockIdx.y;
     float2 *cu = sm + hsz;                                         // [SPREAD_CHUNK]
     float *cex = reinterpret_cast<float *>(cu + SPREAD_CHUNK);     // [SPREAD_CHUNK]
     short *ckey = reinterpret_cast<short *>(cex + SPREAD_CHUNK);   // [SPREAD_CHUNK]
@@ -280,7 +290,7 @@ __global__ void __launch_bounds__(512) k_adj_row(const float2 *__restrict__ V, f
         }
         __syncthreads();
     }
-    fft_pow2<+1>(sm, N, g.log2N, 2, ts, g.twN);
+    fft_ct<+1, LOGN>(sm, 2, g.twN);
     float2 *Ur = U + ((size_t)b * g.R + r) * N;
     for (int ix = threadIdx.x; ix < N; ix += blockDim.x) {
         const int q = (ix - N / 2) & (N - 1);
@@ -288,10 +298,12 @@ __global__ void __launch_bounds__(512) k_adj_row(const float2 *__restrict__ V, f
     }
 }
 
+template <int LOGN>
 __global__ void __launch_bounds__(512) k_adj_col(const float2 *__restrict__ U, float *__restrict__ x,
                           const KArgs g, int CP) {
     extern __shared__ float2 sm[];  // 2CP transforms (stride ts)
-    const int N = g.N, G = g.G, b = blockIdx.y, ts = fft_tstride(N);
+    constexpr int N = 1 << LOGN, G = 2 * N, ts = fft_tstride(N);
+    const int b = blockIdx.y;
     const int x0base = blockIdx.x * CP * 2;
     const float2 *Ub = U + (size_t)b * g.R * N;
     const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -311,7 +323,7 @@ __global__ void __launch_bounds__(512) k_adj_col(const float2 *__restrict__ U, f
         sm[cell_slot(pp * 2, ts, jy)] = make_float2(h0x - h1y, h0y + h1x);
     }
     __syncthreads();
-    fft_pow2<+1>(sm, N, g.log2N, 2 * CP, ts, g.twN);
+    fft_ct<+1, LOGN>(sm, 2 * CP, g.twN);
     float *xb = x + (size_t)b * N * N;
     for (int idx = threadIdx.x; idx < N * CP; idx += blockDim.x) {
         const int pp = idx % CP, iy = idx / CP;
@@ -325,6 +337,24 @@ __global__ void __launch_bounds__(512) k_adj_col(const float2 *__restrict__ U, f
     }
 }
 
+// Calls f(std::integral_constant<int, L>) for the supported image sides
+// N = 2^L, 16 <= N <= 4096.
+template <class F>
+int with_logn(int lg, F &&f) {
+    switch (lg) {
+        case 4: return f(std::integral_constant<int, 4>{});
+        case 5: return f(std::integral_constant<int, 5>{});
+        case 6: return f(std::integral_constant<int, 6>{});
+        case 7: return f(std::integral_constant<int, 7>{});
+        case 8: return f(std::integral_constant<int, 8>{});
+        case 9: return f(std::integral_constant<int, 9>{});
+        case 10: return f(std::integral_constant<int, 10>{});
+        case 11: return f(std::integral_constant<int, 11>{});
+        case 12: return f(std::integral_constant<int, 12>{});
+        default: return TC_ERR_UNSUPPORTED;
+    }
+}
+
 }  // namespace
 
 int launch_radon_fwd_chunk(tc_plan *p, const float *x, float *y, int nb,
@@ -332,11 +362,16 @@ int launch_radon_fwd_chunk(tc_plan *p, const float *x, float *y, int nb,
                            double *obj_acc, cudaStream_t s) {
     const KArgs &g = p->k;
     dim3 gc(g.N / (2 * p->cp_col), nb);
-    TC_PROFILED(TCK_FWD_COL, s, k_fwd_col<<<gc, p->threads_col, p->smem_col, s>>>(x, p->tu, g, p->cp_col));
-    TC_LAUNCHED("k_fwd_col");
     dim3 gr(g.R, nb);
-    TC_PROFILED(TCK_FWD_ROW, s, k_fwd_row<<<gr, p->threads_row, p->smem_row_fwd, s>>>(p->tu, p->pv, g));
-    TC_LAUNCHED("k_fwd_row");
+    int rc = with_logn(g.log2N, [&](auto L) {
+        constexpr int LG = decltype(L)::value;
+        TC_PROFILED(TCK_FWD_COL, s, k_fwd_col<LG><<<gc, p->threads_col, p->smem_col, s>>>(x, p->tu, g, p->cp_col));
+        TC_LAUNCHED("k_fwd_col");
+        TC_PROFILED(TCK_FWD_ROW, s, k_fwd_row<LG><<<gr, p->threads_row, p->smem_row_fwd, s>>>(p->tu, p->pv, g));
+        TC_LAUNCHED("k_fwd_row");
+        return TC_OK;
+    });
+    if (rc) return rc;
     dim3 gd((g.A + 1) / 2, nb);
     int mode = 0;
     if (y) mode |= DET_WRITE_Y;
@@ -348,7 +383,7 @@ int launch_radon_fwd_chunk(tc_plan *p, const float *x, float *y, int nb,
         TC_PROFILED(TCK_FWD_DET, s, k_fwd_det<false><<<gd, p->threads_det, p->smem_det, s>>>(p->pv, y, b, w, resid, p->partials, g, mode));
     TC_LAUNCHED("k_fwd_det");
     if (mode & DET_OBJ) {
-        int rc = launch_reduce_finalize(p->partials, gd.x * gd.y, obj_acc, 1, 1.0, s);
+        rc = launch_reduce_finalize(p->partials, gd.x * gd.y, obj_acc, 1, 1.0, s);
         if (rc) return rc;
     }
     return TC_OK;
@@ -364,12 +399,15 @@ int launch_radon_adj_chunk(tc_plan *p, const float *y, float *x, int nb,
         TC_PROFILED(TCK_ADJ_DET, s, k_adj_det<false><<<gd, p->threads_det, p->smem_det, s>>>(y, p->pv, g));
     TC_LAUNCHED("k_adj_det");
     dim3 gr(g.R, nb);
-    TC_PROFILED(TCK_ADJ_ROW, s, k_adj_row<<<gr, p->threads_row, p->smem_row_adj, s>>>(p->pv, p->tu, g));
-    TC_LAUNCHED("k_adj_row");
     dim3 gc(g.N / (2 * p->cp_col), nb);
-    TC_PROFILED(TCK_ADJ_COL, s, k_adj_col<<<gc, p->threads_col, p->smem_col, s>>>(p->tu, x, g, p->cp_col));
-    TC_LAUNCHED("k_adj_col");
-    return TC_OK;
+    return with_logn(g.log2N, [&](auto L) {
+        constexpr int LG = decltype(L)::value;
+        TC_PROFILED(TCK_ADJ_ROW, s, k_adj_row<LG><<<gr, p->threads_row, p->smem_row_adj, s>>>(p->pv, p->tu, g));
+        TC_LAUNCHED("k_adj_row");
+        TC_PROFILED(TCK_ADJ_COL, s, k_adj_col<LG><<<gc, p->threads_col, p->smem_col, s>>>(p->tu, x, g, p->cp_col));
+        TC_LAUNCHED("k_adj_col");
+        return TC_OK;
+    });
 }
 
 // The dynamic shared-memory limit is an attribute of the kernel (process
@@ -390,10 +428,16 @@ int radon_configure_kernels(tc_plan *p) {
         const size_t sm = (size_t)(2 * cp * fft_tstride(p->k.N)) * 8;
         if (sm <= 200 * 1024 && sm > col_max) col_max = sm;
     }
-    int rc;
-    if ((rc = raise_smem_limit(k_fwd_col, col_max)) || (rc = raise_smem_limit(k_adj_col, col_max)) ||
-        (rc = raise_smem_limit(k_fwd_row, p->smem_row_fwd)) ||
-        (rc = raise_smem_limit(k_adj_row, p->smem_row_adj)) ||
+    int rc = with_logn(p->k.log2N, [&](auto L) {
+        constexpr int LG = decltype(L)::value;
+        int e;
+        if ((e = raise_smem_limit(k_fwd_col<LG>, col_max)) || (e = raise_smem_limit(k_adj_col<LG>, col_max)) ||
+            (e = raise_smem_limit(k_fwd_row<LG>, p->smem_row_fwd)) ||
+            (e = raise_smem_limit(k_adj_row<LG>, p->smem_row_adj)))
+            return e;
+        return TC_OK;
+    });
+    if (rc ||
         (rc = raise_smem_limit(k_fwd_det<true>, p->smem_det)) ||
         (rc = raise_smem_limit(k_adj_det<true>, p->smem_det)) ||
         (rc = raise_smem_limit(k_fwd_det<false>, p->smem_det)) ||
