@@ -116,15 +116,19 @@ __device__ __forceinline__ float es_kernel(float z, float beta) {
     return q > 0.0f ? expf(beta * (sqrtf(q) - 1.0f)) : 0.0f;
 }
 
-// The same kernel with beta_l2 = beta * log2(e), approximate reciprocal square
-// root and exp2 (relative error ~1e-7, well inside the NUFFT's own error).
+// The same kernel with beta_l2 = beta * log2(e), through the one-instruction
+// approximate square root and exp2 (relative errors ~1e-7, well inside the
+// NUFFT's own error; denormals flushed).  Zero outside |z| < 1.
 __device__ __forceinline__ float es_kernel_fast(float z, float beta_l2) {
-    const float q = 1.0f - z * z;
-    return q > 0.0f ? exp2f(beta_l2 * (q * rsqrtf(q) - 1.0f)) : 0.0f;
+    const float q = fmaf(-z, z, 1.0f);
+    float r, e;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(q));
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(fmaf(beta_l2, r, -beta_l2)));
+    return q > 0.0f ? e : 0.0f;
 }
 
 // Entries of one grid row staged per chunk by the spreading kernel.
-#define SPREAD_CHUNK 1536
+#define SPREAD_CHUNK 512
 
 // Block-wide FP64 sum of one float per thread; thread 0 gets the total.
 __device__ __forceinline__ double block_sum_f64(double d, double *red) {

@@ -514,7 +514,7 @@ int tc_plan_build(const tc_geom *geom, int max_batch, tc_plan **out) {
     p->threads_row = std::max(128, N / 8);
     p->threads_det = k.blue ? std::max(256, k.L / 16) : 256;
     p->smem_row_fwd = (size_t)(2 * fft_tstride(N)) * sizeof(float2);
-    p->smem_row_adj = p->smem_row_fwd + (size_t)SPREAD_CHUNK * (sizeof(float2) + sizeof(float) + sizeof(short));
+    p->smem_row_adj = p->smem_row_fwd + (size_t)SPREAD_CHUNK * sizeof(float4);
     p->smem_det = k.blue ? (size_t)spad_size(k.L) * sizeof(float2)
                          : (size_t)(3 * D + k.rp.rad[0]) * sizeof(float2);
     if (p->threads_row > 512 || p->smem_det > 200 * 1024 || p->smem_row_adj > 200 * 1024) {

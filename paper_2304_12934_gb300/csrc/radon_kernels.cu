@@ -95,10 +95,11 @@ __global__ void __launch_bounds__(512) k_fwd_row(const float2 *__restrict__ T, f
     for (int e = g.row_off[r] + threadIdx.x; e < e1; e += blockDim.x) {
         const int4 en = g.ent[e];
         const int key = entry_key(en);
-        const float ex = entry_ex(en);
+        const float nexh = -entry_ex(en) * g.inv_h;
         float2 acc = make_float2(0.f, 0.f);
         for (int t = 0; t < g.w; ++t) {
-            const float wt = es_kernel_fast(((float)t - ex) * g.inv_h, g.beta_l2);
+            // z = (t - ex) / h, formed exactly as in the spreading kernel
+            const float wt = es_kernel_fast(fmaf((float)t, g.inv_h, nexh), g.beta_l2);
             cfma(acc, wt, sm[cell_slot(0, ts, (key + t) & Gm)]);
         }
         Pb[(size_t)entry_s(en) * g.AM + entry_p(en)] = cscale(acc, entry_wy(en));
@@ -231,9 +232,25 @@ __global__ void __launch_bounds__(512) k_adj_det(const float *__restrict__ ysino
     }
 }
 
+// Sum over the staged entries lo..hi-1 covering cell cs of u phi((cs - key -
+// ex) / h); cs - key is an exact small integer, so the weight is bitwise the
+// one the interpolation uses for the same (entry, cell).
+__device__ __forceinline__ float2 spread_record(const float4 *__restrict__ ce, int cs, int lo, int hi,
+                                                const KArgs &g) {
+    const float csf = (float)cs;
+    float2 acc = make_float2(0.f, 0.f);
+    for (int i = lo; i < hi; ++i) {
+        const float4 e = ce[i];
+        const float wt = es_kernel_fast(fmaf(csf - e.z, g.inv_h, e.w), g.beta_l2);
+        acc.x = fmaf(wt, e.x, acc.x);
+        acc.y = fmaf(wt, e.y, acc.y);
+    }
+    return acc;
+}
+
 // Spreading of one grid row, atomic-free.  The row's (point, tap) entries are
 // sorted by jx0 (the key) and taken in chunks: every thread stages one
-// entry's u = phi_y * V[p], gx - jx0 and key in shared memory.  The plan holds
+// entry's u = phi_y * V[p], key and -(gx - jx0) / h in shared memory.  The plan holds
 // one record per touched cell of the chunk, naming the contiguous range of
 // entries whose footprint covers that cell (keys in [cell - w + 1, cell]);
 // one thread per record sums u * phi(cell - key - (gx - jx0)) over its range
@@ -248,9 +265,8 @@ __global__ void __launch_bounds__(512) k_adj_row(const float2 *__restrict__ V, f
     constexpr int N = 1 << LOGN, G = 2 * N;
     constexpr int ts = fft_tstride(N), hsz = 2 * ts;              // grid row: 2 transforms
     const int r = blockIdx.x, b = blockIdx.y;
-    float2 *cu = sm + hsz;                                         // [SPREAD_CHUNK]
-    float *cex = reinterpret_cast<float *>(cu + SPREAD_CHUNK);     // [SPREAD_CHUNK]
-    short *ckey = reinterpret_cast<short *>(cex + SPREAD_CHUNK);   // [SPREAD_CHUNK]
+    // staged entries: (u = phi_y V[p], key, -ex / h); hsz is even, so 16-byte aligned
+    float4 *ce = reinterpret_cast<float4 *>(sm + hsz);             // [SPREAD_CHUNK]
     const int e0 = g.row_off[r], e1 = g.row_off[r + 1];
     for (int c = threadIdx.x; c < hsz; c += blockDim.x) sm[c] = make_float2(0.f, 0.f);
     const float2 *Vb = V + (size_t)b * g.w * g.AM;
@@ -259,19 +275,15 @@ __global__ void __launch_bounds__(512) k_adj_row(const float2 *__restrict__ V, f
         const int n = (e1 - c0) < SPREAD_CHUNK ? (e1 - c0) : SPREAD_CHUNK;
         for (int i = threadIdx.x; i < n; i += blockDim.x) {
             const int4 en = g.ent[c0 + i];
-            cu[i] = cscale(Vb[entry_p(en)], entry_wy(en));
-            cex[i] = entry_ex(en);
-            ckey[i] = (short)entry_key(en);
+            const float2 u = cscale(Vb[entry_p(en)], entry_wy(en));
+            ce[i] = make_float4(u.x, u.y, (float)entry_key(en), -entry_ex(en) * g.inv_h);
         }
         __syncthreads();
         const int rb = roff[2 * kc], rs = roff[2 * kc + 1], re = roff[2 * kc + 2];
         for (int q = rb + threadIdx.x; q < rs; q += blockDim.x) {
             const int2 rc = g.rec[q];
             const int cs = (rc.x & 0x7fff) + g.kmin;
-            const int lo = rc.y & 0xffff, hi = rc.y >> 16;
-            float2 acc = make_float2(0.f, 0.f);
-            for (int i = lo; i < hi; ++i)
-                cfma(acc, es_kernel_fast(((float)(cs - ckey[i]) - cex[i]) * g.inv_h, g.beta_l2), cu[i]);
+            const float2 acc = spread_record(ce, cs, rc.y & 0xffff, rc.y >> 16, g);
             float2 &hc = sm[cell_slot(0, ts, cs & (G - 1))];
             hc = cadd(hc, acc);
         }
@@ -280,10 +292,7 @@ __global__ void __launch_bounds__(512) k_adj_row(const float2 *__restrict__ V, f
             for (int q = rs; q < re; ++q) {  // seam records, in order
                 const int2 rc = g.rec[q];
                 const int cs = (rc.x & 0x7fff) + g.kmin;
-                const int lo = rc.y & 0xffff, hi = rc.y >> 16;
-                float2 acc = make_float2(0.f, 0.f);
-                for (int i = lo; i < hi; ++i)
-                    cfma(acc, es_kernel_fast(((float)(cs - ckey[i]) - cex[i]) * g.inv_h, g.beta_l2), cu[i]);
+                const float2 acc = spread_record(ce, cs, rc.y & 0xffff, rc.y >> 16, g);
                 float2 &hc = sm[cell_slot(0, ts, cs & (G - 1))];
                 hc = cadd(hc, acc);
             }
