@@ -58,10 +58,11 @@ __device__ __forceinline__ float qggmrf_e(float d, const PriorArgs &a, float &in
 // neighbour pair is evaluated once, at its lower voxel, along the 13 forward
 // directions (9 towards z+1, 4 in-plane); both voxels read the pair's rho'
 // from shared memory (the z+1 pairs are kept for the voxel above).
-// Buffers: the z+1 pair values rotate over three slots and the in-plane ones
-// over two, so a step's writes never touch what the previous step's gradient
-// phase still reads; with the plane double buffer this needs two barriers per
-// z step.  dims = 2 skips the z pairs and uses the 8-neighbour weights.
+// Buffers: pair values towards z+1 alternate between two slots (a step's
+// gradient phase reads the previous step's), the in-plane ones use one; the
+// barrier that opens each step orders all reads of the previous step before
+// its writes.  With the plane double buffer that is two barriers per z step.
+// dims = 2 skips the z pairs and uses the 8-neighbour weights.
 // A CTA whose ring lies inside the volume evaluates every direction at every
 // ring cell without per-pair tests (the pairs that leave the ring are never
 // read); CTAs at the volume border test each pair against the border rule.
@@ -77,23 +78,28 @@ __device__ __forceinline__ float qggmrf_e(float d, const PriorArgs &a, float &in
 #define PRS (PRX * PRY)
 #define PRIOR_THREADS 480
 #define PRIOR_FPAD 36  // front pad: unmasked halo reads reach PRX + 1 cells before a plane
-#define PRIOR_SMEM_FLOATS (PRIOR_FPAD + 2 * PRS + 3 * 9 * PRS + 2 * 4 * PRS)
+#define PRIOR_UP_SLOTS 2    // buffers of z+1 pair values
+#define PRIOR_PL_SLOTS 1    // buffers of in-plane pair values
+#define PRIOR_MIN_BLOCKS 4  // 46 KB of shared memory and <= 32 registers: 60 warps per SM
+#define PRIOR_SMEM_FLOATS (PRIOR_FPAD + 2 * PRS + PRIOR_UP_SLOTS * 9 * PRS + PRIOR_PL_SLOTS * 4 * PRS)
 
 // z+1 pairs of one ring cell: fc / fn point at the cell in planes z and z+1,
 // eu at its slot of the current z+1 buffer.
+// gs accumulates the cell's own (forward) share of the gradient sum, w e.
 template <bool MASKED, bool WANT_H>
 __device__ __forceinline__ void prior_up_pairs(const float *fn, float fm, float *eu, unsigned mu,
-                                               const PriorArgs &a, float &hs) {
+                                               const PriorArgs &a, float &gs, float &hs) {
 #pragma unroll
     for (int u = 0; u < 9; ++u) {
         const int dx = u % 3 - 1, dy = u / 3 - 1;
+        const float wu = (dx == 0 && dy == 0) ? a.w1 : ((dx == 0 || dy == 0) ? a.w2 : a.w3);
         float e = 0.f;
         if (!MASKED || (mu & (1u << u))) {
             float inv;
             const float d = fm - fn[dy * PRX + dx];
             e = qggmrf_e(d, a, inv);
-            if (WANT_H)
-                hs = fmaf((dx == 0 && dy == 0) ? a.w1 : ((dx == 0 || dy == 0) ? a.w2 : a.w3), d * d * inv, hs);
+            gs = fmaf(wu, e, gs);
+            if (WANT_H) hs = fmaf(wu, d * d * inv, hs);
         }
         eu[u * PRS] = e;
     }
@@ -105,29 +111,31 @@ __device__ __forceinline__ int pl_dy(int q) { return q == 0 ? 0 : 1; }
 
 template <bool MASKED, bool WANT_H>
 __device__ __forceinline__ void prior_plane_pairs(const float *fc, float fm, float *ep, unsigned mp,
-                                                  const PriorArgs &a, float &hs) {
+                                                  const PriorArgs &a, float &gs, float &hs) {
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
+        const float wq = (q & 1) ? a.w2 : a.w1;
         float e = 0.f;
         if (!MASKED || (mp & (1u << q))) {
             float inv;
             const float d = fm - fc[pl_dy(q) * PRX + pl_dx(q)];
             e = qggmrf_e(d, a, inv);
-            if (WANT_H) hs = fmaf((q & 1) ? a.w2 : a.w1, d * d * inv, hs);
+            gs = fmaf(wq, e, gs);
+            if (WANT_H) hs = fmaf(wq, d * d * inv, hs);
         }
         ep[q * PRS] = e;
     }
 }
 
 template <bool WANT_H, bool DOTS>
-__global__ void __launch_bounds__(PRIOR_THREADS) k_prior(const float *__restrict__ f, float *__restrict__ g,
+__global__ void __launch_bounds__(PRIOR_THREADS, PRIOR_MIN_BLOCKS) k_prior(const float *__restrict__ f, float *__restrict__ g,
                                                           double *__restrict__ partials, const PriorArgs a,
                                                           const float *__restrict__ xprev,
                                                           double *__restrict__ pd1, double *__restrict__ pd2) {
     extern __shared__ float psm[];
     float *fpl = psm + PRIOR_FPAD;    // [2][PRS]
     float *Eu = fpl + 2 * PRS;        // [3][9][PRS]
-    float *Ep = Eu + 3 * 9 * PRS;     // [2][4][PRS]
+    float *Ep = Eu + PRIOR_UP_SLOTS * 9 * PRS;  // [PRIOR_PL_SLOTS][4][PRS]
     __shared__ double red[32];
     const int N = a.N, B = a.B;
     const size_t NN = (size_t)N * N;
@@ -168,7 +176,7 @@ __global__ void __launch_bounds__(PRIOR_THREADS) k_prior(const float *__restrict
     }
     if (ring) {
         for (int u = 0; u < 9; ++u)
-            for (int sl = 0; sl < 3; ++sl) Eu[(sl * 9 + u) * PRS + h] = 0.f;
+            for (int sl = 0; sl < PRIOR_UP_SLOTS; ++sl) Eu[(sl * 9 + u) * PRS + h] = 0.f;
         fpl[h] = inb ? f[(size_t)y * N + x] : 0.f;
     }
     // register prefetch: the plane the next step stores (3D: z + 2, 2D: z + 1)
@@ -176,7 +184,7 @@ __global__ void __launch_bounds__(PRIOR_THREADS) k_prior(const float *__restrict
     float f_nx = (inb && B > 1) ? f[NN + off] : 0.f;
     float h8 = 0.f, h64 = 0.f, a8 = 0.f, a64 = 0.f, b8 = 0.f, b64 = 0.f;
     double hacc = 0.0, d1 = 0.0, d2 = 0.0;
-    int s3 = 0, p3 = 2;  // this step's / previous step's z+1 slot (z mod 3, (z + 2) mod 3)
+    int s3 = 0, p3 = PRIOR_UP_SLOTS - 1;  // this step's / previous step's z+1 slot
     for (int z = 0; z < B; ++z) {
         const int cur = z & 1, nxt = cur ^ 1;
         const bool up = three && z + 1 < B;
@@ -190,38 +198,39 @@ __global__ void __launch_bounds__(PRIOR_THREADS) k_prior(const float *__restrict
             else if (!three && z > 0) fpl[cur * PRS + h] = f_nx;  // 2D: slices are independent
         }
         __syncthreads();
-        float hs = 0.f, fm = 0.f;
+        float hs = 0.f, fm = 0.f, gs = 0.f;
         if (ring) {
             const float *fc = fpl + cur * PRS + h;
             fm = *fc;
             float *eu = Eu + (s3 * 9) * PRS + h;
             if (up) {
-                if (full) prior_up_pairs<false, WANT_H>(fpl + nxt * PRS + h, fm, eu, 0u, a, hs);
-                else prior_up_pairs<true, WANT_H>(fpl + nxt * PRS + h, fm, eu, mup, a, hs);
+                if (full) prior_up_pairs<false, WANT_H>(fpl + nxt * PRS + h, fm, eu, 0u, a, gs, hs);
+                else prior_up_pairs<true, WANT_H>(fpl + nxt * PRS + h, fm, eu, mup, a, gs, hs);
             } else if (three) {
 #pragma unroll
                 for (int u = 0; u < 9; ++u) eu[u * PRS] = 0.f;
             }
-            float *ep = Ep + (cur * 4) * PRS + h;
-            if (full) prior_plane_pairs<false, WANT_H>(fc, fm, ep, 0u, a, hs);
-            else prior_plane_pairs<true, WANT_H>(fc, fm, ep, mpl, a, hs);
+            float *ep = Ep + ((z % PRIOR_PL_SLOTS) * 4) * PRS + h;
+            if (full) prior_plane_pairs<false, WANT_H>(fc, fm, ep, 0u, a, gs, hs);
+            else prior_plane_pairs<true, WANT_H>(fc, fm, ep, mpl, a, gs, hs);
         }
         __syncthreads();
         if (interior) {
-            float gs = 0.f;
+            // minus the shares of the pairs this voxel closes (evaluated at
+            // their lower voxels: in-plane this step, towards z+1 the last)
             if (three) {
-                const float *ec = Eu + (s3 * 9) * PRS + h, *epv = Eu + (p3 * 9) * PRS + h;
+                const float *epv = Eu + (p3 * 9) * PRS + h;
 #pragma unroll
                 for (int u = 0; u < 9; ++u) {
                     const int dx = u % 3 - 1, dy = u / 3 - 1;
                     const float wu = (dx == 0 && dy == 0) ? a.w1 : ((dx == 0 || dy == 0) ? a.w2 : a.w3);
-                    gs = fmaf(wu, ec[u * PRS] - epv[u * PRS - dy * PRX - dx], gs);
+                    gs = fmaf(-wu, epv[u * PRS - dy * PRX - dx], gs);
                 }
             }
-            const float *ep = Ep + (cur * 4) * PRS + h;
+            const float *ep = Ep + ((z % PRIOR_PL_SLOTS) * 4) * PRS + h;
 #pragma unroll
             for (int q = 0; q < 4; ++q)
-                gs = fmaf((q & 1) ? a.w2 : a.w1, ep[q * PRS] - ep[q * PRS - pl_dy(q) * PRX - pl_dx(q)], gs);
+                gs = fmaf((q & 1) ? -a.w2 : -a.w1, ep[q * PRS - pl_dy(q) * PRX - pl_dx(q)], gs);
             const float gn = fmaf(a.gscale, gs, g_old);
             g[i] = gn;
             if (WANT_H) h8 += hs;
@@ -244,7 +253,7 @@ __global__ void __launch_bounds__(PRIOR_THREADS) k_prior(const float *__restrict
         }
         f_nx = f_pf;
         p3 = s3;
-        s3 = s3 == 2 ? 0 : s3 + 1;
+        s3 = s3 == PRIOR_UP_SLOTS - 1 ? 0 : s3 + 1;
     }
     const int bid = blockIdx.y * gridDim.x + blockIdx.x;
     if (WANT_H) {
