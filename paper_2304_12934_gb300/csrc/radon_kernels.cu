@@ -45,6 +45,7 @@ __global__ void __launch_bounds__(512) k_fwd_col(const float *__restrict__ x, fl
     const int b = blockIdx.y;
     const int x0base = blockIdx.x * CP * 2;
     const float *xs = x + (size_t)b * N * N;
+#pragma unroll 8
     for (int idx = threadIdx.x; idx < N * CP; idx += blockDim.x) {
         const int pp = idx % CP, iy = idx / CP;
         const int xc = x0base + 2 * pp;
@@ -59,6 +60,7 @@ __global__ void __launch_bounds__(512) k_fwd_col(const float *__restrict__ x, fl
     fft_ct<-1, LOGN>(sm, 2 * CP, g.twN);
     float2 *Tb = T + (size_t)b * g.R * N;
     constexpr int Gm = 2 * N - 1;
+#pragma unroll 4
     for (int idx = threadIdx.x; idx < g.R * CP; idx += blockDim.x) {
         const int pp = idx % CP, r = idx / CP;
         const int jy = g.jmin + r;
@@ -81,6 +83,7 @@ __global__ void __launch_bounds__(512) k_fwd_row(const float2 *__restrict__ T, f
     constexpr int N = 1 << LOGN, ts = fft_tstride(N);
     const int r = blockIdx.x, b = blockIdx.y;
     const float2 *Tr = T + ((size_t)b * g.R + r) * N;
+#pragma unroll 8
     for (int ix = threadIdx.x; ix < N; ix += blockDim.x) {
         const float2 v = Tr[ix];
         const int q = (ix - N / 2) & (N - 1);
@@ -273,6 +276,7 @@ __global__ void __launch_bounds__(512) k_adj_row(const float2 *__restrict__ V, f
     const int *roff = g.rec_off + (size_t)r * (2 * g.nch + 1);
     for (int kc = 0, c0 = e0; c0 < e1; ++kc, c0 += SPREAD_CHUNK) {
         const int n = (e1 - c0) < SPREAD_CHUNK ? (e1 - c0) : SPREAD_CHUNK;
+#pragma unroll 2
         for (int i = threadIdx.x; i < n; i += blockDim.x) {
             const int4 en = g.ent[c0 + i];
             const float2 u = cscale(Vb[entry_p(en)], entry_wy(en));
@@ -301,6 +305,7 @@ __global__ void __launch_bounds__(512) k_adj_row(const float2 *__restrict__ V, f
     }
     fft_ct<+1, LOGN>(sm, 2, g.twN);
     float2 *Ur = U + ((size_t)b * g.R + r) * N;
+#pragma unroll 4
     for (int ix = threadIdx.x; ix < N; ix += blockDim.x) {
         const int q = (ix - N / 2) & (N - 1);
         Ur[ix] = cadd(sm[spad(q)], cmul(sm[ts + spad(q)], cconj(g.twG[ix])));
@@ -316,6 +321,7 @@ __global__ void __launch_bounds__(512) k_adj_col(const float2 *__restrict__ U, f
     const int x0base = blockIdx.x * CP * 2;
     const float2 *Ub = U + (size_t)b * g.R * N;
     const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 8
     for (int idx = threadIdx.x; idx < G * CP; idx += blockDim.x) {
         const int pp = idx % CP, jy = idx / CP;
         const int xc = x0base + 2 * pp;
@@ -334,6 +340,7 @@ __global__ void __launch_bounds__(512) k_adj_col(const float2 *__restrict__ U, f
     __syncthreads();
     fft_ct<+1, LOGN>(sm, 2 * CP, g.twN);
     float *xb = x + (size_t)b * N * N;
+#pragma unroll 4
     for (int idx = threadIdx.x; idx < N * CP; idx += blockDim.x) {
         const int pp = idx % CP, iy = idx / CP;
         const int xc = x0base + 2 * pp;
