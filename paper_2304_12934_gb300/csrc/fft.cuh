@@ -124,7 +124,7 @@ __host__ __device__ constexpr int fft_tstride(int n) {
 // [(q - 1) * Ns + k], q = 1..R-1, k = 0..Ns-1, so the lanes of a warp (k
 // consecutive) read consecutive words (coalesced global / L1 reads).  Total
 // entries: fft_twiddle_count(n).
-__host__ __device__ __forceinline__ int fft_twiddle_count(int log2n) {
+__host__ __device__ constexpr int fft_twiddle_count(int log2n) {
     int logNs = 0, total = 0;
     while (log2n - logNs > 0) {
         const int lr = (log2n - logNs >= 4) ? 4 : (log2n - logNs);
@@ -233,9 +233,26 @@ __device__ __forceinline__ void stockham_stage_ct(float2 *s, int cnt, const floa
                 for (int q = 0; q < R; ++q) v[i][q] = src[spad(j + q * PER)];
             }
             if constexpr (LOGNS > 0) {
+                // W^q for q = 1..R-1 from the table entries at q = 1, 2, 4, 8:
+                // the other powers are products of at most three of them.
                 const float2 *tk = tws + (j & (NS - 1));
+                float2 w[R];
+                w[1] = tw_get<SIGN>(tk, 0);
+                if constexpr (R > 2) w[2] = tw_get<SIGN>(tk, NS);
+                if constexpr (R > 4) w[4] = tw_get<SIGN>(tk, 3 * NS);
+                if constexpr (R > 8) w[8] = tw_get<SIGN>(tk, 7 * NS);
+                if constexpr (R > 2) w[3] = cmul(w[2], w[1]);
+                if constexpr (R > 4) {
+                    w[5] = cmul(w[4], w[1]);
+                    w[6] = cmul(w[4], w[2]);
+                    w[7] = cmul(w[4], w[3]);
+                }
+                if constexpr (R > 8) {
 #pragma unroll
-                for (int q = 1; q < R; ++q) v[i][q] = cmul(v[i][q], tw_get<SIGN>(tk, (q - 1) * NS));
+                    for (int q = 9; q < 16; ++q) w[q] = cmul(w[8], w[q - 8]);
+                }
+#pragma unroll
+                for (int q = 1; q < R; ++q) v[i][q] = cmul(v[i][q], w[q]);
             }
         }
     }

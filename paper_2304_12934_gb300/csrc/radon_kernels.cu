@@ -45,13 +45,15 @@ __global__ void __launch_bounds__(512) k_fwd_col(const float *__restrict__ x, fl
     const int b = blockIdx.y;
     const int x0base = blockIdx.x * CP * 2;
     const float *xs = x + (size_t)b * N * N;
+    // blockDim.x is a multiple of CP, so a thread keeps its column pair
+    const int pp0 = threadIdx.x % CP, xc0 = x0base + 2 * pp0;
+    const float dx0 = g.dea[xc0], dx1 = g.dea[xc0 + 1];
 #pragma unroll 8
     for (int idx = threadIdx.x; idx < N * CP; idx += blockDim.x) {
-        const int pp = idx % CP, iy = idx / CP;
-        const int xc = x0base + 2 * pp;
-        const float2 f = *reinterpret_cast<const float2 *>(xs + (size_t)iy * N + xc);
+        const int pp = pp0, iy = idx / CP;
+        const float2 f = *reinterpret_cast<const float2 *>(xs + (size_t)iy * N + xc0);
         const float dy = g.dea[iy];
-        const float2 z = make_float2(f.x * g.dea[xc] * dy, f.y * g.dea[xc + 1] * dy);
+        const float2 z = make_float2(f.x * dx0 * dy, f.y * dx1 * dy);
         const int q = (iy - N / 2) & (N - 1);
         sm[(pp * 2) * ts + spad(q)] = z;
         sm[(pp * 2 + 1) * ts + spad(q)] = cmul(z, g.twG[iy]);
@@ -340,16 +342,18 @@ __global__ void __launch_bounds__(512) k_adj_col(const float2 *__restrict__ U, f
     __syncthreads();
     fft_ct<+1, LOGN>(sm, 2 * CP, g.twN);
     float *xb = x + (size_t)b * N * N;
+    // blockDim.x is a multiple of CP, so a thread keeps its column pair
+    const int pp = threadIdx.x % CP, xc = x0base + 2 * pp;
+    const float dx0 = g.dea[xc], dx1 = g.dea[xc + 1];
 #pragma unroll 4
     for (int idx = threadIdx.x; idx < N * CP; idx += blockDim.x) {
-        const int pp = idx % CP, iy = idx / CP;
-        const int xc = x0base + 2 * pp;
+        const int iy = idx / CP;
         const int q = (iy - N / 2) & (N - 1);
         const float2 v = cadd(sm[(pp * 2) * ts + spad(q)],
                               cmul(sm[(pp * 2 + 1) * ts + spad(q)], cconj(g.twG[iy])));
         const float dy = g.dea[iy];
         *reinterpret_cast<float2 *>(xb + (size_t)iy * N + xc) =
-            make_float2(v.x * g.dea[xc] * dy, v.y * g.dea[xc + 1] * dy);
+            make_float2(v.x * dx0 * dy, v.y * dx1 * dy);
     }
 }
 
