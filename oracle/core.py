@@ -28,7 +28,7 @@ __all__ = [
     "build", "lib", "default_angles", "radon_fwd", "radon_adj",
     "radon_fwd_at", "radon_adj_at", "dirichlet", "neighbour_offsets",
     "prior_weights", "rho", "rho_prime", "prior_value_grad", "data_grad",
-    "objective_grad", "power_norm", "prior_lipschitz", "mbir_solve",
+    "objective_grad", "objective_value", "power_norm", "prior_lipschitz", "mbir_solve",
     "PAPER_PRIOR",
 ]
 
@@ -274,6 +274,16 @@ def objective_grad(f, b, wt, lam, prior, dims, theta=None):
     return G, 0.0, g
 
 
+def objective_value(f, b, wt, lam, prior, dims, theta=None):
+    """(G(f), lam H(f)) without the gradient (Sec. 3 Eq. objfn)."""
+    B, N, _ = f.shape
+    _, A, D = b.shape
+    r = radon_fwd(f, A, D, theta) - b
+    G = 0.5 * float(np.sum((wt * r if wt is not None else r) * r))
+    Hl = lam * prior_value_grad(f, dims, **prior)[0] if lam != 0.0 else 0.0
+    return G, Hl
+
+
 def power_norm(n, n_angles, n_det, wt, v0, n_iter, theta=None):
     """Largest eigenvalue of A^T W A by power iteration from the given start.
 
@@ -296,26 +306,42 @@ def power_norm(n, n_angles, n_det, wt, v0, n_iter, theta=None):
 
 def mbir_solve(b, wt, n, n_iter, step, lam=1.0, prior=None, dims=2,
                theta=None, x0=None, restart=True, return_log=False):
-    """Accelerated gradient with restart on Phi = G + lam H (Sec. 3).
+    """Accelerated gradient on Phi = G + lam H (Sec. 3), from x_0 = z_0 = x0
+    (zero by default) with t_0 = 1; all scalars FP64.
 
     Reading of "monotonic accelerated gradient method with restart":
-        x_{k+1} = z_k - step * grad Phi(z_k)
-        restart (t_k := 1) if <grad Phi(z_k), x_{k+1} - x_k> > 0
+        v       = z_k - step * grad Phi(z_k)
+        restart = True (gradient restart):
+            x_{k+1} = v; restart (t_k := 1) if <grad Phi(z_k), x_{k+1} - x_k> > 0
+        restart = "monotone" (function-value test):
+            x_{k+1} = v if Phi(v) <= Phi(x_k), else x_{k+1} = x_k and t_k := 1,
+            so Phi(x_k) never increases
+        restart = False: x_{k+1} = v, no restart (plain FISTA)
         t_{k+1} = (1 + sqrt(1 + 4 t_k^2)) / 2
         z_{k+1} = x_{k+1} + ((t_k - 1)/t_{k+1}) (x_{k+1} - x_k)
-    starting from x_0 = z_0 = x0 (zero by default), t_0 = 1.  All scalars FP64.
     """
     prior = PAPER_PRIOR if prior is None else prior
+    monotone = restart == "monotone"
     B = b.shape[0]
     x = np.zeros((B, n, n)) if x0 is None else np.asarray(x0, np.float64).copy()
     z = x.copy()
     t = 1.0
+    phi_x = sum(objective_value(x, b, wt, lam, prior, dims, theta)) if monotone else None
     log = []
     for k in range(n_iter):
         G, Hl, g = objective_grad(z, b, wt, lam, prior, dims, theta)
-        x_new = z - step * g
-        dot = float(np.sum(g * (x_new - x)))
-        restarted = bool(restart and dot > 0.0)
+        v = z - step * g
+        dot = float(np.sum(g * (v - x)))
+        if monotone:
+            Gv, Hv = objective_value(v, b, wt, lam, prior, dims, theta)
+            accepted = Gv + Hv <= phi_x
+            restarted = not accepted
+            x_new = v if accepted else x.copy()
+            if accepted:
+                phi_x = Gv + Hv
+        else:
+            restarted = bool(restart and dot > 0.0)
+            x_new = v
         if restarted:
             t = 1.0
         t_new = 0.5 * (1.0 + math.sqrt(1.0 + 4.0 * t * t))
@@ -323,5 +349,8 @@ def mbir_solve(b, wt, n, n_iter, step, lam=1.0, prior=None, dims=2,
         z = x_new + beta * (x_new - x)
         x = x_new
         t = t_new
-        log.append(dict(k=k, data=G, prior=Hl, dot=dot, restart=restarted, t=t))
+        entry = dict(k=k, data=G, prior=Hl, dot=dot, restart=restarted, t=t)
+        if monotone:
+            entry["phi_x"] = phi_x
+        log.append(entry)
     return (x, log) if return_log else x

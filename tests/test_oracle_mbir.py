@@ -100,3 +100,70 @@ def test_objective_decreases_with_prior():
     G0, H0, _ = oracle.objective_grad(np.zeros_like(x), b, None, lam, oracle.PAPER_PRIOR, 2, th)
     assert G + H < 0.2 * (G0 + H0)
     assert math.isfinite(G + H)
+
+
+def test_monotone_variant_converges_to_least_squares_monotonically():
+    """Function-value restart (restart="monotone"): Phi(x_k) never increases
+    and the iterates reach the dense least-squares solution, up to where the
+    decrease of a gradient step, (step/2) |grad Phi|^2, falls below the FP64
+    rounding of Phi itself (|x - x*| ~ sqrt(eps Phi* / lambda_min): here about
+    1e-7 relative); the gradient test has no such floor."""
+    N, A, D = 8, 24, 14
+    th, M = _tiny(N, A, D)
+    xt = RNG.standard_normal((N, N))
+    b = (M @ xt.ravel()).reshape(1, A, D) + 0.01 * RNG.standard_normal((1, A, D))
+    xls = np.linalg.lstsq(M, b.ravel(), rcond=None)[0]
+    L = np.linalg.norm(M, 2) ** 2
+    x, log = oracle.mbir_solve(b, None, N, 4000, 1.0 / L, lam=0.0, theta=th,
+                               restart="monotone", return_log=True)
+    assert np.linalg.norm(x.ravel() - xls) <= 1e-6 * np.linalg.norm(xls)
+    # before that floor it keeps pace with the gradient-restart schedule
+    x1k = oracle.mbir_solve(b, None, N, 1000, 1.0 / L, lam=0.0, theta=th, restart="monotone")
+    x1g = oracle.mbir_solve(b, None, N, 1000, 1.0 / L, lam=0.0, theta=th, restart=True)
+    e1k, e1g = (np.linalg.norm(v.ravel() - xls) for v in (x1k, x1g))
+    assert e1k <= 1.5 * e1g
+    phis = [e["phi_x"] for e in log]
+    assert all(b2 <= b1 for b1, b2 in zip(phis, phis[1:]))
+    assert any(e["restart"] for e in log)
+    # the recorded value is the objective at the returned iterate
+    r = M @ x.ravel() - b.ravel()
+    assert abs(phis[-1] - 0.5 * float(r @ r)) <= 1e-12 * max(1.0, phis[-1])
+
+
+def test_monotone_variant_rejects_a_step_that_raises_the_objective():
+    """A step far above 1/L along the leading singular direction overshoots:
+    the monotone variant keeps x_k (bitwise) and resets the momentum."""
+    N, A, D = 8, 24, 14
+    th, M = _tiny(N, A, D)
+    U, S, Vt = np.linalg.svd(M, full_matrices=False)
+    b = (S[0] * U[:, 0]).reshape(1, A, D)      # b = M v_1
+    L = S[0] ** 2
+    x, log = oracle.mbir_solve(b, None, N, 3, 10.0 / L, lam=0.0, theta=th,
+                               restart="monotone", return_log=True)
+    assert all(e["restart"] for e in log)
+    assert np.array_equal(x, np.zeros_like(x))
+    assert log[-1]["phi_x"] == 0.5 * float(np.sum(b * b))
+    # with a safe step the first iterate is the plain gradient step, as in the other modes
+    x1m = oracle.mbir_solve(b, None, N, 1, 1.0 / L, lam=0.0, theta=th, restart="monotone")
+    x1g = oracle.mbir_solve(b, None, N, 1, 1.0 / L, lam=0.0, theta=th, restart=True)
+    assert np.array_equal(x1m, x1g)
+
+
+def test_monotone_variant_with_prior_and_weights():
+    N, A, D = 16, 12, 24
+    th = oracle.default_angles(A)
+    xt = np.zeros((2, N, N))
+    xt[:, 4:12, 5:11] = 1.0
+    b = oracle.radon_fwd(xt, A, D, th) + 0.05 * RNG.standard_normal((2, A, D))
+    w = RNG.uniform(0.3, 1.0, b.shape)
+    lam = 2e-3
+    L = 1.05 * oracle.power_norm(N, A, D, w, RNG.standard_normal((2, N, N)), 30, th) \
+        + lam * oracle.prior_lipschitz()
+    x, log = oracle.mbir_solve(b, w, N, 25, 1.0 / L, lam=lam, theta=th, dims=3,
+                               restart="monotone", return_log=True)
+    phis = [e["phi_x"] for e in log]
+    assert all(b2 <= b1 for b1, b2 in zip(phis, phis[1:]))
+    G, Hl = oracle.objective_value(x, b, w, lam, oracle.PAPER_PRIOR, 3, th)
+    assert abs(phis[-1] - (G + Hl)) <= 1e-12 * phis[-1]
+    G0, H0 = oracle.objective_value(np.zeros_like(x), b, w, lam, oracle.PAPER_PRIOR, 3, th)
+    assert phis[-1] < 0.2 * (G0 + H0)
