@@ -51,7 +51,15 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-angles", type=int, default=16,
                     help="angles of one slice timed by the oracle for the CPU baseline")
-    return ap.parse_args()
+    ap.add_argument("--workload", default=None,
+                    choices=["volume_2048x1024", "tb25_shape", "tb86_shape"],
+                    help="set n, angles, det and slices from a named synthetic workload")
+    args = ap.parse_args()
+    if args.workload:
+        from paper_2304_12934_gb300 import synth
+        wl = synth.WORKLOADS[args.workload]
+        args.n, args.angles, args.det, args.slices = wl.n, wl.n_angles, wl.n_det, wl.slices
+    return args
 
 
 def dist_env():
@@ -378,9 +386,11 @@ def run_ours(args):
                 "dtype": "f32 (FP64 reductions)", "data": "synthetic",
                 "config": {"workload": f"volume {N}x{N}x{B}, {A} angles, {D} bins, Poisson I0=1e4, "
                                        f"26-nbr qGGMRF, 1 MBIR iteration per step",
+                           "name": args.workload or "custom" if (N, A, D, B) != (2048, 128, 2896, 1024)
+                           else "volume_2048x1024",
                            "n": N, "angles": A, "det": D, "slices_per_gpu": B,
                            "slices_per_launch": MB, "kernel_width": plan.kernel_width,
-                           "oversample": 2, "l2": "inputs 17 GB per volume array >> L2; no flush",
+                           "oversample": 2, "l2": f"inputs {4 * N * N * B / 1e9:.1f} GB per volume array >> L2 (129 MB); no flush",
                            "parallelism": f"replicas x{ws}"},
                 "roofline": roofline, "kernels": kernels, "batched_vs_plain": plain,
                 "e2e": e2e, "cpu_baseline": cpu, "gpu_launches": int(gpu_launches),

@@ -161,26 +161,32 @@ int mbir_grad(tc_plan *plan, const float *x, const float *b, const float *w,
 int mbir_power_norm(tc_plan *plan, const float *w, float *v, float *work,
                     int batch, int n_iter, double *lam_out, void *stream);
 
-/* Accelerated gradient with gradient restart (reading of Sec. 3's "monotonic
- * accelerated gradient method with restart"):
- *   x_{k+1} = z_k - step * grad Phi(z_k)
- *   if restart and <grad Phi(z_k), x_{k+1} - x_k> > 0 then t_k := 1
+/* Accelerated gradient with restart (reading of Sec. 3's "monotonic
+ * accelerated gradient method with restart"), v = z_k - step * grad Phi(z_k):
+ *   restart = 1 (gradient test):  x_{k+1} = v;
+ *       if <grad Phi(z_k), x_{k+1} - x_k> > 0 then t_k := 1
+ *   restart = 2 (monotone, function-value test): x_{k+1} = v if Phi(v) <=
+ *       Phi(x_k), else x_{k+1} = x_k and t_k := 1, so Phi(x_k) never
+ *       increases; costs one more forward projection and prior value per
+ *       iteration, and Phi(x) once per call
+ *   restart = 0: x_{k+1} = v (plain FISTA momentum)
  *   t_{k+1} = (1 + sqrt(1 + 4 t_k^2)) / 2
  *   z_{k+1} = x_{k+1} + ((t_k - 1) / t_{k+1}) (x_{k+1} - x_k)
- * All scalars (objective, inner products, t, momentum) are FP64 on the device;
- * no host round trip inside the loop. */
+ * All scalars (objective, inner products, t, momentum, the accept test) are
+ * FP64 on the device; no host round trip inside the loop. */
 typedef struct {
     int n_iter;      /* iterations to run in this call (>= 0) */
     double step;     /* constant step, 1/L with L >= ||A^T W A|| + lambda * 8/(sigma^2 c) */
-    int restart;     /* 1 = gradient restart, 0 = plain FISTA momentum */
+    int restart;     /* 0, 1 or 2 as above; anything else is TC_ERR_INVALID_ARG */
 } tc_solve_opts;
 
 /* Solver state; resuming with the same state continues the iteration exactly.
  *   z, g   caller-owned DEVICE buffers [batch][N][N] (momentum point, gradient)
  *   t      momentum scalar t_k (host copy, updated on return)
  *   k      iterations completed; k == 0 starts fresh (z := x, t := 1)
- *   n_restarts  restarts taken so far
- *   obj    objective terms (data, prior) at the last gradient point */
+ *   n_restarts  restarts taken so far (monotone variant: rejected steps)
+ *   obj    objective terms (data, lambda H) at the last gradient point z;
+ *          with restart = 2, at the returned x */
 typedef struct {
     float *z;
     float *g;

@@ -317,9 +317,22 @@ class SolveState:
         self.obj = (s.obj[0], s.obj[1])
 
 
+def _restart_code(restart) -> int:
+    """True -> 1 (gradient restart), False -> 0 (none), "monotone" -> 2."""
+    if restart == "monotone":
+        return 2
+    if restart is True or restart is False:
+        return 1 if restart else 0
+    raise ValueError(f"restart must be True, False or 'monotone', not {restart!r}")
+
+
 def mbir_solve(plan: Plan, b, w, x, n_iter, step, prior: Prior | None = None, restart=True,
                state: SolveState | None = None, stream=None) -> SolveState:
-    """Run n_iter accelerated-gradient iterations with restart on device buffers (x in/out)."""
+    """Run n_iter accelerated-gradient iterations on device buffers (x in/out).
+
+    restart: True (gradient test), "monotone" (function-value test: Phi(x_k)
+    never increases; state.obj is then the objective at the returned x) or
+    False (plain momentum)."""
     B = x.shape[0]
     _need(x, plan.image_shape(B), "x", plan.device)
     _need(b, plan.sino_shape(B), "b", plan.device)
@@ -328,7 +341,7 @@ def mbir_solve(plan: Plan, b, w, x, n_iter, step, prior: Prior | None = None, re
     st = state if state is not None else SolveState(x)
     cs = st._c()
     pr = prior._c() if prior is not None else None
-    opts = _SolveOpts(int(n_iter), float(step), 1 if restart else 0)
+    opts = _SolveOpts(int(n_iter), float(step), _restart_code(restart))
     _check("mbir_solve", load().mbir_solve(plan.handle, _ptr(b), _ptr(w), _ptr(x), B,
                                            ctypes.byref(pr) if pr is not None else None,
                                            ctypes.byref(opts), ctypes.byref(cs),
@@ -356,7 +369,7 @@ def mbir_solve_host(plan: Plan, b_host, w_host, x_host, n_iter, step, prior: Pri
     st = state if state is not None else SolveState(dx)
     cs = st._c()
     pr = prior._c() if prior is not None else None
-    opts = _SolveOpts(int(n_iter), float(step), 1 if restart else 0)
+    opts = _SolveOpts(int(n_iter), float(step), _restart_code(restart))
     _check("mbir_solve_host", load().mbir_solve_host(
         plan.handle, _ptr(b_host), _ptr(w_host), _ptr(x_host), _ptr(db), _ptr(dw), _ptr(dx), B,
         ctypes.byref(pr) if pr is not None else None, ctypes.byref(opts), ctypes.byref(cs),

@@ -76,6 +76,25 @@ int grad_impl(tc_plan *p, const float *x, const float *b, const float *w,
     return TC_OK;
 }
 
+// *data = 1/2 sum W (A x - b)^2 (FP64), *prior_val = lambda H(x) (when a
+// prior with lambda != 0 is given): the objective's value without its gradient.
+int value_impl(tc_plan *p, const float *x, const float *b, const float *w, const tc_prior *prior,
+               int batch, double *data, double *prior_val, cudaStream_t s,
+               const cudaEvent_t *ready = nullptr) {
+    TC_CUDA(cudaMemsetAsync(data, 0, sizeof(double), s));
+    TC_CUDA(cudaMemsetAsync(prior_val, 0, sizeof(double), s));
+    const size_t ni = img_elems(p), ns = sino_elems(p);
+    for (int c0 = 0; c0 < batch; c0 += p->chunk) {
+        const int nb = batch - c0 < p->chunk ? batch - c0 : p->chunk;
+        if (ready) TC_CUDA(cudaStreamWaitEvent(s, ready[c0 / p->chunk], 0));
+        int rc = launch_radon_fwd_chunk(p, x + c0 * ni, nullptr, nb, b ? b + c0 * ns : nullptr,
+                                        w ? w + c0 * ns : nullptr, p->sr, data, s);
+        if (rc) return rc;
+    }
+    if (prior && prior->lambda != 0.0) return launch_prior_value(p, x, batch, prior, prior_val, s);
+    return TC_OK;
+}
+
 int check_prior(const tc_prior *pr) {
     if (!pr) return TC_OK;
     if (!(pr->dims == 2 || pr->dims == 3) || !(pr->sigma > 0) || !(pr->c > 0) ||
@@ -226,7 +245,25 @@ int solve_loop(tc_plan *p, const float *b, const float *w, float *x, int batch,
                                             opts->step, s)))
             return rc;
     }
-    for (int it = 0; it < opts->n_iter; ++it) {
+    if (opts->restart == 2) {
+        // Monotone variant.  Phi(x_k) is recomputed at the start of every call
+        // (deterministically), so a resumed solve matches an uninterrupted one.
+        if (opts->n_iter > 0) {
+            if ((rc = value_impl(p, x, b, w, prior, batch, p->scal + SC_DATA_X, p->scal + SC_PRIOR_X, s,
+                                 ready)))
+                return rc;
+        }
+        for (int it = 0; it < opts->n_iter; ++it) {
+            if ((rc = grad_impl(p, st->z, b, w, prior, st->g, batch, s, false)))  // g = grad Phi(z_k)
+                return rc;
+            if ((rc = launch_step_to_candidate(p, st->z, st->g, n, s))) return rc;  // g := v
+            if ((rc = value_impl(p, st->g, b, w, prior, batch, p->scal + SC_DATA_V, p->scal + SC_PRIOR_V, s)))
+                return rc;
+            if ((rc = launch_monotone_scalar(p, 0, s))) return rc;
+            if ((rc = launch_update_monotone(p, x, st->z, st->g, n, s))) return rc;
+        }
+    }
+    for (int it = 0; it < (opts->restart == 2 ? 0 : opts->n_iter); ++it) {
         // the prior's value H is only reported for the last gradient point
         const bool fused = prior && prior->lambda != 0.0;  // dots inside the prior kernel
         if ((rc = grad_impl(p, st->z, b, w, prior, st->g, batch, s, it == opts->n_iter - 1,
@@ -242,7 +279,10 @@ int solve_loop(tc_plan *p, const float *b, const float *w, float *x, int batch,
     st->t = sc[SC_T];
     st->k = (int)sc[SC_K];
     st->n_restarts = (int)sc[SC_RESTARTS];
-    if (opts->n_iter > 0) {
+    if (opts->n_iter > 0 && opts->restart == 2) {  // the objective at the returned x
+        st->obj[0] = sc[SC_DATA_X];
+        st->obj[1] = sc[SC_PRIOR_X];
+    } else if (opts->n_iter > 0) {
         st->obj[0] = sc[SC_DATA];
         st->obj[1] = (prior && prior->lambda != 0.0) ? sc[SC_PRIOR] : 0.0;
     }
@@ -252,7 +292,7 @@ int solve_loop(tc_plan *p, const float *b, const float *w, float *x, int batch,
 int check_solve(tc_plan *p, int batch, const tc_prior *prior, const tc_solve_opts *opts,
                 const tc_solve_state *st) {
     if (!p || !opts || !st || batch < 1 || opts->n_iter < 0 || !(opts->step > 0) ||
-        check_prior(prior))
+        opts->restart < 0 || opts->restart > 2 || check_prior(prior))
         return TC_ERR_INVALID_ARG;
     if (check_ptrs({st->z, st->g}, {})) return TC_ERR_INVALID_ARG;
     return TC_OK;

@@ -162,6 +162,12 @@ enum {
     SC_K,            // iteration count (as double)
     SC_STEP,         // step
     SC_NORM,         // scratch norm / Rayleigh quotient
+    // monotone variant (function-value test)
+    SC_DATA_V,       // data term at the candidate v = z - step g
+    SC_PRIOR_V,      // lambda H(v)
+    SC_DATA_X,       // data term at the accepted iterate x_k
+    SC_PRIOR_X,      // lambda H(x_k)
+    SC_ACCEPT,       // 1: this iteration's candidate was accepted
     SC_COUNT = 16
 };
 
@@ -176,6 +182,16 @@ int launch_radon_adj_chunk(tc_plan *p, const float *y, float *x, int nb,
 int launch_prior_grad(tc_plan *p, const float *x, float *g, int nb,
                       const tc_prior *pr, double *h_acc, cudaStream_t s,
                       const float *dot_x = nullptr);
+// h_acc = lambda H(x) only (no gradient).
+int launch_prior_value(tc_plan *p, const float *x, int nb, const tc_prior *pr,
+                       double *h_acc, cudaStream_t s);
+// Monotone variant: v = z - step g in place of g; the accept/restart decision
+// and momentum (init = 1: only set Phi(x_k) from its parts); the update
+// x_{k+1} = accepted ? v : x_k, z_{k+1} = x_{k+1} + beta (x_{k+1} - x_k).
+int launch_step_to_candidate(tc_plan *p, const float *z, float *g, size_t n, cudaStream_t s);
+int launch_monotone_scalar(tc_plan *p, int init, cudaStream_t s);
+int launch_update_monotone(tc_plan *p, float *x, float *z, const float *v, size_t n,
+                           cudaStream_t s);
 int launch_reduce_finalize(const double *partials, int n, double *acc,
                            int accumulate, double scale, cudaStream_t s);
 int launch_dots_gzx_gg(tc_plan *p, const float *g, const float *z, const float *x,

@@ -52,6 +52,11 @@ __device__ __forceinline__ float qggmrf_e(float d, const PriorArgs &a, float &in
     return d * fmaf(a.p, q, a.two_c) * (inv * inv);
 }
 
+// inv alone, for the value sigma^2 rho(d) = d^2 inv
+__device__ __forceinline__ float qggmrf_inv(float d, const PriorArgs &a) {
+    return rcp_approx(a.c + ex2_approx(fmaf(a.qexp, lg2_approx(fabsf(d)), a.lk)));
+}
+
 // qGGMRF prior on a volume [B][N][N] (slices consecutive along z).
 // A CTA owns a PTX x PTY column of voxels and marches along z holding a ring
 // (tile + 1-voxel halo) of two f planes in shared memory.  Each unordered
@@ -86,7 +91,8 @@ __device__ __forceinline__ float qggmrf_e(float d, const PriorArgs &a, float &in
 // z+1 pairs of one ring cell: fc / fn point at the cell in planes z and z+1,
 // eu at its slot of the current z+1 buffer.
 // gs accumulates the cell's own (forward) share of the gradient sum, w e.
-template <bool MASKED, bool WANT_H>
+// GRAD = false: the value alone (no pair derivatives, nothing stored).
+template <bool MASKED, bool WANT_H, bool GRAD>
 __device__ __forceinline__ void prior_up_pairs(const float *fn, float fm, float *eu, unsigned mu,
                                                const PriorArgs &a, float &gs, float &hs) {
 #pragma unroll
@@ -95,13 +101,17 @@ __device__ __forceinline__ void prior_up_pairs(const float *fn, float fm, float 
         const float wu = (dx == 0 && dy == 0) ? a.w1 : ((dx == 0 || dy == 0) ? a.w2 : a.w3);
         float e = 0.f;
         if (!MASKED || (mu & (1u << u))) {
-            float inv;
             const float d = fm - fn[dy * PRX + dx];
-            e = qggmrf_e(d, a, inv);
-            gs = fmaf(wu, e, gs);
-            if (WANT_H) hs = fmaf(wu, d * d * inv, hs);
+            if (GRAD) {
+                float inv;
+                e = qggmrf_e(d, a, inv);
+                gs = fmaf(wu, e, gs);
+                if (WANT_H) hs = fmaf(wu, d * d * inv, hs);
+            } else {
+                hs = fmaf(wu, d * d * qggmrf_inv(d, a), hs);
+            }
         }
-        eu[u * PRS] = e;
+        if (GRAD) eu[u * PRS] = e;
     }
 }
 
@@ -109,7 +119,7 @@ __device__ __forceinline__ void prior_up_pairs(const float *fn, float fm, float 
 __device__ __forceinline__ int pl_dx(int q) { return q == 0 ? 1 : (q == 1 ? -1 : (q == 2 ? 0 : 1)); }
 __device__ __forceinline__ int pl_dy(int q) { return q == 0 ? 0 : 1; }
 
-template <bool MASKED, bool WANT_H>
+template <bool MASKED, bool WANT_H, bool GRAD>
 __device__ __forceinline__ void prior_plane_pairs(const float *fc, float fm, float *ep, unsigned mp,
                                                   const PriorArgs &a, float &gs, float &hs) {
 #pragma unroll
@@ -117,17 +127,21 @@ __device__ __forceinline__ void prior_plane_pairs(const float *fc, float fm, flo
         const float wq = (q & 1) ? a.w2 : a.w1;
         float e = 0.f;
         if (!MASKED || (mp & (1u << q))) {
-            float inv;
             const float d = fm - fc[pl_dy(q) * PRX + pl_dx(q)];
-            e = qggmrf_e(d, a, inv);
-            gs = fmaf(wq, e, gs);
-            if (WANT_H) hs = fmaf(wq, d * d * inv, hs);
+            if (GRAD) {
+                float inv;
+                e = qggmrf_e(d, a, inv);
+                gs = fmaf(wq, e, gs);
+                if (WANT_H) hs = fmaf(wq, d * d * inv, hs);
+            } else {
+                hs = fmaf(wq, d * d * qggmrf_inv(d, a), hs);
+            }
         }
-        ep[q * PRS] = e;
+        if (GRAD) ep[q * PRS] = e;
     }
 }
 
-template <bool WANT_H, bool DOTS>
+template <bool WANT_H, bool DOTS, bool GRAD = true>
 __global__ void __launch_bounds__(PRIOR_THREADS, PRIOR_MIN_BLOCKS) k_prior(const float *__restrict__ f, float *__restrict__ g,
                                                           double *__restrict__ partials, const PriorArgs a,
                                                           const float *__restrict__ xprev,
@@ -191,7 +205,7 @@ __global__ void __launch_bounds__(PRIOR_THREADS, PRIOR_MIN_BLOCKS) k_prior(const
         const int pz = three ? z + 2 : z + 1;
         const float f_pf = (inb && pz < B) ? f[(size_t)pz * NN + off] : 0.f;
         const size_t i = (size_t)z * NN + off;
-        const float g_old = interior ? g[i] : 0.f;
+        const float g_old = (GRAD && interior) ? g[i] : 0.f;
         const float x_old = (DOTS && interior) ? xprev[i] : 0.f;
         if (ring) {
             if (up) fpl[nxt * PRS + h] = f_nx;                 // 3D: plane z + 1
@@ -204,18 +218,20 @@ __global__ void __launch_bounds__(PRIOR_THREADS, PRIOR_MIN_BLOCKS) k_prior(const
             fm = *fc;
             float *eu = Eu + (s3 * 9) * PRS + h;
             if (up) {
-                if (full) prior_up_pairs<false, WANT_H>(fpl + nxt * PRS + h, fm, eu, 0u, a, gs, hs);
-                else prior_up_pairs<true, WANT_H>(fpl + nxt * PRS + h, fm, eu, mup, a, gs, hs);
-            } else if (three) {
+                if (full) prior_up_pairs<false, WANT_H, GRAD>(fpl + nxt * PRS + h, fm, eu, 0u, a, gs, hs);
+                else prior_up_pairs<true, WANT_H, GRAD>(fpl + nxt * PRS + h, fm, eu, mup, a, gs, hs);
+            } else if (GRAD && three) {
 #pragma unroll
                 for (int u = 0; u < 9; ++u) eu[u * PRS] = 0.f;
             }
             float *ep = Ep + ((z % PRIOR_PL_SLOTS) * 4) * PRS + h;
-            if (full) prior_plane_pairs<false, WANT_H>(fc, fm, ep, 0u, a, gs, hs);
-            else prior_plane_pairs<true, WANT_H>(fc, fm, ep, mpl, a, gs, hs);
+            if (full) prior_plane_pairs<false, WANT_H, GRAD>(fc, fm, ep, 0u, a, gs, hs);
+            else prior_plane_pairs<true, WANT_H, GRAD>(fc, fm, ep, mpl, a, gs, hs);
         }
         __syncthreads();
-        if (interior) {
+        if (!GRAD) {
+            if (interior) h8 += hs;
+        } else if (interior) {
             // minus the shares of the pairs this voxel closes (evaluated at
             // their lower voxels: in-plane this step, towards z+1 the last)
             if (three) {
@@ -362,6 +378,65 @@ __global__ void k_update(float4 *__restrict__ x, float4 *__restrict__ z,
     }
 }
 
+// Monotone variant (function-value test), all decisions in FP64 on the device.
+// g := z - step g (the candidate v overwrites the gradient, which this
+// variant no longer needs).
+__global__ void k_step_to_candidate(const float4 *__restrict__ z, float4 *__restrict__ g, size_t n4,
+                                    const double *__restrict__ sc) {
+    const float step = (float)sc[SC_STEP];
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const float4 zv = z[i], gv = g[i];
+        g[i] = make_float4(fmaf(-step, gv.x, zv.x), fmaf(-step, gv.y, zv.y), fmaf(-step, gv.z, zv.z),
+                           fmaf(-step, gv.w, zv.w));
+    }
+}
+
+// init: nothing to decide (Phi(x_k) is held as SC_DATA_X + SC_PRIOR_X).
+// Otherwise accept v if Phi(v) <= Phi(x_k); on rejection keep x_k and
+// restart the momentum (t := 1, beta = 0).
+__global__ void k_monotone_scalar(double *sc, int init) {
+    if (threadIdx.x != 0 || blockIdx.x != 0 || init) return;
+    const double phi_v = sc[SC_DATA_V] + sc[SC_PRIOR_V];
+    const double phi_x = sc[SC_DATA_X] + sc[SC_PRIOR_X];
+    const bool accept = phi_v <= phi_x;
+    double t = sc[SC_T];
+    if (accept) {
+        sc[SC_DATA_X] = sc[SC_DATA_V];
+        sc[SC_PRIOR_X] = sc[SC_PRIOR_V];
+    } else {
+        t = 1.0;
+        sc[SC_RESTARTS] += 1.0;
+    }
+    const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
+    sc[SC_BETA] = accept ? (t - 1.0) / tn : 0.0;
+    sc[SC_T] = tn;
+    sc[SC_K] += 1.0;
+    sc[SC_ACCEPT] = accept ? 1.0 : 0.0;
+}
+
+__global__ void k_update_monotone(float4 *__restrict__ x, float4 *__restrict__ z,
+                                  const float4 *__restrict__ v, size_t n4, const double *__restrict__ sc) {
+    const bool accept = sc[SC_ACCEPT] != 0.0;
+    const float beta = (float)sc[SC_BETA];
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const float4 xv = x[i];
+        if (!accept) {  // x_{k+1} = x_k, z_{k+1} = x_k
+            z[i] = xv;
+            continue;
+        }
+        const float4 xn = v[i];
+        float4 zn;
+        zn.x = fmaf(beta, xn.x - xv.x, xn.x);
+        zn.y = fmaf(beta, xn.y - xv.y, xn.y);
+        zn.z = fmaf(beta, xn.z - xv.z, xn.z);
+        zn.w = fmaf(beta, xn.w - xv.w, xn.w);
+        x[i] = xn;
+        z[i] = zn;
+    }
+}
+
 __global__ void k_scale_inv_sqrt(float4 *__restrict__ v, size_t n4, const double *__restrict__ sq) {
     const float s = (float)(1.0 / sqrt(*sq));
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4;
@@ -441,6 +516,46 @@ int launch_prior_grad(tc_plan *p, const float *x, float *g, int nb,
         if (rc) return rc;
     }
     if (h_acc) return launch_reduce_finalize(part, blocks, h_acc, 0, prior_value_scale(pr), s);
+    return TC_OK;
+}
+
+int launch_prior_value(tc_plan *p, const float *x, int nb, const tc_prior *pr,
+                       double *h_acc, cudaStream_t s) {
+    const PriorArgs a = make_prior_args(p->k.N, nb, pr);
+    dim3 grid((a.N + PTX - 1) / PTX, (a.N + PTY - 1) / PTY);
+    const int blocks = grid.x * grid.y;
+    if (blocks > p->slot) return TC_ERR_UNSUPPORTED;
+    double *part = p->partials + (size_t)1 * p->slot;
+    const size_t smem = PRIOR_SMEM_FLOATS * sizeof(float);
+    TC_PROFILED(TCK_PRIOR, s, (k_prior<true, false, false><<<grid, PRIOR_THREADS, smem, s>>>(
+                                  x, nullptr, part, a, nullptr, nullptr, nullptr)));
+    TC_LAUNCHED("k_prior");
+    return launch_reduce_finalize(part, blocks, h_acc, 0, prior_value_scale(pr), s);
+}
+
+int launch_step_to_candidate(tc_plan *p, const float *z, float *g, size_t n, cudaStream_t s) {
+    const size_t n4 = n / 4;
+    TC_PROFILED(TCK_UPDATE, s,
+                k_step_to_candidate<<<grid_for(n4), TC_RED_THREADS, 0, s>>>(
+        reinterpret_cast<const float4 *>(z), reinterpret_cast<float4 *>(g), n4, p->scal));
+    TC_LAUNCHED("k_step_to_candidate");
+    return TC_OK;
+}
+
+int launch_monotone_scalar(tc_plan *p, int init, cudaStream_t s) {
+    TC_PROFILED(TCK_SCALAR, s, k_monotone_scalar<<<1, 32, 0, s>>>(p->scal, init));
+    TC_LAUNCHED("k_monotone_scalar");
+    return TC_OK;
+}
+
+int launch_update_monotone(tc_plan *p, float *x, float *z, const float *v, size_t n,
+                           cudaStream_t s) {
+    const size_t n4 = n / 4;
+    TC_PROFILED(TCK_UPDATE, s,
+                k_update_monotone<<<grid_for(n4), TC_RED_THREADS, 0, s>>>(
+        reinterpret_cast<float4 *>(x), reinterpret_cast<float4 *>(z),
+        reinterpret_cast<const float4 *>(v), n4, p->scal));
+    TC_LAUNCHED("k_update_monotone");
     return TC_OK;
 }
 
@@ -553,7 +668,8 @@ int prior_configure_kernels() {
     const int smem = (int)(PRIOR_SMEM_FLOATS * sizeof(float));
     int rc;
     if ((rc = raise_prior_smem(k_prior<true, false>, smem)) || (rc = raise_prior_smem(k_prior<false, false>, smem)) ||
-        (rc = raise_prior_smem(k_prior<true, true>, smem)) || (rc = raise_prior_smem(k_prior<false, true>, smem)))
+        (rc = raise_prior_smem(k_prior<true, true>, smem)) || (rc = raise_prior_smem(k_prior<false, true>, smem)) ||
+        (rc = raise_prior_smem(k_prior<true, false, false>, smem)))
         return rc;
     return TC_OK;
 }

@@ -176,6 +176,11 @@ WORKLOADS = {
     "noisy_512x16": Workload("noisy_512x16", 512, 180, 724, 16, 50, 1e4, 2),
     "diff_1024x64": Workload("diff_1024x64", 1024, 360, 1448, 64, 0, None, 3),
     "volume_2048x1024": Workload("volume_2048x1024", 2048, 128, 2896, 1024, 100, 1e4, 3),
+    # shapes of the paper's two real-data experiments (Sec. 5), as synthetic
+    # stand-ins: 400 projections x 2048 bins and 202 projections x 2448 bins,
+    # 128 slices each, reconstructed on a 2048^2 grid
+    "tb25_shape": Workload("tb25_shape", 2048, 400, 2048, 128, 100, 1e4, 3),
+    "tb86_shape": Workload("tb86_shape", 2048, 202, 2448, 128, 100, 1e4, 3),
 }
 
 

@@ -67,3 +67,11 @@ def test_product_path_does_not_import_oracle():
             src = open(f).read()
             assert "import oracle" not in src and "from oracle" not in src, f
             assert "radon_oracle" not in src, f
+
+
+def test_restart_modes_map_to_the_abi_codes():
+    from paper_2304_12934_gb300 import api
+    assert api._restart_code(True) == 1 and api._restart_code(False) == 0
+    assert api._restart_code("monotone") == 2
+    with pytest.raises(ValueError):
+        api._restart_code("sometimes")

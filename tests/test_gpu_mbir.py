@@ -207,3 +207,69 @@ def _tall_prior_case(api, dims):
     pd = dict(p=prior.p, sigma=prior.sigma, c=prior.c)
     Hv, gh = oracle.prior_value_grad(f, dims, **pd)
     return np64(g), float(obj.cpu().numpy()[1]), prior.lam * gh, prior.lam * Hv
+
+
+# ------------------------------------------------- monotone variant (NEXT) ----
+def _noisy_weighted(B=2):
+    ells = [synth.random_ellipses(N, synth.BASE_SEED + 40 + k, scale=1.0 / N) for k in range(B)]
+    th = oracle.default_angles(A)
+    p = np.stack([synth.ellipse_line_integrals(e, th, D) for e in ells])
+    b, w = synth.poisson_measurement(p, 1e4, 15)
+    return b.astype(np.float32).astype(np.float64), w.astype(np.float32).astype(np.float64)
+
+
+def test_monotone_solver_matches_oracle(api):
+    """Function-value test (Sec. 3 reading): 20 iterations on weighted noisy
+    data with the 26-neighbour prior against the oracle's monotone schedule;
+    the reported objective is the one at the returned x."""
+    b, w = _noisy_weighted(2)
+    lam = 1e-2
+    v0 = synth.random_start((2, N, N), 3)
+    step = 1.0 / (1.05 * oracle.power_norm(N, A, D, w, v0, 30) + 8.0 * lam / ((1 / 0.7) ** 2 * 1e-4))
+    prior = api.Prior(lam=lam, dims=3)
+    pd = dict(p=prior.p, sigma=prior.sigma, c=prior.c)
+    xo, log = oracle.mbir_solve(b, w, N, 20, step, lam=lam, prior=pd, dims=3,
+                                restart="monotone", return_log=True)
+    with api.Plan(N, A, D, max_batch=2) as plan:
+        x = torch.zeros((2, N, N), device="cuda:0")
+        st = api.mbir_solve(plan, t32(b), t32(w), x, 20, step, prior, restart="monotone")
+    assert st.k == 20
+    assert rel(np64(x), xo) <= 1e-3
+    G, Hl = oracle.objective_value(np64(x), b, w, lam, pd, 3)
+    assert abs(st.obj[0] - G) <= 1e-5 * G and abs(st.obj[1] - Hl) <= 1e-5 * Hl
+    assert abs(sum(st.obj) - log[-1]["phi_x"]) <= 1e-4 * log[-1]["phi_x"]
+
+
+def test_monotone_objective_never_increases_and_resumes_bitwise(api):
+    b, w = _noisy_weighted(2)
+    lam = 1e-2
+    v0 = synth.random_start((2, N, N), 4)
+    step = 1.0 / (1.05 * oracle.power_norm(N, A, D, w, v0, 30) + 8.0 * lam / ((1 / 0.7) ** 2 * 1e-4))
+    prior = api.Prior(lam=lam, dims=3)
+    with api.Plan(N, A, D, max_batch=2) as plan:
+        bt, wt = t32(b), t32(w)
+        x1 = torch.zeros((2, N, N), device="cuda:0")
+        api.mbir_solve(plan, bt, wt, x1, 12, step, prior, restart="monotone")
+        x2 = torch.zeros((2, N, N), device="cuda:0")
+        st = api.SolveState(x2)
+        phis = []
+        for _ in range(12):   # one iteration per call: Phi(x_k) is recomputed each time
+            api.mbir_solve(plan, bt, wt, x2, 1, step, prior, restart="monotone", state=st)
+            phis.append(sum(st.obj))
+    assert st.k == 12
+    assert all(p2 <= p1 for p1, p2 in zip(phis, phis[1:]))
+    assert torch.equal(x1, x2)
+
+
+def test_monotone_rejects_an_overshooting_step(api):
+    """A step 1000 times 1/L raises the objective: x stays at its start
+    (bitwise), every step is rejected and counted as a restart."""
+    f, b = _data(1)
+    L = 1.0 / _step(0.0)
+    with api.Plan(N, A, D) as plan:
+        x = torch.zeros((1, N, N), device="cuda:0")
+        st = api.mbir_solve(plan, t32(b), None, x, 3, 1000.0 / L, None, restart="monotone")
+    assert st.n_restarts == 3
+    assert torch.count_nonzero(x) == 0
+    assert abs(st.obj[0] - 0.5 * float(np.sum(b * b))) <= 1e-5 * 0.5 * float(np.sum(b * b))
+    assert st.obj[1] == 0.0

@@ -149,7 +149,9 @@ def test_theta_zero_gives_column_sums(api):
     assert np.abs(y[off:off + N] - col).max() <= 2e-5 * np.abs(col).max()
 
 
-@pytest.mark.parametrize("N,A,D", [(2048, 128, 2896), (512, 180, 724)])
+@pytest.mark.parametrize("N,A,D", [(2048, 128, 2896), (512, 180, 724),
+                                   (2048, 400, 2048),   # 400 projections x 2048 bins (D = 2^11)
+                                   (2048, 202, 2448)])  # 202 projections x 2448 bins (D = 16 * 9 * 17)
 def test_full_size_sampled_entries(api, N, A, D):
     """Full-size operators in the batched launch configuration, checked on
     sampled outputs that the oracle computes one by one (closed form)."""
