@@ -372,3 +372,30 @@ __device__ void bluestein(float2 *s, int D, int L, int log2L, const float2 *__re
     }
     __syncthreads();
 }
+
+// The same with L = 2^LOGL fixed at compile time (fft_ct offsets).
+template <int SIGN, int LOGL>
+__device__ void bluestein_ct(float2 *s, int D, const float2 *__restrict__ chirp,
+                             const float2 *__restrict__ bhat, const float2 *__restrict__ twL) {
+    constexpr int L = 1 << LOGL;
+    for (int n = threadIdx.x; n < L; n += blockDim.x) {
+        float2 a = make_float2(0.f, 0.f);
+        if (n < D) {
+            float2 v = s[spad(n)];
+            if (SIGN > 0) v.y = -v.y;
+            a = cmul(v, chirp[n]);
+        }
+        s[spad(n)] = a;
+    }
+    __syncthreads();
+    fft_ct<-1, LOGL>(s, 1, twL);
+    for (int n = threadIdx.x; n < L; n += blockDim.x) s[spad(n)] = cmul(s[spad(n)], bhat[n]);
+    __syncthreads();
+    fft_ct<+1, LOGL>(s, 1, twL);
+    for (int k = threadIdx.x; k < D; k += blockDim.x) {
+        float2 v = cmul(s[spad(k)], chirp[k]);
+        if (SIGN > 0) v.y = -v.y;
+        s[spad(k)] = v;
+    }
+    __syncthreads();
+}

@@ -15,6 +15,7 @@ namespace {
 struct PriorArgs {
     int N, B, dims;
     float p, c, qexp;  // qexp = 2 - p
+    float cq;          // c (2 - p)
     float lk;          // qexp * log2(1 / sigma)
     float two_c;       // 2 c
     float gscale;      // 2 lambda / sigma^2: scale of the gradient sum
@@ -40,16 +41,17 @@ __device__ __forceinline__ float rcp_approx(float x) {
 }
 
 // rho(d) = u^2 / (c + |u|^(2-p)), u = d / sigma (Eq. reg3), differentiated by
-// hand:  rho'(d) = (d / sigma^2) (p |u|^(2-p) + 2c) / (c + |u|^(2-p))^2.
-// Returns sigma^2 rho'(d) (the constant is applied once per voxel) and
-// inv = 1 / (c + |u|^(2-p)), from which sigma^2 rho(d) = d^2 inv.
+// hand:  rho'(d) = (d / sigma^2) (p |u|^(2-p) + 2c) / (c + |u|^(2-p))^2
+//                = (d / sigma^2) inv (p + c (2 - p) inv),  inv = 1 / (c + |u|^(2-p)).
+// Returns sigma^2 rho'(d) (the constant is applied once per voxel) and inv,
+// from which sigma^2 rho(d) = d^2 inv.
 // |u|^(2-p) = 2^((2-p) log2|d| + (2-p) log2(1/sigma)); at d = 0, log2 gives
 // -inf and the power 0.
 __device__ __forceinline__ float qggmrf_e(float d, const PriorArgs &a, float &inv_out) {
     const float q = ex2_approx(fmaf(a.qexp, lg2_approx(fabsf(d)), a.lk));
     const float inv = rcp_approx(a.c + q);
     inv_out = inv;
-    return d * fmaf(a.p, q, a.two_c) * (inv * inv);
+    return (d * inv) * fmaf(a.cq, inv, a.p);
 }
 
 // inv alone, for the value sigma^2 rho(d) = d^2 inv
@@ -87,16 +89,22 @@ __device__ __forceinline__ float qggmrf_inv(float d, const PriorArgs &a) {
 #define PRIOR_PL_SLOTS 1    // buffers of in-plane pair values
 #define PRIOR_MIN_BLOCKS 4  // 46 KB of shared memory and <= 32 registers: 60 warps per SM
 #define PRIOR_SMEM_FLOATS (PRIOR_FPAD + 2 * PRS + PRIOR_UP_SLOTS * 9 * PRS + PRIOR_PL_SLOTS * 4 * PRS)
+// the first warp covers only the bottom halo row, the last only the top one
+static_assert(PRX >= 32 && (PRIOR_THREADS / 32 - 1) * 32 >= (PRY - 1) * PRX && PRIOR_THREADS >= PRS,
+              "halo-row warps");
 
 // z+1 pairs of one ring cell: fc / fn point at the cell in planes z and z+1,
 // eu at its slot of the current z+1 buffer.
 // gs accumulates the cell's own (forward) share of the gradient sum, w e.
 // GRAD = false: the value alone (no pair derivatives, nothing stored).
-template <bool MASKED, bool WANT_H, bool GRAD>
+// DIRS: directions evaluated at all (compile time; the others are skipped and
+// their slots left untouched, for rows of the halo that never need them).
+template <bool MASKED, bool WANT_H, bool GRAD, unsigned DIRS = 0x1ffu>
 __device__ __forceinline__ void prior_up_pairs(const float *fn, float fm, float *eu, unsigned mu,
                                                const PriorArgs &a, float &gs, float &hs) {
 #pragma unroll
     for (int u = 0; u < 9; ++u) {
+        if (!(DIRS & (1u << u))) continue;
         const int dx = u % 3 - 1, dy = u / 3 - 1;
         const float wu = (dx == 0 && dy == 0) ? a.w1 : ((dx == 0 || dy == 0) ? a.w2 : a.w3);
         float e = 0.f;
@@ -119,11 +127,12 @@ __device__ __forceinline__ void prior_up_pairs(const float *fn, float fm, float 
 __device__ __forceinline__ int pl_dx(int q) { return q == 0 ? 1 : (q == 1 ? -1 : (q == 2 ? 0 : 1)); }
 __device__ __forceinline__ int pl_dy(int q) { return q == 0 ? 0 : 1; }
 
-template <bool MASKED, bool WANT_H, bool GRAD>
+template <bool MASKED, bool WANT_H, bool GRAD, unsigned DIRS = 0xfu>
 __device__ __forceinline__ void prior_plane_pairs(const float *fc, float fm, float *ep, unsigned mp,
                                                   const PriorArgs &a, float &gs, float &hs) {
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
+        if (!(DIRS & (1u << q))) continue;
         const float wq = (q & 1) ? a.w2 : a.w1;
         float e = 0.f;
         if (!MASKED || (mp & (1u << q))) {
@@ -153,7 +162,7 @@ __global__ void __launch_bounds__(PRIOR_THREADS, PRIOR_MIN_BLOCKS) k_prior(const
     __shared__ double red[32];
     const int N = a.N, B = a.B;
     const size_t NN = (size_t)N * N;
-    const int h = threadIdx.x;
+    const int h = threadIdx.x, warp = h >> 5;
     const int hx = h % PRX, hy = h / PRX;
     const int x0 = blockIdx.x * PTX - 1, y0 = blockIdx.y * PTY - 1;
     const int x = x0 + hx, y = y0 + hy;
@@ -213,20 +222,32 @@ __global__ void __launch_bounds__(PRIOR_THREADS, PRIOR_MIN_BLOCKS) k_prior(const
         }
         __syncthreads();
         float hs = 0.f, fm = 0.f, gs = 0.f;
-        if (ring) {
+        // the value alone needs the pairs of interior cells only (a pair
+        // enters H at its lower voxel); the gradient also needs the halo's
+        if (GRAD ? ring : interior) {
             const float *fc = fpl + cur * PRS + h;
             fm = *fc;
             float *eu = Eu + (s3 * 9) * PRS + h;
-            if (up) {
-                if (full) prior_up_pairs<false, WANT_H, GRAD>(fpl + nxt * PRS + h, fm, eu, 0u, a, gs, hs);
-                else prior_up_pairs<true, WANT_H, GRAD>(fpl + nxt * PRS + h, fm, eu, mup, a, gs, hs);
-            } else if (GRAD && three) {
+            float *ep = Ep + ((z % PRIOR_PL_SLOTS) * 4) * PRS + h;
+            const float *fn = fpl + nxt * PRS + h;
+            if (GRAD && three && !up) {
 #pragma unroll
                 for (int u = 0; u < 9; ++u) eu[u * PRS] = 0.f;
             }
-            float *ep = Ep + ((z % PRIOR_PL_SLOTS) * 4) * PRS + h;
-            if (full) prior_plane_pairs<false, WANT_H, GRAD>(fc, fm, ep, 0u, a, gs, hs);
-            else prior_plane_pairs<true, WANT_H, GRAD>(fc, fm, ep, mpl, a, gs, hs);
+            if (!full) {
+                if (up) prior_up_pairs<true, WANT_H, GRAD>(fn, fm, eu, mup, a, gs, hs);
+                prior_plane_pairs<true, WANT_H, GRAD>(fc, fm, ep, mpl, a, gs, hs);
+            } else if (GRAD && warp == 0) {
+                // bottom halo row: only pairs towards dy = +1 reach the interior
+                if (up) prior_up_pairs<false, WANT_H, GRAD, 0x1c0u>(fn, fm, eu, 0u, a, gs, hs);
+                prior_plane_pairs<false, WANT_H, GRAD, 0xeu>(fc, fm, ep, 0u, a, gs, hs);
+            } else if (GRAD && warp == PRIOR_THREADS / 32 - 1) {
+                // top halo row: only the z+1 pairs towards dy = -1
+                if (up) prior_up_pairs<false, WANT_H, GRAD, 0x007u>(fn, fm, eu, 0u, a, gs, hs);
+            } else {
+                if (up) prior_up_pairs<false, WANT_H, GRAD>(fn, fm, eu, 0u, a, gs, hs);
+                prior_plane_pairs<false, WANT_H, GRAD>(fc, fm, ep, 0u, a, gs, hs);
+            }
         }
         __syncthreads();
         if (!GRAD) {
@@ -470,6 +491,7 @@ PriorArgs make_prior_args(int n, int nb, const tc_prior *pr) {
     a.p = (float)pr->p;
     a.c = (float)pr->c;
     a.qexp = (float)(2.0 - pr->p);
+    a.cq = (float)(pr->c * (2.0 - pr->p));
     a.lk = (float)((2.0 - pr->p) * std::log2(1.0 / pr->sigma));
     a.two_c = (float)(2.0 * pr->c);
     a.gscale = (float)(2.0 * pr->lambda / (pr->sigma * pr->sigma));

@@ -121,7 +121,8 @@ __global__ void __launch_bounds__(512) k_fwd_row(const float2 *__restrict__ T, f
 template <bool BLUE>
 __device__ __forceinline__ int didx(int i) { return BLUE ? spad(i) : i; }
 
-template <bool BLUE>
+// LOGL > 0: Bluestein length 2^LOGL fixed at compile time.
+template <bool BLUE, int LOGL = 0>
 __global__ void __launch_bounds__(512) k_fwd_det(const float2 *__restrict__ P, float *__restrict__ y,
                           const float *__restrict__ bsino, const float *__restrict__ wsino,
                           float *__restrict__ resid, double *__restrict__ partials,
@@ -162,7 +163,8 @@ __global__ void __launch_bounds__(512) k_fwd_det(const float2 *__restrict__ P, f
     __syncthreads();
     const float2 *res;
     if (BLUE) {
-        bluestein<+1>(sm, D, g.L, g.log2L, g.chirp, g.bhat, g.twL);
+        if constexpr (LOGL > 0) bluestein_ct<+1, LOGL>(sm, D, g.chirp, g.bhat, g.twL);
+        else bluestein<+1>(sm, D, g.L, g.log2L, g.chirp, g.bhat, g.twL);
         res = sm;
     } else {
         res = fft_mixed<+1>(bufA, bufB, g.rp, tw, root0);
@@ -191,7 +193,7 @@ __global__ void __launch_bounds__(512) k_fwd_det(const float2 *__restrict__ P, f
 }
 
 // ------------------------------------------------------------ adjoint ------
-template <bool BLUE>
+template <bool BLUE, int LOGL = 0>
 __global__ void __launch_bounds__(512) k_adj_det(const float *__restrict__ ysino, float2 *__restrict__ V,
                           const KArgs g) {
     extern __shared__ float2 sm[];
@@ -210,7 +212,8 @@ __global__ void __launch_bounds__(512) k_adj_det(const float *__restrict__ ysino
     __syncthreads();
     const float2 *Z;
     if (BLUE) {
-        bluestein<-1>(sm, D, g.L, g.log2L, g.chirp, g.bhat, g.twL);
+        if constexpr (LOGL > 0) bluestein_ct<-1, LOGL>(sm, D, g.chirp, g.bhat, g.twL);
+        else bluestein<-1>(sm, D, g.L, g.log2L, g.chirp, g.bhat, g.twL);
         Z = sm;
     } else {
         Z = fft_mixed<-1>(bufA, bufB, g.rp, tw, root0);
@@ -375,6 +378,21 @@ int with_logn(int lg, F &&f) {
     }
 }
 
+// Bluestein lengths L = 2^8 .. 2^13 (the plan caps L at 8192) get compile-time
+// FFTs; other lengths keep the run-time form.
+template <class F>
+void with_logl(int lg, F &&f) {
+    switch (lg) {
+        case 8: f(std::integral_constant<int, 8>{}); break;
+        case 9: f(std::integral_constant<int, 9>{}); break;
+        case 10: f(std::integral_constant<int, 10>{}); break;
+        case 11: f(std::integral_constant<int, 11>{}); break;
+        case 12: f(std::integral_constant<int, 12>{}); break;
+        case 13: f(std::integral_constant<int, 13>{}); break;
+        default: f(std::integral_constant<int, 0>{}); break;
+    }
+}
+
 }  // namespace
 
 int launch_radon_fwd_chunk(tc_plan *p, const float *x, float *y, int nb,
@@ -398,7 +416,10 @@ int launch_radon_fwd_chunk(tc_plan *p, const float *x, float *y, int nb,
     if (resid) mode |= DET_RESID;
     if (resid && obj_acc) mode |= DET_OBJ;
     if (g.blue)
-        TC_PROFILED(TCK_FWD_DET, s, k_fwd_det<true><<<gd, p->threads_det, p->smem_det, s>>>(p->pv, y, b, w, resid, p->partials, g, mode));
+        with_logl(g.log2L, [&](auto L) {
+            TC_PROFILED(TCK_FWD_DET, s, k_fwd_det<true, decltype(L)::value><<<gd, p->threads_det, p->smem_det, s>>>(
+                                            p->pv, y, b, w, resid, p->partials, g, mode));
+        });
     else
         TC_PROFILED(TCK_FWD_DET, s, k_fwd_det<false><<<gd, p->threads_det, p->smem_det, s>>>(p->pv, y, b, w, resid, p->partials, g, mode));
     TC_LAUNCHED("k_fwd_det");
@@ -414,7 +435,10 @@ int launch_radon_adj_chunk(tc_plan *p, const float *y, float *x, int nb,
     const KArgs &g = p->k;
     dim3 gd((g.A + 1) / 2, nb);
     if (g.blue)
-        TC_PROFILED(TCK_ADJ_DET, s, k_adj_det<true><<<gd, p->threads_det, p->smem_det, s>>>(y, p->pv, g));
+        with_logl(g.log2L, [&](auto L) {
+            TC_PROFILED(TCK_ADJ_DET, s, k_adj_det<true, decltype(L)::value><<<gd, p->threads_det, p->smem_det, s>>>(
+                                            y, p->pv, g));
+        });
     else
         TC_PROFILED(TCK_ADJ_DET, s, k_adj_det<false><<<gd, p->threads_det, p->smem_det, s>>>(y, p->pv, g));
     TC_LAUNCHED("k_adj_det");
@@ -463,5 +487,11 @@ int radon_configure_kernels(tc_plan *p) {
         (rc = raise_smem_limit(k_fwd_det<false>, p->smem_det)) ||
         (rc = raise_smem_limit(k_adj_det<false>, p->smem_det)))
         return rc;
-    return TC_OK;
+    if (p->k.blue)
+        with_logl(p->k.log2L, [&](auto L) {
+            constexpr int LL = decltype(L)::value;
+            if (!rc) rc = raise_smem_limit(k_fwd_det<true, LL>, p->smem_det);
+            if (!rc) rc = raise_smem_limit(k_adj_det<true, LL>, p->smem_det);
+        });
+    return rc;
 }
