@@ -182,6 +182,8 @@ int launch_radon_adj_chunk(tc_plan *p, const float *y, float *x, int nb,
 int launch_prior_grad(tc_plan *p, const float *x, float *g, int nb,
                       const tc_prior *pr, double *h_acc, cudaStream_t s,
                       const float *dot_x = nullptr);
+// CTAs (and FP64 partial sums) of one prior launch on N x N slices.
+int prior_tile_count(int n);
 // h_acc = lambda H(x) only (no gradient).
 int launch_prior_value(tc_plan *p, const float *x, int nb, const tc_prior *pr,
                        double *h_acc, cudaStream_t s);

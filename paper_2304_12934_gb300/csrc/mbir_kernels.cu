@@ -511,6 +511,8 @@ double prior_value_scale(const tc_prior *pr) { return 2.0 * pr->lambda / (pr->si
 
 }  // namespace
 
+int prior_tile_count(int n) { return ((n + PTX - 1) / PTX) * ((n + PTY - 1) / PTY); }
+
 int launch_prior_grad(tc_plan *p, const float *x, float *g, int nb,
                       const tc_prior *pr, double *h_acc, cudaStream_t s, const float *dot_x) {
     const PriorArgs a = make_prior_args(p->k.N, nb, pr);
