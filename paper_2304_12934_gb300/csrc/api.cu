@@ -232,9 +232,57 @@ namespace {
 
 // The accelerated-gradient loop.  fresh_z: z := x is still to be done;
 // ready: per-chunk events gating the first iteration (host streaming).
+// Destination of the last iteration's x_{k+1} in a host-streamed solve.
+struct HostOut {
+    float *x_host;                   // [batch][N][N], host
+    cudaStream_t cs;                 // copy stream
+    std::vector<cudaEvent_t> *ev;    // events created here, owned by the caller
+};
+
+// Last iteration of the gradient-restart schedule with a prior, x_{k+1}
+// streamed out slab by slab: x_{k+1} = z_k - step g_k needs no global scalar,
+// so a slab's x_{k+1} is final once its data gradient and its prior (which
+// reads a one-slice halo) are done; its copy to the host then overlaps the
+// remaining chunks.  The restart test and z_{k+1} follow at the end.  The
+// result equals the in-place update bit for bit.
+int last_iteration_streamed(tc_plan *p, const float *b, const float *w, float *x, int batch,
+                            const tc_prior *prior, const tc_solve_opts *opts, tc_solve_state *st,
+                            cudaStream_t s, const cudaEvent_t *ready, const HostOut &out) {
+    TC_CUDA(cudaMemsetAsync(p->scal + SC_DATA, 0, 2 * sizeof(double), s));
+    const size_t ni = img_elems(p), ns = sino_elems(p);
+    const int nslab = (batch + p->chunk - 1) / p->chunk;
+    auto finish = [&](int j) -> int {
+        const int z0 = j * p->chunk, z1 = z0 + p->chunk < batch ? z0 + p->chunk : batch;
+        int rc = launch_prior_grad(p, st->z, st->g, batch, prior, p->scal + SC_PRIOR, s, x, z0, z1);
+        if (!rc) rc = launch_step_to_candidate(p, st->z + z0 * ni, st->g + z0 * ni, (size_t)(z1 - z0) * ni, s);
+        if (rc) return rc;
+        cudaEvent_t e = nullptr;
+        TC_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        out.ev->push_back(e);
+        TC_CUDA(cudaEventRecord(e, s));
+        TC_CUDA(cudaStreamWaitEvent(out.cs, e, 0));
+        TC_CUDA(cudaMemcpyAsync(out.x_host + z0 * ni, st->g + z0 * ni, (size_t)(z1 - z0) * ni * sizeof(float),
+                                cudaMemcpyDeviceToHost, out.cs));
+        return TC_OK;
+    };
+    for (int c = 0; c < nslab; ++c) {
+        const int c0 = c * p->chunk, nb = batch - c0 < p->chunk ? batch - c0 : p->chunk;
+        if (ready) TC_CUDA(cudaStreamWaitEvent(s, ready[c], 0));
+        int rc = launch_radon_fwd_chunk(p, st->z + c0 * ni, nullptr, nb, b + c0 * ns,
+                                        w ? w + c0 * ns : nullptr, p->sr, p->scal + SC_DATA, s);
+        if (!rc) rc = launch_radon_adj_chunk(p, p->sr, st->g + c0 * ni, nb, s);
+        if (!rc && c > 0) rc = finish(c - 1);  // slab c holds the upper halo of slab c - 1
+        if (rc) return rc;
+    }
+    int rc = finish(nslab - 1);
+    if (!rc) rc = launch_solver_scalar(p, opts->restart, s);
+    if (!rc) rc = launch_update_monotone(p, x, st->z, st->g, img_elems(p) * batch, s, 1);
+    return rc;
+}
+
 int solve_loop(tc_plan *p, const float *b, const float *w, float *x, int batch,
                const tc_prior *prior, const tc_solve_opts *opts, tc_solve_state *st,
-               cudaStream_t s, bool fresh_z, const cudaEvent_t *ready) {
+               cudaStream_t s, bool fresh_z, const cudaEvent_t *ready, const HostOut *out = nullptr) {
     const size_t n = img_elems(p) * batch;
     int rc;
     if (st->k == 0) {
@@ -266,6 +314,12 @@ int solve_loop(tc_plan *p, const float *b, const float *w, float *x, int batch,
     for (int it = 0; it < (opts->restart == 2 ? 0 : opts->n_iter); ++it) {
         // the prior's value H is only reported for the last gradient point
         const bool fused = prior && prior->lambda != 0.0;  // dots inside the prior kernel
+        if (out && fused && it == opts->n_iter - 1) {
+            if ((rc = last_iteration_streamed(p, b, w, x, batch, prior, opts, st, s,
+                                              it == 0 ? ready : nullptr, *out)))
+                return rc;
+            continue;
+        }
         if ((rc = grad_impl(p, st->z, b, w, prior, st->g, batch, s, it == opts->n_iter - 1,
                             it == 0 ? ready : nullptr, fused ? x : nullptr)))
             return rc;
@@ -301,9 +355,12 @@ int check_solve(tc_plan *p, int batch, const tc_prior *prior, const tc_solve_opt
 // Stream and events owned by one host-streamed solve.
 struct CopyStream {
     cudaStream_t cs = nullptr;
-    std::vector<cudaEvent_t> ev;
+    std::vector<cudaEvent_t> ev;      // inbound slabs (+ the start event); fixed during the solve
+    std::vector<cudaEvent_t> out_ev;  // outbound slabs, appended while the last iteration runs
     ~CopyStream() {
         for (cudaEvent_t e : ev)
+            if (e) cudaEventDestroy(e);
+        for (cudaEvent_t e : out_ev)
             if (e) cudaEventDestroy(e);
         if (cs) cudaStreamDestroy(cs);
     }
@@ -424,11 +481,17 @@ int mbir_solve_host(tc_plan *p, const float *b_host, const float *w_host, float 
     const bool overlap = opts->n_iter > 0;
     if (!overlap)
         for (int c = 0; c < nslab; ++c) TC_CUDA(cudaStreamWaitEvent(s, cp.ev[c], 0));
+    // the last gradient-restart iteration with a prior sends x back slab by
+    // slab while it runs; otherwise x goes back after the solve
+    const bool stream_out = overlap && opts->restart != 2 && prior && prior->lambda != 0.0;
+    const HostOut out{x_host, cp.cs, &cp.out_ev};
     int rc = solve_loop(p, dev_b, w_host ? dev_w : nullptr, dev_x, batch, prior, opts, st, s,
-                        false, overlap ? cp.ev.data() : nullptr);
+                        false, overlap ? cp.ev.data() : nullptr, stream_out ? &out : nullptr);
     if (rc) return rc;
-    TC_CUDA(cudaMemcpyAsync(x_host, dev_x, (size_t)batch * ni * sizeof(float), cudaMemcpyDeviceToHost, s));
+    if (!stream_out)
+        TC_CUDA(cudaMemcpyAsync(x_host, dev_x, (size_t)batch * ni * sizeof(float), cudaMemcpyDeviceToHost, s));
     TC_CUDA(cudaStreamSynchronize(s));
+    TC_CUDA(cudaStreamSynchronize(cp.cs));
     return TC_OK;
 }
 

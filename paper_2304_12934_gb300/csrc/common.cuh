@@ -179,9 +179,12 @@ int launch_radon_adj_chunk(tc_plan *p, const float *y, float *x, int nb,
                            cudaStream_t s);
 // g += lambda grad H(x); h_acc (or NULL) = lambda H(x); with dot_x, also
 // scal[SC_DOT_GZX] = <g, x - dot_x>, scal[SC_DOT_GG] = <g, g> of the final g.
+// x holds nb slices; only slices [z0, z1) (z1 < 0: nb) get their gradient
+// (neighbours outside the range are read) and enter the sums, which a slab
+// with z0 > 0 adds to those already held.
 int launch_prior_grad(tc_plan *p, const float *x, float *g, int nb,
                       const tc_prior *pr, double *h_acc, cudaStream_t s,
-                      const float *dot_x = nullptr);
+                      const float *dot_x = nullptr, int z0 = 0, int z1 = -1);
 // CTAs (and FP64 partial sums) of one prior launch on N x N slices.
 int prior_tile_count(int n);
 // h_acc = lambda H(x) only (no gradient).
@@ -193,7 +196,7 @@ int launch_prior_value(tc_plan *p, const float *x, int nb, const tc_prior *pr,
 int launch_step_to_candidate(tc_plan *p, const float *z, float *g, size_t n, cudaStream_t s);
 int launch_monotone_scalar(tc_plan *p, int init, cudaStream_t s);
 int launch_update_monotone(tc_plan *p, float *x, float *z, const float *v, size_t n,
-                           cudaStream_t s);
+                           cudaStream_t s, int accept_all = 0);
 int launch_reduce_finalize(const double *partials, int n, double *acc,
                            int accumulate, double scale, cudaStream_t s);
 int launch_dots_gzx_gg(tc_plan *p, const float *g, const float *z, const float *x,

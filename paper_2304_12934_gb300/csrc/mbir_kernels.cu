@@ -14,6 +14,7 @@ namespace {
 
 struct PriorArgs {
     int N, B, dims;
+    int z0, z1;        // slices of the volume [0, B) whose gradient this launch produces
     float p, c, qexp;  // qexp = 2 - p
     float cq;          // c (2 - p)
     float lk;          // qexp * log2(1 / sigma)
@@ -76,8 +77,8 @@ __device__ __forceinline__ float qggmrf_inv(float d, const PriorArgs &a) {
 // WANT_H also accumulates H (otherwise only the gradient is produced).
 // DOTS also accumulates <g, f - xprev> and <g, g> of the final gradient g (the
 // inner products of the solver's restart test), sparing a separate pass.
-// Per-thread sums run in FP32 over 8 z steps, then over 8 such groups, then in
-// FP64 (the FP64 pipe of this part is narrow), always in the same order.
+// Per-thread sums run in FP32 over 8, 64 and 512 z steps and in FP64 from the
+// block sum on (the FP64 pipe of this part is narrow), always in the same order.
 #define PTX 32
 #define PTY 12
 #define PRX (PTX + 2)
@@ -197,28 +198,33 @@ __global__ void __launch_bounds__(PRIOR_THREADS, PRIOR_MIN_BLOCKS) k_prior(const
             if (inb && ring_in(pl_dx(q), pl_dy(q)) && (interior || is_interior(pl_dx(q), pl_dy(q))))
                 mpl |= 1u << q;
     }
+    // A slab [z0, z1) of a 3D volume starts one plane below, at the halo plane,
+    // whose step only evaluates the pairs towards z0 (no gradient, no sums).
+    const int zs = (three && a.z0 > 0) ? a.z0 - 1 : a.z0;
+    const size_t off = (size_t)y * N + x;
     if (ring) {
         for (int u = 0; u < 9; ++u)
             for (int sl = 0; sl < PRIOR_UP_SLOTS; ++sl) Eu[(sl * 9 + u) * PRS + h] = 0.f;
-        fpl[h] = inb ? f[(size_t)y * N + x] : 0.f;
+        fpl[h] = inb ? f[(size_t)zs * NN + off] : 0.f;
     }
     // register prefetch: the plane the next step stores (3D: z + 2, 2D: z + 1)
-    const size_t off = (size_t)y * N + x;
-    float f_nx = (inb && B > 1) ? f[NN + off] : 0.f;
-    float h8 = 0.f, h64 = 0.f, a8 = 0.f, a64 = 0.f, b8 = 0.f, b64 = 0.f;
-    double hacc = 0.0, d1 = 0.0, d2 = 0.0;
+    float f_nx = (inb && zs + 1 < B) ? f[(size_t)(zs + 1) * NN + off] : 0.f;
+    // per-thread sums: FP32 over 8, 64 and 512 z steps (a level never adds
+    // more than 8 terms for volumes up to 4096 slices), FP64 from the block sum on
+    float h8 = 0.f, h64 = 0.f, h512 = 0.f, a8 = 0.f, a64 = 0.f, a512 = 0.f, b8 = 0.f, b64 = 0.f, b512 = 0.f;
     int s3 = 0, p3 = PRIOR_UP_SLOTS - 1;  // this step's / previous step's z+1 slot
-    for (int z = 0; z < B; ++z) {
-        const int cur = z & 1, nxt = cur ^ 1;
+    for (int z = zs; z < a.z1; ++z) {
+        const int cur = (z - zs) & 1, nxt = cur ^ 1;
+        const bool own = z >= a.z0;
         const bool up = three && z + 1 < B;
         const int pz = three ? z + 2 : z + 1;
         const float f_pf = (inb && pz < B) ? f[(size_t)pz * NN + off] : 0.f;
         const size_t i = (size_t)z * NN + off;
-        const float g_old = (GRAD && interior) ? g[i] : 0.f;
-        const float x_old = (DOTS && interior) ? xprev[i] : 0.f;
+        const float g_old = (GRAD && own && interior) ? g[i] : 0.f;
+        const float x_old = (DOTS && own && interior) ? xprev[i] : 0.f;
         if (ring) {
             if (up) fpl[nxt * PRS + h] = f_nx;                 // 3D: plane z + 1
-            else if (!three && z > 0) fpl[cur * PRS + h] = f_nx;  // 2D: slices are independent
+            else if (!three && z > zs) fpl[cur * PRS + h] = f_nx;  // 2D: slices are independent
         }
         __syncthreads();
         float hs = 0.f, fm = 0.f, gs = 0.f;
@@ -251,8 +257,8 @@ __global__ void __launch_bounds__(PRIOR_THREADS, PRIOR_MIN_BLOCKS) k_prior(const
         }
         __syncthreads();
         if (!GRAD) {
-            if (interior) h8 += hs;
-        } else if (interior) {
+            if (own && interior) h8 += hs;
+        } else if (own && interior) {
             // minus the shares of the pairs this voxel closes (evaluated at
             // their lower voxels: in-plane this step, towards z+1 the last)
             if (three) {
@@ -280,11 +286,7 @@ __global__ void __launch_bounds__(PRIOR_THREADS, PRIOR_MIN_BLOCKS) k_prior(const
             h64 += h8; a64 += a8; b64 += b8;
             h8 = a8 = b8 = 0.f;
             if ((z & 63) == 63) {
-                if (WANT_H) hacc += (double)h64;
-                if (DOTS) {
-                    d1 += (double)a64;
-                    d2 += (double)b64;
-                }
+                h512 += h64; a512 += a64; b512 += b64;
                 h64 = a64 = b64 = 0.f;
             }
         }
@@ -294,12 +296,12 @@ __global__ void __launch_bounds__(PRIOR_THREADS, PRIOR_MIN_BLOCKS) k_prior(const
     }
     const int bid = blockIdx.y * gridDim.x + blockIdx.x;
     if (WANT_H) {
-        const double tot = block_sum_f64(hacc + ((double)h64 + (double)h8), red);
+        const double tot = block_sum_f64((double)h512 + ((double)h64 + (double)h8), red);
         if (threadIdx.x == 0) partials[bid] = tot;
     }
     if (DOTS) {
-        const double t1 = block_sum_f64(d1 + ((double)a64 + (double)a8), red);
-        const double t2 = block_sum_f64(d2 + ((double)b64 + (double)b8), red);
+        const double t1 = block_sum_f64((double)a512 + ((double)a64 + (double)a8), red);
+        const double t2 = block_sum_f64((double)b512 + ((double)b64 + (double)b8), red);
         if (threadIdx.x == 0) {
             pd1[bid] = t1;
             pd2[bid] = t2;
@@ -436,9 +438,12 @@ __global__ void k_monotone_scalar(double *sc, int init) {
     sc[SC_ACCEPT] = accept ? 1.0 : 0.0;
 }
 
+// accept_all: v is x_{k+1} (the gradient-restart schedule, with x_{k+1}
+// formed ahead of the restart decision).
 __global__ void k_update_monotone(float4 *__restrict__ x, float4 *__restrict__ z,
-                                  const float4 *__restrict__ v, size_t n4, const double *__restrict__ sc) {
-    const bool accept = sc[SC_ACCEPT] != 0.0;
+                                  const float4 *__restrict__ v, size_t n4, const double *__restrict__ sc,
+                                  int accept_all) {
+    const bool accept = accept_all || sc[SC_ACCEPT] != 0.0;
     const float beta = (float)sc[SC_BETA];
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4;
          i += (size_t)gridDim.x * blockDim.x) {
@@ -487,6 +492,8 @@ PriorArgs make_prior_args(int n, int nb, const tc_prior *pr) {
     PriorArgs a;
     a.N = n;
     a.B = nb;
+    a.z0 = 0;
+    a.z1 = nb;
     a.dims = pr->dims;
     a.p = (float)pr->p;
     a.c = (float)pr->c;
@@ -514,8 +521,14 @@ double prior_value_scale(const tc_prior *pr) { return 2.0 * pr->lambda / (pr->si
 int prior_tile_count(int n) { return ((n + PTX - 1) / PTX) * ((n + PTY - 1) / PTY); }
 
 int launch_prior_grad(tc_plan *p, const float *x, float *g, int nb,
-                      const tc_prior *pr, double *h_acc, cudaStream_t s, const float *dot_x) {
-    const PriorArgs a = make_prior_args(p->k.N, nb, pr);
+                      const tc_prior *pr, double *h_acc, cudaStream_t s, const float *dot_x,
+                      int z0, int z1) {
+    PriorArgs a = make_prior_args(p->k.N, nb, pr);
+    if (z1 < 0) z1 = nb;
+    if (z0 < 0 || z0 >= z1 || z1 > nb) return TC_ERR_INVALID_ARG;
+    a.z0 = z0;
+    a.z1 = z1;
+    const int acc = z0 > 0;  // a later slab adds to the sums of the earlier ones
     dim3 grid((a.N + PTX - 1) / PTX, (a.N + PTY - 1) / PTY);
     const int blocks = grid.x * grid.y;
     if (blocks > p->slot) return TC_ERR_UNSUPPORTED;
@@ -535,11 +548,11 @@ int launch_prior_grad(tc_plan *p, const float *x, float *g, int nb,
     }
     TC_LAUNCHED("k_prior");
     if (dot_x) {
-        int rc = launch_reduce_finalize(p1, blocks, p->scal + SC_DOT_GZX, 0, 1.0, s);
-        if (!rc) rc = launch_reduce_finalize(p2, blocks, p->scal + SC_DOT_GG, 0, 1.0, s);
+        int rc = launch_reduce_finalize(p1, blocks, p->scal + SC_DOT_GZX, acc, 1.0, s);
+        if (!rc) rc = launch_reduce_finalize(p2, blocks, p->scal + SC_DOT_GG, acc, 1.0, s);
         if (rc) return rc;
     }
-    if (h_acc) return launch_reduce_finalize(part, blocks, h_acc, 0, prior_value_scale(pr), s);
+    if (h_acc) return launch_reduce_finalize(part, blocks, h_acc, acc, prior_value_scale(pr), s);
     return TC_OK;
 }
 
@@ -573,12 +586,12 @@ int launch_monotone_scalar(tc_plan *p, int init, cudaStream_t s) {
 }
 
 int launch_update_monotone(tc_plan *p, float *x, float *z, const float *v, size_t n,
-                           cudaStream_t s) {
+                           cudaStream_t s, int accept_all) {
     const size_t n4 = n / 4;
     TC_PROFILED(TCK_UPDATE, s,
                 k_update_monotone<<<grid_for(n4), TC_RED_THREADS, 0, s>>>(
         reinterpret_cast<float4 *>(x), reinterpret_cast<float4 *>(z),
-        reinterpret_cast<const float4 *>(v), n4, p->scal));
+        reinterpret_cast<const float4 *>(v), n4, p->scal, accept_all));
     TC_LAUNCHED("k_update_monotone");
     return TC_OK;
 }

@@ -163,9 +163,12 @@ def test_host_buffer_solve_matches_device_solve(api):
     assert torch.equal(xh, x.cpu())
 
 
-def test_host_streamed_solve_in_slabs_matches_device_solve(api):
+@pytest.mark.parametrize("n_iter", [4, 1])
+def test_host_streamed_solve_in_slabs_matches_device_solve(api, n_iter):
     """Five slices copied in slabs of two on the copy stream, weights and the
-    3D prior: identical to the same solve on resident device buffers."""
+    3D prior: identical to the same solve on resident device buffers.  The last
+    iteration returns x slab by slab while later slabs still compute (with
+    n_iter = 1 that iteration also waits for the inbound slabs)."""
     B = 5
     f, b = _data(B)
     rng = np.random.default_rng(9)
@@ -174,13 +177,16 @@ def test_host_streamed_solve_in_slabs_matches_device_solve(api):
     prior = api.Prior(lam=1e-3, dims=3)
     with api.Plan(N, A, D, max_batch=2) as plan:
         x = torch.zeros((B, N, N), device="cuda:0")
-        sd = api.mbir_solve(plan, t32(b), t32(w), x, 4, step, prior)
+        sd = api.mbir_solve(plan, t32(b), t32(w), x, n_iter, step, prior)
         bh = torch.tensor(b, dtype=torch.float32).pin_memory()
         wh = torch.tensor(w, dtype=torch.float32).pin_memory()
         xh = torch.zeros((B, N, N), dtype=torch.float32).pin_memory()
-        sh = api.mbir_solve_host(plan, bh, wh, xh, 4, step, prior)
+        sh = api.mbir_solve_host(plan, bh, wh, xh, n_iter, step, prior)
     assert torch.equal(xh, x.cpu())
-    assert sh.k == sd.k == 4 and sh.n_restarts == sd.n_restarts
+    assert sh.k == sd.k == n_iter and sh.n_restarts == sd.n_restarts
+    assert torch.equal(sh.z.cpu(), sd.z.cpu())
+    assert abs(sh.obj[0] - sd.obj[0]) <= 1e-12 * abs(sd.obj[0])
+    assert abs(sh.obj[1] - sd.obj[1]) <= 1e-9 * abs(sd.obj[1])
 
 
 @pytest.mark.parametrize("dims", [3, 2])
