@@ -154,7 +154,7 @@ def algorithmic_bytes(name, N, A, D, w, B):
         "k_adj_col": grid_rows + img,
         "k_prior": 4 * img,  # f, g read + g written, and x_prev for the fused restart dots
         "k_dots_gzx_gg": 3 * img,
-        "k_update": 5 * img,
+        "k_update": 4 * img,  # x and the next iterate read, x and z written
     }
     return per.get(name, 0) * B
 

@@ -181,7 +181,8 @@ typedef struct {
 } tc_solve_opts;
 
 /* Solver state; resuming with the same state continues the iteration exactly.
- *   z, g   caller-owned DEVICE buffers [batch][N][N] (momentum point, gradient)
+ *   z, g   caller-owned DEVICE buffers [batch][N][N] (momentum point; g is
+ *          scratch: the gradient or the next iterate, depending on the step)
  *   t      momentum scalar t_k (host copy, updated on return)
  *   k      iterations completed; k == 0 starts fresh (z := x, t := 1)
  *   n_restarts  restarts taken so far (monotone variant: rejected steps)

@@ -56,7 +56,7 @@ int check_ptrs(std::initializer_list<const void *> req, std::initializer_list<co
 int grad_impl(tc_plan *p, const float *x, const float *b, const float *w,
               const tc_prior *prior, float *grad, int batch, cudaStream_t s,
               bool want_prior_value = true, const cudaEvent_t *ready = nullptr,
-              const float *dot_x = nullptr) {
+              const float *dot_x = nullptr, double step = 0.0) {
     TC_CUDA(cudaMemsetAsync(p->scal + SC_DATA, 0, 2 * sizeof(double), s));
     const size_t ni = img_elems(p), ns = sino_elems(p);
     for (int c0 = 0; c0 < batch; c0 += p->chunk) {
@@ -70,7 +70,7 @@ int grad_impl(tc_plan *p, const float *x, const float *b, const float *w,
     }
     if (prior && prior->lambda != 0.0) {
         int rc = launch_prior_grad(p, x, grad, batch, prior,
-                                   want_prior_value ? p->scal + SC_PRIOR : nullptr, s, dot_x);
+                                   want_prior_value ? p->scal + SC_PRIOR : nullptr, s, dot_x, 0, -1, step);
         if (rc) return rc;
     }
     return TC_OK;
@@ -253,8 +253,9 @@ int last_iteration_streamed(tc_plan *p, const float *b, const float *w, float *x
     const int nslab = (batch + p->chunk - 1) / p->chunk;
     auto finish = [&](int j) -> int {
         const int z0 = j * p->chunk, z1 = z0 + p->chunk < batch ? z0 + p->chunk : batch;
-        int rc = launch_prior_grad(p, st->z, st->g, batch, prior, p->scal + SC_PRIOR, s, x, z0, z1);
-        if (!rc) rc = launch_step_to_candidate(p, st->z + z0 * ni, st->g + z0 * ni, (size_t)(z1 - z0) * ni, s);
+        // the prior kernel leaves x_{k+1} = z - step g of the slab in g
+        int rc = launch_prior_grad(p, st->z, st->g, batch, prior, p->scal + SC_PRIOR, s, x, z0, z1,
+                                   opts->step);
         if (rc) return rc;
         cudaEvent_t e = nullptr;
         TC_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
@@ -320,12 +321,16 @@ int solve_loop(tc_plan *p, const float *b, const float *w, float *x, int batch,
                 return rc;
             continue;
         }
+        // fused: the prior kernel also forms the restart dots and leaves
+        // x_{k+1} = z_k - step g in g; otherwise separate dots and update
         if ((rc = grad_impl(p, st->z, b, w, prior, st->g, batch, s, it == opts->n_iter - 1,
-                            it == 0 ? ready : nullptr, fused ? x : nullptr)))
+                            it == 0 ? ready : nullptr, fused ? x : nullptr, opts->step)))
             return rc;
         if (!fused && (rc = launch_dots_gzx_gg(p, st->g, st->z, x, n, s))) return rc;
         if ((rc = launch_solver_scalar(p, opts->restart, s))) return rc;
-        if ((rc = launch_update(p, x, st->z, st->g, n, s))) return rc;
+        if (fused) rc = launch_update_monotone(p, x, st->z, st->g, n, s, 1);
+        else rc = launch_update(p, x, st->z, st->g, n, s);
+        if (rc) return rc;
     }
     double sc[SC_COUNT];
     TC_CUDA(cudaMemcpyAsync(sc, p->scal, sizeof(sc), cudaMemcpyDeviceToHost, s));

@@ -178,13 +178,14 @@ int launch_radon_fwd_chunk(tc_plan *p, const float *x, float *y, int nb,
 int launch_radon_adj_chunk(tc_plan *p, const float *y, float *x, int nb,
                            cudaStream_t s);
 // g += lambda grad H(x); h_acc (or NULL) = lambda H(x); with dot_x, also
-// scal[SC_DOT_GZX] = <g, x - dot_x>, scal[SC_DOT_GG] = <g, g> of the final g.
+// scal[SC_DOT_GZX] = <g, x - dot_x>, scal[SC_DOT_GG] = <g, g> of the final g,
+// and g then receives x - step g (the solver's next iterate) instead.
 // x holds nb slices; only slices [z0, z1) (z1 < 0: nb) get their gradient
 // (neighbours outside the range are read) and enter the sums, which a slab
 // with z0 > 0 adds to those already held.
 int launch_prior_grad(tc_plan *p, const float *x, float *g, int nb,
                       const tc_prior *pr, double *h_acc, cudaStream_t s,
-                      const float *dot_x = nullptr, int z0 = 0, int z1 = -1);
+                      const float *dot_x = nullptr, int z0 = 0, int z1 = -1, double step = 0.0);
 // CTAs (and FP64 partial sums) of one prior launch on N x N slices.
 int prior_tile_count(int n);
 // h_acc = lambda H(x) only (no gradient).

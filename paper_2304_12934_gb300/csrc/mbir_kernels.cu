@@ -20,6 +20,7 @@ struct PriorArgs {
     float lk;          // qexp * log2(1 / sigma)
     float two_c;       // 2 c
     float gscale;      // 2 lambda / sigma^2: scale of the gradient sum
+    float step;        // DOTS: the solver's step; g receives z - step * grad instead of grad
     float w1, w2, w3;  // weights at distance 1, sqrt 2, sqrt 3
 };
 
@@ -76,7 +77,8 @@ __device__ __forceinline__ float qggmrf_inv(float d, const PriorArgs &a) {
 // read); CTAs at the volume border test each pair against the border rule.
 // WANT_H also accumulates H (otherwise only the gradient is produced).
 // DOTS also accumulates <g, f - xprev> and <g, g> of the final gradient g (the
-// inner products of the solver's restart test), sparing a separate pass.
+// inner products of the solver's restart test), sparing a separate pass, and
+// stores the solver's next iterate f - step g in place of g.
 // Per-thread sums run in FP32 over 8, 64 and 512 z steps and in FP64 from the
 // block sum on (the FP64 pipe of this part is narrow), always in the same order.
 #define PTX 32
@@ -275,7 +277,8 @@ __global__ void __launch_bounds__(PRIOR_THREADS, PRIOR_MIN_BLOCKS) k_prior(const
             for (int q = 0; q < 4; ++q)
                 gs = fmaf((q & 1) ? -a.w2 : -a.w1, ep[q * PRS - pl_dy(q) * PRX - pl_dx(q)], gs);
             const float gn = fmaf(a.gscale, gs, g_old);
-            g[i] = gn;
+            // the solver needs x_{k+1} = z_k - step grad, not grad itself
+            g[i] = DOTS ? fmaf(-a.step, gn, fm) : gn;
             if (WANT_H) h8 += hs;
             if (DOTS) {
                 a8 = fmaf(gn, fm - x_old, a8);
@@ -502,6 +505,7 @@ PriorArgs make_prior_args(int n, int nb, const tc_prior *pr) {
     a.lk = (float)((2.0 - pr->p) * std::log2(1.0 / pr->sigma));
     a.two_c = (float)(2.0 * pr->c);
     a.gscale = (float)(2.0 * pr->lambda / (pr->sigma * pr->sigma));
+    a.step = 0.f;
     // w_mn proportional to 1/distance, normalised over the full neighbourhood
     double z;
     if (pr->dims == 3) z = 6.0 + 12.0 / sqrt(2.0) + 8.0 / sqrt(3.0);
@@ -522,8 +526,9 @@ int prior_tile_count(int n) { return ((n + PTX - 1) / PTX) * ((n + PTY - 1) / PT
 
 int launch_prior_grad(tc_plan *p, const float *x, float *g, int nb,
                       const tc_prior *pr, double *h_acc, cudaStream_t s, const float *dot_x,
-                      int z0, int z1) {
+                      int z0, int z1, double step) {
     PriorArgs a = make_prior_args(p->k.N, nb, pr);
+    a.step = (float)step;
     if (z1 < 0) z1 = nb;
     if (z0 < 0 || z0 >= z1 || z1 > nb) return TC_ERR_INVALID_ARG;
     a.z0 = z0;
