@@ -235,6 +235,22 @@ const char *tc_profile_kernel_name(int id);
 /* Kernel launches issued by this library since it was loaded (host counter). */
 long long tc_launch_count(void);
 
+/* ------------------------------------------------------ device status --- */
+/* Kernels that wait on a device barrier (the TMA-staged forward column pass)
+ * bound each wait to one second; on expiry they record TC_ERR_TIMEOUT in the
+ * plan's device status and return early, leaving their outputs incomplete.
+ * mbir_solve, mbir_solve_host and mbir_power_norm (which synchronise)
+ * report that status when they return; after radon_fwd, radon_adj or
+ * mbir_grad (asynchronous), tc_plan_status synchronises the device, returns
+ * the status (TC_OK or TC_ERR_TIMEOUT) and clears it. */
+int tc_plan_status(tc_plan *plan);
+
+/* Self-test of the bounded wait: one kernel waits on a barrier that never
+ * completes, with a 2 ms limit.  Returns TC_ERR_TIMEOUT when the wait
+ * expired and the kernel returned as designed (the context stays usable);
+ * synchronises the given stream. */
+int tc_selftest_wait_timeout(void *stream);
+
 /* ------------------------------------------------------ no allocation --- */
 /* Prior gradient and value without any device allocation.  There is no
  * counterpart of this entry point in the paper; it exists for callers that

@@ -55,7 +55,8 @@ SYMBOLS = ("tc_status_string", "tc_last_error_detail", "tc_plan_create", "tc_pla
            "tc_plan_device_bytes", "radon_fwd", "radon_adj", "mbir_grad",
            "mbir_power_norm", "mbir_solve", "mbir_solve_host", "tc_profile_enable",
            "tc_profile_collect", "tc_profile_kernel_name", "tc_launch_count",
-           "tc_plan_autotune", "tc_plan_set_launch", "tc_prior_grad_noalloc")
+           "tc_plan_autotune", "tc_plan_set_launch", "tc_prior_grad_noalloc",
+           "tc_plan_status", "tc_selftest_wait_timeout")
 
 
 def lib_path() -> str:
@@ -100,6 +101,8 @@ def load(build_if_missing: bool = True):
     L.tc_plan_autotune.argtypes = [vp, vp, vp, i, i, ctypes.POINTER(i), ctypes.POINTER(i), vp]
     L.tc_plan_set_launch.argtypes = [vp, i, i]
     L.tc_prior_grad_noalloc.argtypes = [vp, vp, i, i, ctypes.POINTER(_Prior), vp, vp]
+    L.tc_plan_status.argtypes = [vp]
+    L.tc_selftest_wait_timeout.argtypes = [vp]
     for fn in ("tc_profile_enable", "tc_profile_collect", "tc_plan_create", "tc_plan_destroy",
                "radon_fwd", "radon_adj", "mbir_grad", "mbir_power_norm", "mbir_solve",
                "mbir_solve_host", "tc_plan_autotune", "tc_plan_set_launch",

@@ -95,6 +95,16 @@ int value_impl(tc_plan *p, const float *x, const float *b, const float *w, const
     return TC_OK;
 }
 
+// The plan's device status (bounded waits) after the stream has drained;
+// a recorded timeout is returned once and cleared.
+int take_dev_status(tc_plan *p, cudaStream_t s) {
+    int st = TC_OK;
+    TC_CUDA(cudaMemcpyAsync(&st, p->dev_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    TC_CUDA(cudaStreamSynchronize(s));
+    if (st != TC_OK) TC_CUDA(cudaMemsetAsync(p->dev_err, 0, sizeof(int), s));
+    return st;
+}
+
 int check_prior(const tc_prior *pr) {
     if (!pr) return TC_OK;
     if (!(pr->dims == 2 || pr->dims == 3) || !(pr->sigma > 0) || !(pr->c > 0) ||
@@ -223,7 +233,15 @@ int mbir_power_norm(tc_plan *p, const float *w, float *v, float *work, int batch
     TC_CUDA(cudaMemcpyAsync(&lam, p->scal + SC_DOT_GZX, sizeof(double), cudaMemcpyDeviceToHost, s));
     TC_CUDA(cudaStreamSynchronize(s));
     *lam_out = lam;
-    return TC_OK;
+    return take_dev_status(p, s);
+}
+
+int tc_plan_status(tc_plan *p) {
+    if (!p) return TC_ERR_INVALID_ARG;
+    DeviceGuard dg(p->device);
+    if (!dg.ok) return TC_ERR_CUDA;
+    TC_CUDA(cudaDeviceSynchronize());
+    return take_dev_status(p, nullptr);
 }
 
 }  // extern "C"
@@ -345,6 +363,7 @@ int solve_loop(tc_plan *p, const float *b, const float *w, float *x, int batch,
         st->obj[0] = sc[SC_DATA];
         st->obj[1] = (prior && prior->lambda != 0.0) ? sc[SC_PRIOR] : 0.0;
     }
+    if ((rc = take_dev_status(p, s))) return rc;
     return TC_OK;
 }
 

@@ -75,12 +75,20 @@ struct tc_plan {
     double *partials;     // TC_N_SLOTS slots of `slot` per-block FP64 partial sums
     int slot;
     double *scal;         // device scalars of the solver
+    int *dev_err;         // device status of bounded waits (TC_OK or TC_ERR_TIMEOUT)
     long long bytes;
     // launch configuration
     int cp_col;           // column pairs per CTA in the column passes
     int threads_col, threads_row, threads_det;
     size_t smem_col, smem_row_fwd, smem_row_adj, smem_det;
+    size_t smem_col_tma;  // forward column pass with its image strip staged by TMA (0: not used)
 };
+
+// Extra shared memory of the TMA forward column pass: 128 bytes of alignment
+// slack, the image strip (N rows x 2 cp floats) and its mbarrier.
+__host__ __device__ constexpr size_t col_strip_bytes(int n, int cp) {
+    return 128 + (size_t)n * 2 * cp * sizeof(float) + 16;
+}
 
 // One (polar point, tap row) entry of a grid row's bin, 16 bytes:
 //   x: polar point index p = a * Mh + m

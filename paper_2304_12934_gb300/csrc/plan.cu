@@ -197,13 +197,16 @@ int plan_set_col_pairs(tc_plan *p, int cp) {
     p->cp_col = cp;
     p->threads_col = std::max(64, 2 * cp * N / 16);
     p->smem_col = smem;
+    // TMA staging of the image strip needs rows of >= 16 bytes (cp >= 2)
+    p->smem_col_tma = cp >= 2 ? smem + col_strip_bytes(N, cp) : 0;
+    if (p->smem_col_tma > 200 * 1024) p->smem_col_tma = 0;
     return TC_OK;
 }
 
 void tc_plan_free(tc_plan *p) {
     if (!p) return;
     void *ptrs[] = {p->dea64, p->dea, p->twN, p->twG, p->twD, p->row_off, p->ent, p->rec, p->rec_off,
-                    p->tu, p->pv, p->sr, p->partials, p->scal, p->angle_flip, p->shiftD,
+                    p->tu, p->pv, p->sr, p->partials, p->scal, p->dev_err, p->angle_flip, p->shiftD,
                     p->chirp, p->bhat, p->twL};
     for (void *q : ptrs)
         if (q) cudaFree(q);
@@ -530,11 +533,13 @@ int tc_plan_build(const tc_geom *geom, int max_batch, tc_plan **out) {
         (rc = alloc_dev((void **)&p->pv, MB * w * (size_t)k.AM * sizeof(float2), bytes)) ||
         (rc = alloc_dev((void **)&p->sr, MB * (size_t)A * D * sizeof(float), bytes)) ||
         (rc = alloc_dev((void **)&p->partials, (size_t)TC_N_SLOTS * p->slot * sizeof(double), bytes)) ||
-        (rc = alloc_dev((void **)&p->scal, SC_COUNT * sizeof(double), bytes))) {
+        (rc = alloc_dev((void **)&p->scal, SC_COUNT * sizeof(double), bytes)) ||
+        (rc = alloc_dev((void **)&p->dev_err, sizeof(int), bytes))) {
         tc_plan_free(p);
         return rc;
     }
     TC_CUDA(cudaMemset(p->scal, 0, SC_COUNT * sizeof(double)));
+    TC_CUDA(cudaMemset(p->dev_err, 0, sizeof(int)));
     p->bytes = bytes;
     if ((rc = radon_configure_kernels(p)) || (rc = prior_configure_kernels())) {
         tc_plan_free(p);

@@ -20,11 +20,13 @@
 //              inverse FFT_G along x evaluated at the N image columns
 //   col pass   Hermitian completion, inverse FFT_G along y at the N image
 //              rows for two columns at once, real part, deapodise
+#include <cstring>
 #include <type_traits>
 
 #include "common.cuh"
 #include "profile.cuh"
 #include "fft.cuh"
+#include "tma.cuh"
 
 namespace {
 
@@ -37,21 +39,43 @@ __host__ __device__ constexpr int cell_slot(int t0, int ts, int c) {
 // ------------------------------------------------------------ forward ------
 // The pass kernels take the image side as a template parameter (N = 2^LOGN),
 // so their FFTs and shared-memory layouts are fixed at compile time.
-template <int LOGN>
+// TMA: the CTA's strip of 2CP image columns (N rows x 16 or 32 bytes, the
+// partial-sector reads that bound the L1 path) is staged in shared memory by
+// bulk tensor copies, outside the LSU/L1 pipeline (CP >= 2).
+template <int LOGN, bool TMA>
 __global__ void __launch_bounds__(512) k_fwd_col(const float *__restrict__ x, float2 *__restrict__ T,
-                          const KArgs g, int CP) {
-    extern __shared__ float2 sm[];  // 2CP transforms (stride ts)
+                          const KArgs g, int CP, const __grid_constant__ CUtensorMap tmx,
+                          int *__restrict__ err) {
+    extern __shared__ float2 sm[];  // 2CP transforms (stride ts) [, strip, barrier]
     constexpr int N = 1 << LOGN, ts = fft_tstride(N);
     const int b = blockIdx.y;
     const int x0base = blockIdx.x * CP * 2;
-    const float *xs = x + (size_t)b * N * N;
+    const float *src = x + (size_t)b * N * N + x0base;  // row iy of the strip at src + iy * pitch
+    int pitch = N;
+    if constexpr (TMA) {
+        const unsigned base = smem_u32(sm + 2 * CP * ts);
+        float *strip = reinterpret_cast<float *>(reinterpret_cast<char *>(sm + 2 * CP * ts) +
+                                                 (((base + 127u) & ~127u) - base));
+        uint64_t *bar = reinterpret_cast<uint64_t *>(strip + N * 2 * CP);
+        constexpr int BR = N < 256 ? N : 256;  // rows per box (a box side is at most 256)
+        if (threadIdx.x == 0) {
+            mbar_init(bar, 1);
+            mbar_expect_tx(bar, (unsigned)(N * 2 * CP * sizeof(float)));
+            for (int r = 0; r < N; r += BR) tma_load_3d(strip + r * 2 * CP, &tmx, bar, x0base, r, b);
+        }
+        __syncthreads();
+        const bool late = !mbar_wait(bar, 0, err);
+        if (__syncthreads_or(late)) return;  // all threads leave together
+        src = strip;
+        pitch = 2 * CP;
+    }
     // blockDim.x is a multiple of CP, so a thread keeps its column pair
     const int pp0 = threadIdx.x % CP, xc0 = x0base + 2 * pp0;
     const float dx0 = g.dea[xc0], dx1 = g.dea[xc0 + 1];
 #pragma unroll 8
     for (int idx = threadIdx.x; idx < N * CP; idx += blockDim.x) {
         const int pp = pp0, iy = idx / CP;
-        const float2 f = *reinterpret_cast<const float2 *>(xs + (size_t)iy * N + xc0);
+        const float2 f = *reinterpret_cast<const float2 *>(src + (size_t)iy * pitch + 2 * pp0);
         const float dy = g.dea[iy];
         const float2 z = make_float2(f.x * dx0 * dy, f.y * dx1 * dy);
         const int q = (iy - N / 2) & (N - 1);
@@ -62,9 +86,8 @@ __global__ void __launch_bounds__(512) k_fwd_col(const float *__restrict__ x, fl
     fft_ct<-1, LOGN>(sm, 2 * CP, g.twN);
     float2 *Tb = T + (size_t)b * g.R * N;
     constexpr int Gm = 2 * N - 1;
-#pragma unroll 4
-    for (int idx = threadIdx.x; idx < g.R * CP; idx += blockDim.x) {
-        const int pp = idx % CP, r = idx / CP;
+    // the two real columns of pair pp in grid row r, packed as in T
+    auto row_out = [&](int pp, int r) {
         const int jy = g.jmin + r;
         const float2 zp = sm[cell_slot(pp * 2, ts, jy & Gm)];
         const float2 zm = cconj(sm[cell_slot(pp * 2, ts, (-jy) & Gm)]);
@@ -74,7 +97,12 @@ __global__ void __launch_bounds__(512) k_fwd_col(const float *__restrict__ x, fl
         o.y = 0.5f * (zp.y + zm.y);
         o.z = 0.5f * d.y;   // (zp - zm) / (2i)
         o.w = -0.5f * d.x;
-        *reinterpret_cast<float4 *>(Tb + (size_t)r * N + x0base + 2 * pp) = o;
+        return o;
+    };
+#pragma unroll 4
+    for (int idx = threadIdx.x; idx < g.R * CP; idx += blockDim.x) {
+        const int pp = idx % CP, r = idx / CP;
+        *reinterpret_cast<float4 *>(Tb + (size_t)r * N + x0base + 2 * pp) = row_out(pp, r);
     }
 }
 
@@ -401,9 +429,19 @@ int launch_radon_fwd_chunk(tc_plan *p, const float *x, float *y, int nb,
     const KArgs &g = p->k;
     dim3 gc(g.N / (2 * p->cp_col), nb);
     dim3 gr(g.R, nb);
+    // the image strips by TMA when the plan allows it and the map encodes
+    CUtensorMap tmx;
+    std::memset(&tmx, 0, sizeof(tmx));
+    const bool use_tma = p->smem_col_tma > 0 &&
+                         tma_encode_f32_3d(&tmx, x, g.N, g.N, nb, 2 * p->cp_col, g.N < 256 ? g.N : 256) == TC_OK;
     int rc = with_logn(g.log2N, [&](auto L) {
         constexpr int LG = decltype(L)::value;
-        TC_PROFILED(TCK_FWD_COL, s, k_fwd_col<LG><<<gc, p->threads_col, p->smem_col, s>>>(x, p->tu, g, p->cp_col));
+        if (use_tma)
+            TC_PROFILED(TCK_FWD_COL, s, k_fwd_col<LG, true><<<gc, p->threads_col, p->smem_col_tma, s>>>(
+                                            x, p->tu, g, p->cp_col, tmx, p->dev_err));
+        else
+            TC_PROFILED(TCK_FWD_COL, s, k_fwd_col<LG, false><<<gc, p->threads_col, p->smem_col, s>>>(
+                                            x, p->tu, g, p->cp_col, tmx, p->dev_err));
         TC_LAUNCHED("k_fwd_col");
         TC_PROFILED(TCK_FWD_ROW, s, k_fwd_row<LG><<<gr, p->threads_row, p->smem_row_fwd, s>>>(p->tu, p->pv, g));
         TC_LAUNCHED("k_fwd_row");
@@ -467,15 +505,18 @@ int raise_smem_limit(F *fn, size_t bytes) {
 
 int radon_configure_kernels(tc_plan *p) {
     // the column passes may be retuned to up to 4 column pairs per CTA
-    size_t col_max = p->smem_col;
+    size_t col_max = p->smem_col, tma_max = p->smem_col_tma;
     for (int cp = 1; cp <= 4; cp <<= 1) {
         const size_t sm = (size_t)(2 * cp * fft_tstride(p->k.N)) * 8;
         if (sm <= 200 * 1024 && sm > col_max) col_max = sm;
+        const size_t st = sm + col_strip_bytes(p->k.N, cp);
+        if (cp >= 2 && st <= 200 * 1024 && st > tma_max) tma_max = st;
     }
     int rc = with_logn(p->k.log2N, [&](auto L) {
         constexpr int LG = decltype(L)::value;
         int e;
-        if ((e = raise_smem_limit(k_fwd_col<LG>, col_max)) || (e = raise_smem_limit(k_adj_col<LG>, col_max)) ||
+        if ((e = raise_smem_limit(k_fwd_col<LG, false>, col_max)) || (e = raise_smem_limit(k_adj_col<LG>, col_max)) ||
+            (p->smem_col_tma && (e = raise_smem_limit(k_fwd_col<LG, true>, tma_max))) ||
             (e = raise_smem_limit(k_fwd_row<LG>, p->smem_row_fwd)) ||
             (e = raise_smem_limit(k_adj_row<LG>, p->smem_row_adj)))
             return e;

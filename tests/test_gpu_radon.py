@@ -203,3 +203,37 @@ def test_rotation_axis_offset_matches_oracle(api, N, A, D, delta, kind):
 def test_rotation_axis_offset_out_of_range_is_rejected(api, delta):
     with pytest.raises(api.TcError):
         api.Plan(32, 8, 92, center_offset=delta)
+
+
+@pytest.mark.parametrize("N,A,D", [(2048, 128, 2896), (128, 90, 184), (16, 7, 24)])
+def test_tma_staged_column_pass_equals_plain_loads(api, N, A, D):
+    """With two or more column pairs per CTA the forward column pass stages
+    its image strip by TMA; with one it reads global memory directly.  The
+    arithmetic is the same, so the outputs agree bit for bit."""
+    rng = np.random.default_rng(N + 1)
+    x = t32(rng.standard_normal((2, N, N)))
+    with api.Plan(N, A, D, max_batch=2) as plan:
+        plan.set_launch(2, 2)
+        y_tma = api.radon_fwd(plan, x).clone()
+        plan.set_launch(2, 1)
+        y_plain = api.radon_fwd(plan, x).clone()
+        assert load_status(api, plan) == 0
+    assert torch.equal(y_tma, y_plain)
+
+
+def load_status(api, plan):
+    return api.load().tc_plan_status(plan.handle)
+
+
+def test_bounded_wait_times_out_and_the_context_stays_usable(api):
+    """A barrier that never completes: the bounded wait expires (2 ms), the
+    kernel records TC_ERR_TIMEOUT and returns; later work runs normally."""
+    L = api.load()
+    assert L.tc_selftest_wait_timeout(None) == -4
+    N, A, D = 64, 33, 92
+    f = synth.rasterize(N, synth.random_ellipses(N, synth.BASE_SEED + 7))[None]
+    with api.Plan(N, A, D) as plan:
+        y = api.radon_fwd(plan, t32(f)).double().cpu().numpy()
+        assert L.tc_plan_status(plan.handle) == 0
+    yo = oracle.radon_fwd(f.astype(np.float32).astype(np.float64), A, D)
+    assert rel(y, yo) <= REL_TOL
