@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--plain-slices", type=int, default=32)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--uneven-slices", type=int, default=512,
+                    help="slices of the uneven-size batching measurement (0 skips it)")
     ap.add_argument("--cpu-angles", type=int, default=16,
                     help="angles of one slice timed by the oracle for the CPU baseline")
     ap.add_argument("--workload", default=None,
@@ -248,6 +250,70 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------- uneven-size batching ---
+def uneven_batch(api, synth, dev, n_slices, reps=3):
+    """Gradient evaluations (A, A^T, 8-neighbour prior) of n_slices slices of
+    uneven side (256..2048) and angle count (64..256), seeded: per geometry
+    one plan over all its slices, the whole batch captured in one CUDA graph;
+    against the plain form, one slice per launch through plans of one slice."""
+    import numpy as np
+    import torch
+    rng = np.random.default_rng(synth.BASE_SEED + 3)
+    sides = rng.choice([256, 512, 1024, 2048], n_slices)
+    angs = rng.choice([64, 128, 256], n_slices)
+    groups = sorted(set(zip(sides.tolist(), angs.tolist())))
+    prior = api.Prior(lam=1e-2, dims=2)
+    bufs = []
+    for n, a in groups:
+        cnt = int(np.sum((sides == n) & (angs == a)))
+        d = synth.det_for(n)
+        g = torch.Generator(device=dev)
+        g.manual_seed(n * 1000 + a)
+        x = torch.rand((cnt, n, n), device=dev, generator=g)
+        b = torch.rand((cnt, a, d), device=dev, generator=g)
+        w = torch.rand((cnt, a, d), device=dev, generator=g)
+        bufs.append(dict(n=n, a=a, d=d, cnt=cnt, x=x, b=b, w=w, grad=torch.empty_like(x),
+                         obj=torch.zeros(2, dtype=torch.float64, device=dev),
+                         pb=api.Plan(n, a, d, max_batch=min(cnt, 64), device=dev),
+                         p1=api.Plan(n, a, d, max_batch=1, device=dev)))
+
+    def batched():
+        for q in bufs:
+            api.mbir_grad(q["pb"], q["x"], q["b"], q["w"], prior, grad=q["grad"], obj=q["obj"])
+
+    def plain():
+        for q in bufs:
+            for k in range(q["cnt"]):
+                api.mbir_grad(q["p1"], q["x"][k:k + 1], q["b"][k:k + 1], q["w"][k:k + 1], prior,
+                              grad=q["grad"][k:k + 1], obj=q["obj"])
+
+    stream = torch.cuda.current_stream(dev)
+    batched()
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        batched()
+    res = {}
+    for name, fn in (("graph", graph.replay), ("plain", plain)):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        res[name] = n_slices * reps / (e0.elapsed_time(e1) / 1e3)
+    for q in bufs:
+        q["pb"].close()
+        q["p1"].close()
+    return {"metric": "slice-gradients/s (A, A^T, 8-neighbour prior)", "slices": n_slices,
+            "geometries": len(groups), "graph_batched": round(res["graph"], 1),
+            "plain_one_slice_per_launch": round(res["plain"], 1),
+            "speedup": round(res["graph"] / res["plain"], 3),
+            "sizes": "sides {256,512,1024,2048}, angles {64,128,256}, D = 2 round(N/sqrt 2), seeded"}
+
+
 # ------------------------------------------------------------- CUDA path ---
 def run_ours(args):
     import numpy as np
@@ -369,6 +435,11 @@ def run_ours(args):
                "d2h_bytes_per_step": int(xh.numel() * 4),
                "call": "mbir_solve_host(n_iter=1) per step: H2D b, w, x; one iteration; D2H x"}
 
+    # ---- uneven sizes: one CUDA graph over per-geometry batches vs one slice per launch
+    uneven = None
+    if rank == 0 and args.uneven_slices > 0:
+        uneven = uneven_batch(api, synth, dev, args.uneven_slices)
+
     # ---- CPU oracle baseline (rank 0, N = 1)
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
@@ -394,6 +465,7 @@ def run_ours(args):
                            "parallelism": f"replicas x{ws}"},
                 "roofline": roofline, "kernels": kernels, "batched_vs_plain": plain,
                 "e2e": e2e, "cpu_baseline": cpu, "gpu_launches": int(gpu_launches),
+                "uneven_batch": uneven,
                 "clocks": clk.summary(), "solver": {"step": step, "restarts": st.n_restarts,
                                                     "obj": list(st.obj)}}
         print(json.dumps(line), flush=True)
