@@ -52,7 +52,12 @@ const char *tc_last_error_detail(void);
 /* Scan geometry of one family of slices (Sec. 2.1; Sec. 2.2 for sigma and w).
  *   n             image side N; power of two, 16 <= N <= 4096
  *   n_angles      A >= 1
- *   n_det         D; even, 4 <= D <= 16384
+ *   n_det         D; even, 4 <= D <= 16384.  tc_plan_create returns
+ *                 TC_ERR_UNSUPPORTED when the detector DFT of one CTA would
+ *                 exceed 200 KB of shared memory: lengths with a prime
+ *                 factor > 32 use Bluestein with L = 2^k >= 2D - 1 (up to
+ *                 L = 8192, i.e. D <= 4096), other lengths (and longer ones)
+ *                 a mixed-radix DFT needing about 24 D bytes (D <~ 8500)
  *   angles        HOST pointer to A angles in radians, or NULL for a*pi/A;
  *                 copied during tc_plan_create
  *   oversample    sigma, the grid oversampling factor; must be 2

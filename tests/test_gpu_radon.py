@@ -237,3 +237,29 @@ def test_bounded_wait_times_out_and_the_context_stays_usable(api):
         assert L.tc_plan_status(plan.handle) == 0
     yo = oracle.radon_fwd(f.astype(np.float32).astype(np.float64), A, D)
     assert rel(y, yo) <= REL_TOL
+
+
+def test_largest_image_side(api):
+    """N = 4096 (the largest side): one column pair per CTA (plain loads) and
+    a detector DFT of 5792 = 32 * 181 bins (mixed radix with the radix 181);
+    sampled outputs against the oracle's closed form."""
+    N, A, D = 4096, 24, 5792
+    f = synth.rasterize(N, synth.random_ellipses(N, synth.BASE_SEED + 11)).astype(np.float32)[None]
+    rng = np.random.default_rng(4096)
+    yy = rng.standard_normal((1, A, D)).astype(np.float32)
+    with api.Plan(N, A, D) as plan:
+        y = api.radon_fwd(plan, t32(f)).double().cpu().numpy()[0]
+        x = api.radon_adj(plan, t32(yy)).double().cpu().numpy()[0]
+    ai = rng.integers(0, A, 12)
+    ii = rng.integers(D // 4, 3 * D // 4, 12)
+    ys = oracle.radon_fwd_at(f[0].astype(np.float64), A, D, ai, ii)
+    assert np.abs(y[ai, ii] - ys).max() <= REL_TOL * 2 * float(np.sqrt(np.mean(y ** 2)))
+    pix = rng.integers(0, N * N, 12)
+    xs = oracle.radon_adj_at(yy[0].astype(np.float64), N, pix)
+    assert np.abs(x.ravel()[pix] - xs).max() <= REL_TOL * 2 * float(np.sqrt(np.mean(x ** 2)))
+
+
+def test_detector_beyond_the_shared_memory_limit_is_unsupported(api):
+    with pytest.raises(api.TcError) as e:
+        api.Plan(64, 8, 16384)   # mixed radix would need 393 KB of shared memory
+    assert e.value.code == -5
