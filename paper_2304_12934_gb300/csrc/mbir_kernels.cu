@@ -6,6 +6,7 @@
 // per thread before promoting to FP64, then sums per-block FP64 partials in a
 // fixed order, so results are bit-reproducible run to run.
 #include <cmath>
+#include <type_traits>
 
 #include "common.cuh"
 #include "profile.cuh"
@@ -214,9 +215,12 @@ __global__ void __launch_bounds__(PRIOR_THREADS, PRIOR_MIN_BLOCKS) k_prior(const
     // per-thread sums: FP32 over 8, 64 and 512 z steps (a level never adds
     // more than 8 terms for volumes up to 4096 slices), FP64 from the block sum on
     float h8 = 0.f, h64 = 0.f, h512 = 0.f, a8 = 0.f, a64 = 0.f, a512 = 0.f, b8 = 0.f, b64 = 0.f, b512 = 0.f;
-    int s3 = 0, p3 = PRIOR_UP_SLOTS - 1;  // this step's / previous step's z+1 slot
-    for (int z = zs; z < a.z1; ++z) {
-        const int cur = (z - zs) & 1, nxt = cur ^ 1;
+    static_assert(PRIOR_UP_SLOTS == 2 && PRIOR_PL_SLOTS == 1, "buffer slots alternate with the z parity");
+    // One z step; PAR = (z - zs) & 1 fixes every buffer (planes, z+1 pair
+    // slots) at compile time, so the march runs two steps per iteration.
+    auto step = [&](auto par, int z) {
+        constexpr int cur = decltype(par)::value, nxt = cur ^ 1;
+        constexpr int s3 = cur, p3 = nxt;  // this step's / previous step's z+1 slot
         const bool own = z >= a.z0;
         const bool up = three && z + 1 < B;
         const int pz = three ? z + 2 : z + 1;
@@ -236,7 +240,7 @@ __global__ void __launch_bounds__(PRIOR_THREADS, PRIOR_MIN_BLOCKS) k_prior(const
             const float *fc = fpl + cur * PRS + h;
             fm = *fc;
             float *eu = Eu + (s3 * 9) * PRS + h;
-            float *ep = Ep + ((z % PRIOR_PL_SLOTS) * 4) * PRS + h;
+            float *ep = Ep + h;
             const float *fn = fpl + nxt * PRS + h;
             if (GRAD && three && !up) {
 #pragma unroll
@@ -272,7 +276,7 @@ __global__ void __launch_bounds__(PRIOR_THREADS, PRIOR_MIN_BLOCKS) k_prior(const
                     gs = fmaf(-wu, epv[u * PRS - dy * PRX - dx], gs);
                 }
             }
-            const float *ep = Ep + ((z % PRIOR_PL_SLOTS) * 4) * PRS + h;
+            const float *ep = Ep + h;
 #pragma unroll
             for (int q = 0; q < 4; ++q)
                 gs = fmaf((q & 1) ? -a.w2 : -a.w1, ep[q * PRS - pl_dy(q) * PRX - pl_dx(q)], gs);
@@ -294,9 +298,13 @@ __global__ void __launch_bounds__(PRIOR_THREADS, PRIOR_MIN_BLOCKS) k_prior(const
             }
         }
         f_nx = f_pf;
-        p3 = s3;
-        s3 = s3 == PRIOR_UP_SLOTS - 1 ? 0 : s3 + 1;
+    };
+    int z = zs;
+    for (; z + 1 < a.z1; z += 2) {
+        step(std::integral_constant<int, 0>{}, z);
+        step(std::integral_constant<int, 1>{}, z + 1);
     }
+    if (z < a.z1) step(std::integral_constant<int, 0>{}, z);
     const int bid = blockIdx.y * gridDim.x + blockIdx.x;
     if (WANT_H) {
         const double tot = block_sum_f64((double)h512 + ((double)h64 + (double)h8), red);
