@@ -263,7 +263,8 @@ struct HostOut {
 // reads a one-slice halo) are done; its copy to the host then overlaps the
 // remaining chunks.  The restart test and z_{k+1} follow at the end.  The
 // result equals the in-place update bit for bit.
-int last_iteration_streamed(tc_plan *p, const float *b, const float *w, float *x, int batch,
+// x holds x_k and gb is the gradient buffer; on return x holds x_{k+1}.
+int last_iteration_streamed(tc_plan *p, const float *b, const float *w, float *x, float *gb, int batch,
                             const tc_prior *prior, const tc_solve_opts *opts, tc_solve_state *st,
                             cudaStream_t s, const cudaEvent_t *ready, const HostOut &out) {
     TC_CUDA(cudaMemsetAsync(p->scal + SC_DATA, 0, 2 * sizeof(double), s));
@@ -271,8 +272,8 @@ int last_iteration_streamed(tc_plan *p, const float *b, const float *w, float *x
     const int nslab = (batch + p->chunk - 1) / p->chunk;
     auto finish = [&](int j) -> int {
         const int z0 = j * p->chunk, z1 = z0 + p->chunk < batch ? z0 + p->chunk : batch;
-        // the prior kernel leaves x_{k+1} = z - step g of the slab in g
-        int rc = launch_prior_grad(p, st->z, st->g, batch, prior, p->scal + SC_PRIOR, s, x, z0, z1,
+        // the prior kernel leaves x_{k+1} = z - step g of the slab in gb
+        int rc = launch_prior_grad(p, st->z, gb, batch, prior, p->scal + SC_PRIOR, s, x, z0, z1,
                                    opts->step);
         if (rc) return rc;
         cudaEvent_t e = nullptr;
@@ -280,7 +281,7 @@ int last_iteration_streamed(tc_plan *p, const float *b, const float *w, float *x
         out.ev->push_back(e);
         TC_CUDA(cudaEventRecord(e, s));
         TC_CUDA(cudaStreamWaitEvent(out.cs, e, 0));
-        TC_CUDA(cudaMemcpyAsync(out.x_host + z0 * ni, st->g + z0 * ni, (size_t)(z1 - z0) * ni * sizeof(float),
+        TC_CUDA(cudaMemcpyAsync(out.x_host + z0 * ni, gb + z0 * ni, (size_t)(z1 - z0) * ni * sizeof(float),
                                 cudaMemcpyDeviceToHost, out.cs));
         return TC_OK;
     };
@@ -289,13 +290,13 @@ int last_iteration_streamed(tc_plan *p, const float *b, const float *w, float *x
         if (ready) TC_CUDA(cudaStreamWaitEvent(s, ready[c], 0));
         int rc = launch_radon_fwd_chunk(p, st->z + c0 * ni, nullptr, nb, b + c0 * ns,
                                         w ? w + c0 * ns : nullptr, p->sr, p->scal + SC_DATA, s);
-        if (!rc) rc = launch_radon_adj_chunk(p, p->sr, st->g + c0 * ni, nb, s);
+        if (!rc) rc = launch_radon_adj_chunk(p, p->sr, gb + c0 * ni, nb, s);
         if (!rc && c > 0) rc = finish(c - 1);  // slab c holds the upper halo of slab c - 1
         if (rc) return rc;
     }
     int rc = finish(nslab - 1);
     if (!rc) rc = launch_solver_scalar(p, opts->restart, s);
-    if (!rc) rc = launch_update_monotone(p, x, st->z, st->g, img_elems(p) * batch, s, 1);
+    if (!rc) rc = launch_update_monotone(p, x, st->z, gb, img_elems(p) * batch, s, 1);
     return rc;
 }
 
@@ -330,26 +331,36 @@ int solve_loop(tc_plan *p, const float *b, const float *w, float *x, int batch,
             if ((rc = launch_update_monotone(p, x, st->z, st->g, n, s))) return rc;
         }
     }
+    // With a prior the iterate alternates between x and the scratch buffer
+    // g: the prior kernel writes x_{k+1} into the buffer not holding x_k, and
+    // the update then only writes z.  It returns to x at the end of the call.
+    float *xa = x, *xb = st->g;  // xa: x_k; xb: gradient / next iterate
     for (int it = 0; it < (opts->restart == 2 ? 0 : opts->n_iter); ++it) {
         // the prior's value H is only reported for the last gradient point
         const bool fused = prior && prior->lambda != 0.0;  // dots inside the prior kernel
         if (out && fused && it == opts->n_iter - 1) {
-            if ((rc = last_iteration_streamed(p, b, w, x, batch, prior, opts, st, s,
+            if ((rc = last_iteration_streamed(p, b, w, xa, xb, batch, prior, opts, st, s,
                                               it == 0 ? ready : nullptr, *out)))
                 return rc;
             continue;
         }
         // fused: the prior kernel also forms the restart dots and leaves
-        // x_{k+1} = z_k - step g in g; otherwise separate dots and update
-        if ((rc = grad_impl(p, st->z, b, w, prior, st->g, batch, s, it == opts->n_iter - 1,
-                            it == 0 ? ready : nullptr, fused ? x : nullptr, opts->step)))
+        // x_{k+1} = z_k - step g in xb; otherwise separate dots and update
+        if ((rc = grad_impl(p, st->z, b, w, prior, xb, batch, s, it == opts->n_iter - 1,
+                            it == 0 ? ready : nullptr, fused ? xa : nullptr, opts->step)))
             return rc;
-        if (!fused && (rc = launch_dots_gzx_gg(p, st->g, st->z, x, n, s))) return rc;
+        if (!fused && (rc = launch_dots_gzx_gg(p, xb, st->z, xa, n, s))) return rc;
         if ((rc = launch_solver_scalar(p, opts->restart, s))) return rc;
-        if (fused) rc = launch_update_monotone(p, x, st->z, st->g, n, s, 1);
-        else rc = launch_update(p, x, st->z, st->g, n, s);
-        if (rc) return rc;
+        if (fused) {
+            if ((rc = launch_update_monotone(p, xa, st->z, xb, n, s, 1, 1))) return rc;  // z only
+            float *t = xa;
+            xa = xb;
+            xb = t;
+        } else if ((rc = launch_update(p, xa, st->z, xb, n, s))) {
+            return rc;
+        }
     }
+    if (xa != x && (rc = launch_copy(x, xa, n, s))) return rc;
     double sc[SC_COUNT];
     TC_CUDA(cudaMemcpyAsync(sc, p->scal, sizeof(sc), cudaMemcpyDeviceToHost, s));
     TC_CUDA(cudaStreamSynchronize(s));

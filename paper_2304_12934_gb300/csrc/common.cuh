@@ -205,7 +205,7 @@ int launch_prior_value(tc_plan *p, const float *x, int nb, const tc_prior *pr,
 int launch_step_to_candidate(tc_plan *p, const float *z, float *g, size_t n, cudaStream_t s);
 int launch_monotone_scalar(tc_plan *p, int init, cudaStream_t s);
 int launch_update_monotone(tc_plan *p, float *x, float *z, const float *v, size_t n,
-                           cudaStream_t s, int accept_all = 0);
+                           cudaStream_t s, int accept_all = 0, int keep_x = 0);
 int launch_reduce_finalize(const double *partials, int n, double *acc,
                            int accumulate, double scale, cudaStream_t s);
 int launch_dots_gzx_gg(tc_plan *p, const float *g, const float *z, const float *x,

@@ -450,10 +450,11 @@ __global__ void k_monotone_scalar(double *sc, int init) {
 }
 
 // accept_all: v is x_{k+1} (the gradient-restart schedule, with x_{k+1}
-// formed ahead of the restart decision).
+// formed ahead of the restart decision); with keep_x as well, x_{k+1} stays
+// where v is and only z is written.
 __global__ void k_update_monotone(float4 *__restrict__ x, float4 *__restrict__ z,
                                   const float4 *__restrict__ v, size_t n4, const double *__restrict__ sc,
-                                  int accept_all) {
+                                  int accept_all, int keep_x) {
     const bool accept = accept_all || sc[SC_ACCEPT] != 0.0;
     const float beta = (float)sc[SC_BETA];
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4;
@@ -469,7 +470,7 @@ __global__ void k_update_monotone(float4 *__restrict__ x, float4 *__restrict__ z
         zn.y = fmaf(beta, xn.y - xv.y, xn.y);
         zn.z = fmaf(beta, xn.z - xv.z, xn.z);
         zn.w = fmaf(beta, xn.w - xv.w, xn.w);
-        x[i] = xn;
+        if (!keep_x) x[i] = xn;
         z[i] = zn;
     }
 }
@@ -599,12 +600,12 @@ int launch_monotone_scalar(tc_plan *p, int init, cudaStream_t s) {
 }
 
 int launch_update_monotone(tc_plan *p, float *x, float *z, const float *v, size_t n,
-                           cudaStream_t s, int accept_all) {
+                           cudaStream_t s, int accept_all, int keep_x) {
     const size_t n4 = n / 4;
     TC_PROFILED(TCK_UPDATE, s,
                 k_update_monotone<<<grid_for(n4), TC_RED_THREADS, 0, s>>>(
         reinterpret_cast<float4 *>(x), reinterpret_cast<float4 *>(z),
-        reinterpret_cast<const float4 *>(v), n4, p->scal, accept_all));
+        reinterpret_cast<const float4 *>(v), n4, p->scal, accept_all, keep_x));
     TC_LAUNCHED("k_update_monotone");
     return TC_OK;
 }
