@@ -351,7 +351,10 @@ int solve_loop(tc_plan *p, const float *b, const float *w, float *x, int batch,
             return rc;
         if (!fused && (rc = launch_dots_gzx_gg(p, xb, st->z, xa, n, s))) return rc;
         if ((rc = launch_solver_scalar(p, opts->restart, s))) return rc;
-        if (fused) {
+        if (fused && it == opts->n_iter - 1 && xa == x) {
+            // last step with x_k in x: write x_{k+1} there too (cheaper than a copy back)
+            if ((rc = launch_update_monotone(p, xa, st->z, xb, n, s, 1, 0))) return rc;
+        } else if (fused) {
             if ((rc = launch_update_monotone(p, xa, st->z, xb, n, s, 1, 1))) return rc;  // z only
             float *t = xa;
             xa = xb;
