@@ -156,7 +156,7 @@ def algorithmic_bytes(name, N, A, D, w, B):
         "k_adj_col": grid_rows + img,
         "k_prior": 4 * img,  # f, g read + g written, and x_prev for the fused restart dots
         "k_dots_gzx_gg": 3 * img,
-        "k_update": 4 * img,  # x and the next iterate read, x and z written
+        "k_update": 3 * img,  # x_k and the next iterate read, z written (x_{k+1} stays where it was made)
     }
     return per.get(name, 0) * B
 
