@@ -327,7 +327,7 @@ int solve_loop(tc_plan *p, const float *b, const float *w, float *x, int batch,
             if ((rc = launch_step_to_candidate(p, st->z, st->g, n, s))) return rc;  // g := v
             if ((rc = value_impl(p, st->g, b, w, prior, batch, p->scal + SC_DATA_V, p->scal + SC_PRIOR_V, s)))
                 return rc;
-            if ((rc = launch_monotone_scalar(p, 0, s))) return rc;
+            if ((rc = launch_monotone_scalar(p, s))) return rc;
             if ((rc = launch_update_monotone(p, x, st->z, st->g, n, s))) return rc;
         }
     }

@@ -200,10 +200,10 @@ int prior_tile_count(int n);
 int launch_prior_value(tc_plan *p, const float *x, int nb, const tc_prior *pr,
                        double *h_acc, cudaStream_t s);
 // Monotone variant: v = z - step g in place of g; the accept/restart decision
-// and momentum (init = 1: only set Phi(x_k) from its parts); the update
-// x_{k+1} = accepted ? v : x_k, z_{k+1} = x_{k+1} + beta (x_{k+1} - x_k).
+// and momentum; the update x_{k+1} = accepted ? v : x_k,
+// z_{k+1} = x_{k+1} + beta (x_{k+1} - x_k).
 int launch_step_to_candidate(tc_plan *p, const float *z, float *g, size_t n, cudaStream_t s);
-int launch_monotone_scalar(tc_plan *p, int init, cudaStream_t s);
+int launch_monotone_scalar(tc_plan *p, cudaStream_t s);
 int launch_update_monotone(tc_plan *p, float *x, float *z, const float *v, size_t n,
                            cudaStream_t s, int accept_all = 0, int keep_x = 0);
 int launch_reduce_finalize(const double *partials, int n, double *acc,

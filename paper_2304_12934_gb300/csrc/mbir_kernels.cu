@@ -228,6 +228,10 @@ __global__ void __launch_bounds__(PRIOR_THREADS, PRIOR_MIN_BLOCKS) k_prior(const
         const size_t i = (size_t)z * NN + off;
         const float g_old = (GRAD && own && interior) ? g[i] : 0.f;
         const float x_old = (DOTS && own && interior) ? xprev[i] : 0.f;
+        if (GRAD && interior && z + 2 < a.z1) {  // the same lines two planes on, into L2
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(g + i + 2 * NN));
+            if (DOTS) asm volatile("prefetch.global.L2 [%0];" ::"l"(xprev + i + 2 * NN));
+        }
         if (ring) {
             if (up) fpl[nxt * PRS + h] = f_nx;                 // 3D: plane z + 1
             else if (!three && z > zs) fpl[cur * PRS + h] = f_nx;  // 2D: slices are independent
@@ -426,11 +430,10 @@ __global__ void k_step_to_candidate(const float4 *__restrict__ z, float4 *__rest
     }
 }
 
-// init: nothing to decide (Phi(x_k) is held as SC_DATA_X + SC_PRIOR_X).
-// Otherwise accept v if Phi(v) <= Phi(x_k); on rejection keep x_k and
-// restart the momentum (t := 1, beta = 0).
-__global__ void k_monotone_scalar(double *sc, int init) {
-    if (threadIdx.x != 0 || blockIdx.x != 0 || init) return;
+// Phi(x_k) is held as SC_DATA_X + SC_PRIOR_X.  Accept v if Phi(v) <= Phi(x_k);
+// on rejection keep x_k and restart the momentum (t := 1, beta = 0).
+__global__ void k_monotone_scalar(double *sc) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
     const double phi_v = sc[SC_DATA_V] + sc[SC_PRIOR_V];
     const double phi_x = sc[SC_DATA_X] + sc[SC_PRIOR_X];
     const bool accept = phi_v <= phi_x;
@@ -593,8 +596,8 @@ int launch_step_to_candidate(tc_plan *p, const float *z, float *g, size_t n, cud
     return TC_OK;
 }
 
-int launch_monotone_scalar(tc_plan *p, int init, cudaStream_t s) {
-    TC_PROFILED(TCK_SCALAR, s, k_monotone_scalar<<<1, 32, 0, s>>>(p->scal, init));
+int launch_monotone_scalar(tc_plan *p, cudaStream_t s) {
+    TC_PROFILED(TCK_SCALAR, s, k_monotone_scalar<<<1, 32, 0, s>>>(p->scal));
     TC_LAUNCHED("k_monotone_scalar");
     return TC_OK;
 }
