@@ -208,6 +208,30 @@ __host__ __device__ constexpr int fft_twiddle_offset(int logns) {
     return logns <= 4 ? 0 : fft_twiddle_offset(logns - 4) + (15 << (logns - 4));
 }
 
+// v[q] *= W^q, q = 1..R-1, from the table entries at q = 1, 2, 4, 8 (tk: the
+// leg-1 entry of this butterfly, stride NS between legs): the other powers
+// are products of at most three of them.
+template <int SIGN, int R, int NS>
+__device__ __forceinline__ void apply_stage_twiddles(float2 *v, const float2 *__restrict__ tk) {
+    float2 w[R];
+    w[1] = tw_get<SIGN>(tk, 0);
+    if constexpr (R > 2) w[2] = tw_get<SIGN>(tk, NS);
+    if constexpr (R > 4) w[4] = tw_get<SIGN>(tk, 3 * NS);
+    if constexpr (R > 8) w[8] = tw_get<SIGN>(tk, 7 * NS);
+    if constexpr (R > 2) w[3] = cmul(w[2], w[1]);
+    if constexpr (R > 4) {
+        w[5] = cmul(w[4], w[1]);
+        w[6] = cmul(w[4], w[2]);
+        w[7] = cmul(w[4], w[3]);
+    }
+    if constexpr (R > 8) {
+#pragma unroll
+        for (int q = 9; q < 16; ++q) w[q] = cmul(w[8], w[q - 8]);
+    }
+#pragma unroll
+    for (int q = 1; q < R; ++q) v[q] = cmul(v[q], w[q]);
+}
+
 template <int SIGN, int LOGN, int LOGR, int LOGNS, int IT>
 __device__ __forceinline__ void stockham_stage_ct(float2 *s, int cnt, const float2 *__restrict__ tw) {
     constexpr int R = 1 << LOGR, LOGPER = LOGN - LOGR, PER = 1 << LOGPER, NS = 1 << LOGNS;
@@ -232,28 +256,7 @@ __device__ __forceinline__ void stockham_stage_ct(float2 *s, int cnt, const floa
 #pragma unroll
                 for (int q = 0; q < R; ++q) v[i][q] = src[spad(j + q * PER)];
             }
-            if constexpr (LOGNS > 0) {
-                // W^q for q = 1..R-1 from the table entries at q = 1, 2, 4, 8:
-                // the other powers are products of at most three of them.
-                const float2 *tk = tws + (j & (NS - 1));
-                float2 w[R];
-                w[1] = tw_get<SIGN>(tk, 0);
-                if constexpr (R > 2) w[2] = tw_get<SIGN>(tk, NS);
-                if constexpr (R > 4) w[4] = tw_get<SIGN>(tk, 3 * NS);
-                if constexpr (R > 8) w[8] = tw_get<SIGN>(tk, 7 * NS);
-                if constexpr (R > 2) w[3] = cmul(w[2], w[1]);
-                if constexpr (R > 4) {
-                    w[5] = cmul(w[4], w[1]);
-                    w[6] = cmul(w[4], w[2]);
-                    w[7] = cmul(w[4], w[3]);
-                }
-                if constexpr (R > 8) {
-#pragma unroll
-                    for (int q = 9; q < 16; ++q) w[q] = cmul(w[8], w[q - 8]);
-                }
-#pragma unroll
-                for (int q = 1; q < R; ++q) v[i][q] = cmul(v[i][q], w[q]);
-            }
+            if constexpr (LOGNS > 0) apply_stage_twiddles<SIGN, R, NS>(v[i], tws + (j & (NS - 1)));
         }
     }
     __syncthreads();
@@ -285,6 +288,38 @@ __device__ __forceinline__ void fft_ct(float2 *s, int cnt, const float2 *__restr
         stockham_stage_ct<SIGN, LOGN, 2, LOGNS, 4>(s, cnt, tw);
     } else if constexpr (LOGN - LOGNS == 1) {
         stockham_stage_ct<SIGN, LOGN, 1, LOGNS, 8>(s, cnt, tw);
+    }
+}
+
+// A pair of transforms (cnt = 2) of length 2^LOGN, LOGN = 3 (mod 4), run with
+// blockDim.x == n / 8: the last (radix-8) stage then gives each thread one
+// butterfly of each transform at the same index, and instead of storing it
+// calls emit(k, X0[k], X1[k]) for its eight output indices k (natural order;
+// a warp's k are consecutive).  The shared buffer keeps the second-to-last
+// stage's result.
+template <int SIGN, int LOGN, int LOGNS = 0, class Emit>
+__device__ __forceinline__ void fft_ct_pair_emit(float2 *s, const float2 *__restrict__ tw, Emit &&emit) {
+    if constexpr (LOGN - LOGNS >= 4) {
+        stockham_stage_ct<SIGN, LOGN, 4, LOGNS, 1>(s, 2, tw);
+        fft_ct_pair_emit<SIGN, LOGN, LOGNS + 4>(s, tw, emit);
+    } else {
+        static_assert(LOGN - LOGNS == 3, "the last stage is radix 8");
+        constexpr int R = 8, LOGR = 3, PER = 1 << (LOGN - LOGR), NS = 1 << LOGNS;
+        constexpr int TS = fft_tstride(1 << LOGN), LSTRIDE = PER + PER / 16;
+        const int j = threadIdx.x;  // < PER = blockDim.x
+        float2 v[2][R];
+#pragma unroll
+        for (int tr = 0; tr < 2; ++tr) {
+            const float2 *sj = s + tr * TS + spad(j);
+#pragma unroll
+            for (int q = 0; q < R; ++q) v[tr][q] = sj[q * LSTRIDE];
+            if constexpr (LOGNS > 0)
+                apply_stage_twiddles<SIGN, R, NS>(v[tr], tw + fft_twiddle_offset(LOGNS) + (j & (NS - 1)));
+            dft_reg<SIGN, R>(v[tr]);
+        }
+        const int base = ((j >> LOGNS) << (LOGNS + LOGR)) + (j & (NS - 1));
+#pragma unroll
+        for (int q = 0; q < R; ++q) emit(base + q * NS, v[0][q], v[1][q]);
     }
 }
 

@@ -336,8 +336,17 @@ __global__ void __launch_bounds__(512) k_adj_row(const float2 *__restrict__ V, f
         }
         __syncthreads();
     }
-    fft_ct<+1, LOGN>(sm, 2, g.twN);
     float2 *Ur = U + ((size_t)b * g.R + r) * N;
+    if constexpr (LOGN % 4 == 3) {
+        if (blockDim.x == N / 8) {  // the last FFT stage writes the image row directly
+            fft_ct_pair_emit<+1, LOGN>(sm, g.twN, [&](int q, float2 x0, float2 x1) {
+                const int ix = (q + N / 2) & (N - 1);
+                Ur[ix] = cadd(x0, cmul(x1, cconj(g.twG[ix])));
+            });
+            return;
+        }
+    }
+    fft_ct<+1, LOGN>(sm, 2, g.twN);
 #pragma unroll 4
     for (int ix = threadIdx.x; ix < N; ix += blockDim.x) {
         const int q = (ix - N / 2) & (N - 1);
