@@ -29,7 +29,7 @@ __all__ = [
     "radon_fwd_at", "radon_adj_at", "dirichlet", "neighbour_offsets",
     "prior_weights", "rho", "rho_prime", "prior_value_grad", "data_grad",
     "objective_grad", "objective_value", "power_norm", "prior_lipschitz", "mbir_solve",
-    "PAPER_PRIOR",
+    "normal_op", "PAPER_PRIOR",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -156,6 +156,14 @@ def radon_adj_at(y, n, pix_idx, theta=None, delta: float = 0.0) -> np.ndarray:
     if rc:
         raise ValueError(f"oracle_radon_adj_at failed: {rc}")
     return out
+
+
+def normal_op(f: np.ndarray, n_angles: int, n_det: int, theta=None, delta: float = 0.0) -> np.ndarray:
+    """A^T A f for f of shape [N,N] or [B,N,N]: the Hessian of the unweighted data
+    term (Sec. 3 Eqs. gradient, transpose), as the plain composition of the exact
+    operators above."""
+    n = f.shape[-1]
+    return radon_adj(radon_fwd(f, n_angles, n_det, theta, delta), n, theta, delta)
 
 
 def dirichlet(D: int, u: float) -> float:
