@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--chunk", type=int, default=64, help="slices per launch (plan max_batch)")
     ap.add_argument("--plain-slices", type=int, default=32)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--normal-slices", type=int, default=64,
+                    help="slices of the unweighted 1024^2 solve comparing the Toeplitz-plus-Hankel "
+                         "normal operator with the gridded operators (0: skip)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--uneven-slices", type=int, default=512,
                     help="slices of the uneven-size batching measurement (0 skips it)")
@@ -157,6 +160,10 @@ def algorithmic_bytes(name, N, A, D, w, B):
         "k_prior": 4 * img,  # f, g read + g written, and x_prev for the fused restart dots
         "k_dots_gzx_gg": 3 * img,
         "k_update": 3 * img,  # x_k and the next iterate read, z written (x_{k+1} stays where it was made)
+        # normal operator A^T A (Toeplitz-plus-Hankel embedding): half-plane rows ky = 0..N
+        "k_nrm_col_fwd": img + 8 * (N + 1) * N,
+        "k_nrm_row": 2 * 8 * (N + 1) * N,
+        "k_nrm_col_adj": 8 * (N + 1) * N + 2 * img,  # rows in; gradient out, A^T b in
     }
     return per.get(name, 0) * B
 
@@ -314,6 +321,82 @@ def uneven_batch(api, synth, dev, n_slices, reps=3):
             "sizes": "sides {256,512,1024,2048}, angles {64,128,256}, D = 2 round(N/sqrt 2), seeded"}
 
 
+def normal_operator(api, synth, dev, n_slices, iters=3):
+    """Unweighted MBIR (noise-free analytic data, W = I, 26-neighbour prior) on
+    n_slices slices of 1024^2 with 360 angles and 1448 bins: the data term's
+    Hessian through the gridded A and A^T against the Toeplitz-plus-Hankel normal
+    operator (no gridding).  Both solves start from zero with the same step."""
+    import numpy as np
+    import torch
+    N, A, D = 1024, 360, 1448
+    theta = np.arange(A) * (math.pi / A)
+    b = synth.ellipsoid_sinogram_torch(N, n_slices, theta, D, dev, scale=1.0 / N, seed=synth.BASE_SEED + 5)
+    prior = api.Prior(lam=1e-2, dims=3)
+    stream = torch.cuda.current_stream(dev)
+    out = {"workload": f"{n_slices} slices of {N}x{N}, {A} angles, {D} bins, noise-free, W = I, "
+                       f"26-nbr qGGMRF", "iterations": iters}
+    with api.Plan(N, A, D, max_batch=n_slices, device=dev) as plan:
+        t0 = time.perf_counter()
+        plan.prepare_normal()
+        out["prepare_s"] = round(time.perf_counter() - t0, 3)
+        v = torch.tensor(synth.random_start((4, N, N), 17), dtype=torch.float32, device=dev)
+        step = 1.0 / (1.05 * api.mbir_power_norm(plan, v, None, n_iter=15) + api.prior_lipschitz(prior))
+        xs, prof = {}, {}
+        for mode in (False, True):
+            x = torch.zeros((n_slices, N, N), device=dev)
+            st = api.SolveState(x)
+            api.mbir_solve(plan, b, None, x, 1, step, prior, state=st, normal=mode)
+            torch.cuda.synchronize()
+            api.profile_enable(True)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            api.mbir_solve(plan, b, None, x, iters, step, prior, state=st, normal=mode)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            prof[mode] = api.profile_collect()
+            api.profile_enable(False)
+            out["normal_slice_iter_s" if mode else "gridded_slice_iter_s"] = round(
+                n_slices * iters / (e0.elapsed_time(e1) / 1e3), 1)
+            xs[mode] = x
+        out["speedup"] = round(out["normal_slice_iter_s"] / out["gridded_slice_iter_s"], 3)
+        out["rel_diff_x"] = float((xs[True] - xs[False]).norm() / xs[False].norm().clamp(min=1e-30))
+        out["kernels_normal"] = {k: {"launches": c, "ms_per_launch": round(m / c, 4),
+                                     "gbs_alg": round(algorithmic_bytes(k, N, A, D, plan.kernel_width,
+                                                                        n_slices) / (m / c / 1e3) / 1e9, 1)
+                                     if k.startswith("k_nrm") else None}
+                                 for k, (c, m) in sorted(prof[True].items(), key=lambda kv: -kv[1][1])}
+    return out
+
+
+def normal_vs_gridded_operator(api, plan, x, reps=3):
+    """A^T A on one launch of slices of the main workload: gridded A then A^T
+    against the Toeplitz-plus-Hankel embedding (device ms per launch)."""
+    import torch
+    stream = torch.cuda.current_stream(x.device)
+    t0 = time.perf_counter()
+    plan.prepare_normal()
+    prep = time.perf_counter() - t0
+    y = api.radon_fwd(plan, x)
+    g = api.radon_adj(plan, y)
+    nx = api.radon_normal(plan, x)
+    torch.cuda.synchronize()
+    res = {}
+    for name, fn in (("gridded_ms", lambda: api.radon_adj(plan, api.radon_fwd(plan, x, y=y), x=g)),
+                     ("normal_ms", lambda: api.radon_normal(plan, x, out=nx))):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        res[name] = round(e0.elapsed_time(e1) / reps, 3)
+    res["speedup"] = round(res["gridded_ms"] / res["normal_ms"], 3)
+    res["rel_diff"] = float((nx - g).norm() / g.norm().clamp(min=1e-30))
+    res["slices"] = x.shape[0]
+    res["prepare_s"] = round(prep, 3)
+    return res
+
+
 # ------------------------------------------------------------- CUDA path ---
 def run_ours(args):
     import numpy as np
@@ -435,6 +518,13 @@ def run_ours(args):
                "d2h_bytes_per_step": int(xh.numel() * 4),
                "call": "mbir_solve_host(n_iter=1) per step: H2D b, w, x; one iteration; D2H x"}
 
+    # ---- normal operator (Toeplitz-plus-Hankel) against the gridded pair
+    normal = None
+    if rank == 0 and args.normal_slices > 0:
+        normal = {"headline_operator": normal_vs_gridded_operator(api, plan, x[:MB].contiguous()),
+                  "unweighted_solve": normal_operator(api, synth, dev, args.normal_slices)}
+        torch.cuda.empty_cache()
+
     # ---- uneven sizes: one CUDA graph over per-geometry batches vs one slice per launch
     uneven = None
     if rank == 0 and args.uneven_slices > 0:
@@ -465,7 +555,7 @@ def run_ours(args):
                            "parallelism": f"replicas x{ws}"},
                 "roofline": roofline, "kernels": kernels, "batched_vs_plain": plain,
                 "e2e": e2e, "cpu_baseline": cpu, "gpu_launches": int(gpu_launches),
-                "uneven_batch": uneven,
+                "uneven_batch": uneven, "normal_operator": normal,
                 "clocks": clk.summary(), "solver": {"step": step, "restarts": st.n_restarts,
                                                     "obj": list(st.obj)}}
         print(json.dumps(line), flush=True)

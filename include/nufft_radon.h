@@ -127,6 +127,30 @@ int radon_fwd(tc_plan *plan, const float *x, float *y, int batch, void *stream);
  *   y  [batch][A][D] float32 in;  x [batch][N][N] float32 out (overwritten). */
 int radon_adj(tc_plan *plan, const float *y, float *x, int batch, void *stream);
 
+/* x_out = A^T A x, the Hessian of the unweighted data term (Sec. 3 Eqs.
+ * gradient and transpose), without gridding.  For even D (with the Nyquist
+ * pair weighted 1/2, as in radon_fwd) the detector-bin sum of two shifted
+ * Dirichlet kernels is exact in closed form, which makes A^T A Toeplitz plus
+ * Hankel in the pixel coordinates:
+ *   (A^T A x)(p') = sum_p x(p) [T(p' - p) + H(p' + p)],
+ *   T(d) = sum_a K(s_d(a)) - cos(pi s_d(a)) / 2D,
+ *   H(e) = sum_a cos(pi (s_e(a) + 2 delta)) / 2D,
+ * with s_d(a) = d_x cos(theta_a) + d_y sin(theta_a) and K the Dirichlet
+ * kernel.  Both are convolutions on the 2N-periodic grid: one 2D FFT of the
+ * image (half plane), a pointwise product with the precomputed spectra of T
+ * and H, and the inverse 2D FFT at the N x N pixels.  The result equals
+ * radon_adj(radon_fwd(x)) up to FP32 rounding and the NUFFT's own kernel
+ * error, and costs no interpolation, spreading or detector transforms.
+ *   x, x_out  [batch][N][N] float32 DEVICE (may be the same buffer).
+ * The first call on a plan builds the spectra (FP64, synchronous on the
+ * stream; device memory about 12 (N+1) 2N bytes, plus a 16 (2N)^2-byte
+ * temporary), as tc_plan_prepare_normal does; later calls are asynchronous. */
+int radon_normal(tc_plan *plan, const float *x, float *x_out, int batch, void *stream);
+
+/* Builds the spectra of radon_normal's kernels if not yet built (idempotent,
+ * synchronous).  Call it before capturing radon_normal into a CUDA graph. */
+int tc_plan_prepare_normal(tc_plan *plan, void *stream);
+
 /* ---------------------------------------------------------------- prior --- */
 /* qGGMRF prior (Sec. 3 Eqs. reg2, reg3; defaults of Sec. 5):
  *   H(f) = sum_m sum_{n in N(m)} w_mn rho(f_m - f_n),
@@ -183,6 +207,12 @@ typedef struct {
     int n_iter;      /* iterations to run in this call (>= 0) */
     double step;     /* constant step, 1/L with L >= ||A^T W A|| + lambda * 8/(sigma^2 c) */
     int restart;     /* 0, 1 or 2 as above; anything else is TC_ERR_INVALID_ARG */
+    int normal;      /* 1: unweighted data term (w must be NULL) through radon_normal's
+                        embedding: grad = A^T A z - A^T b, with A^T b (in state->atb)
+                        and ||b||^2 formed once per call.  Restart 0 or 1 only; the
+                        reported data term 1/2 <z, A^T A z> - <z, A^T b> + 1/2 ||b||^2
+                        loses relative precision as the residual vanishes.  0: the
+                        gridded operators. */
 } tc_solve_opts;
 
 /* Solver state; resuming with the same state continues the iteration exactly.
@@ -192,7 +222,9 @@ typedef struct {
  *   k      iterations completed; k == 0 starts fresh (z := x, t := 1)
  *   n_restarts  restarts taken so far (monotone variant: rejected steps)
  *   obj    objective terms (data, lambda H) at the last gradient point z;
- *          with restart = 2, at the returned x */
+ *          with restart = 2, at the returned x
+ *   atb    with opts->normal: caller-owned DEVICE buffer [batch][N][N] that
+ *          receives A^T b (else ignored, may be NULL) */
 typedef struct {
     float *z;
     float *g;
@@ -200,6 +232,7 @@ typedef struct {
     int k;
     int n_restarts;
     double obj[2];
+    float *atb;
 } tc_solve_state;
 
 /* Run opts->n_iter iterations on device buffers.

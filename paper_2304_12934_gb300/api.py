@@ -41,13 +41,14 @@ class _Prior(ctypes.Structure):
 
 
 class _SolveOpts(ctypes.Structure):
-    _fields_ = [("n_iter", ctypes.c_int), ("step", ctypes.c_double), ("restart", ctypes.c_int)]
+    _fields_ = [("n_iter", ctypes.c_int), ("step", ctypes.c_double), ("restart", ctypes.c_int),
+                ("normal", ctypes.c_int)]
 
 
 class _SolveState(ctypes.Structure):
     _fields_ = [("z", ctypes.c_void_p), ("g", ctypes.c_void_p), ("t", ctypes.c_double),
                 ("k", ctypes.c_int), ("n_restarts", ctypes.c_int),
-                ("obj", ctypes.c_double * 2)]
+                ("obj", ctypes.c_double * 2), ("atb", ctypes.c_void_p)]
 
 
 # every symbol the C header declares
@@ -56,7 +57,7 @@ SYMBOLS = ("tc_status_string", "tc_last_error_detail", "tc_plan_create", "tc_pla
            "mbir_power_norm", "mbir_solve", "mbir_solve_host", "tc_profile_enable",
            "tc_profile_collect", "tc_profile_kernel_name", "tc_launch_count",
            "tc_plan_autotune", "tc_plan_set_launch", "tc_prior_grad_noalloc",
-           "tc_plan_status", "tc_selftest_wait_timeout")
+           "tc_plan_status", "tc_selftest_wait_timeout", "radon_normal", "tc_plan_prepare_normal")
 
 
 def lib_path() -> str:
@@ -103,10 +104,12 @@ def load(build_if_missing: bool = True):
     L.tc_prior_grad_noalloc.argtypes = [vp, vp, i, i, ctypes.POINTER(_Prior), vp, vp]
     L.tc_plan_status.argtypes = [vp]
     L.tc_selftest_wait_timeout.argtypes = [vp]
+    L.radon_normal.argtypes = [vp, vp, vp, i, vp]
+    L.tc_plan_prepare_normal.argtypes = [vp, vp]
     for fn in ("tc_profile_enable", "tc_profile_collect", "tc_plan_create", "tc_plan_destroy",
                "radon_fwd", "radon_adj", "mbir_grad", "mbir_power_norm", "mbir_solve",
                "mbir_solve_host", "tc_plan_autotune", "tc_plan_set_launch",
-               "tc_prior_grad_noalloc"):
+               "tc_prior_grad_noalloc", "radon_normal", "tc_plan_prepare_normal"):
         getattr(L, fn).restype = i
     _LIB = L
     return L
@@ -206,6 +209,12 @@ class Plan:
                                                            _stream(stream, self.device)))
         return ch.value, cp.value
 
+    def prepare_normal(self, stream=None):
+        """Build the spectra of radon_normal's Toeplitz-plus-Hankel kernels now
+        (otherwise the first radon_normal call does; needed before graph capture)."""
+        _check("tc_plan_prepare_normal", load().tc_plan_prepare_normal(self.handle,
+                                                                       _stream(stream, self.device)))
+
     def set_launch(self, chunk, col_pairs=0):
         """Slices per launch (1..max_batch) and column pairs per CTA (1, 2, 4; 0 keeps)."""
         _check("tc_plan_set_launch", load().tc_plan_set_launch(self.handle, int(chunk), int(col_pairs)))
@@ -262,6 +271,19 @@ def radon_adj(plan: Plan, y: torch.Tensor, x: torch.Tensor | None = None, stream
     return x.reshape(plan.image_shape(B)[1:]) if sq else x
 
 
+def radon_normal(plan: Plan, x: torch.Tensor, out: torch.Tensor | None = None, stream=None):
+    """out = A^T A x by Toeplitz-plus-Hankel embedding (no gridding).  x: [B,N,N] or [N,N]."""
+    B, sq = _batch_of(x, plan.image_shape(1)[1:])
+    xb = x.reshape(plan.image_shape(B))
+    _need(xb, plan.image_shape(B), "x", plan.device)
+    if out is None:
+        out = torch.empty(plan.image_shape(B), device=plan.device, dtype=torch.float32)
+    ob = out.reshape(plan.image_shape(B))
+    _need(ob, plan.image_shape(B), "out", plan.device)
+    _check("radon_normal", load().radon_normal(plan.handle, _ptr(xb), _ptr(ob), B, _stream(stream, plan.device)))
+    return out.reshape(plan.image_shape(B)[1:]) if sq else out
+
+
 def mbir_grad(plan: Plan, x, b, w=None, prior: Prior | None = None, grad=None, obj=None, stream=None):
     """grad = A^T W (A x - b) + lam grad H(x); obj (device float64 [2]) = (data, lam H)."""
     B = x.shape[0]
@@ -309,10 +331,12 @@ class SolveState:
         self.k = 0
         self.n_restarts = 0
         self.obj = (0.0, 0.0)
+        self.atb = None  # A^T b, allocated by a normal-operator solve
 
     def _c(self):
         s = _SolveState(self.z.data_ptr(), self.g.data_ptr(), self.t, self.k, self.n_restarts)
         s.obj[0], s.obj[1] = self.obj
+        s.atb = self.atb.data_ptr() if self.atb is not None else None
         return s
 
     def _load(self, s):
@@ -330,21 +354,25 @@ def _restart_code(restart) -> int:
 
 
 def mbir_solve(plan: Plan, b, w, x, n_iter, step, prior: Prior | None = None, restart=True,
-               state: SolveState | None = None, stream=None) -> SolveState:
+               state: SolveState | None = None, stream=None, normal=False) -> SolveState:
     """Run n_iter accelerated-gradient iterations on device buffers (x in/out).
 
     restart: True (gradient test), "monotone" (function-value test: Phi(x_k)
     never increases; state.obj is then the objective at the returned x) or
-    False (plain momentum)."""
+    False (plain momentum).
+    normal: unweighted data term (w must be None) through the Toeplitz-plus-Hankel
+    normal operator (radon_normal) instead of the gridded A and A^T."""
     B = x.shape[0]
     _need(x, plan.image_shape(B), "x", plan.device)
     _need(b, plan.sino_shape(B), "b", plan.device)
     if w is not None:
         _need(w, plan.sino_shape(B), "w", plan.device)
     st = state if state is not None else SolveState(x)
+    if normal and st.atb is None:
+        st.atb = torch.empty_like(x)
     cs = st._c()
     pr = prior._c() if prior is not None else None
-    opts = _SolveOpts(int(n_iter), float(step), _restart_code(restart))
+    opts = _SolveOpts(int(n_iter), float(step), _restart_code(restart), int(bool(normal)))
     _check("mbir_solve", load().mbir_solve(plan.handle, _ptr(b), _ptr(w), _ptr(x), B,
                                            ctypes.byref(pr) if pr is not None else None,
                                            ctypes.byref(opts), ctypes.byref(cs),
@@ -354,10 +382,11 @@ def mbir_solve(plan: Plan, b, w, x, n_iter, step, prior: Prior | None = None, re
 
 
 def mbir_solve_host(plan: Plan, b_host, w_host, x_host, n_iter, step, prior: Prior | None = None,
-                    restart=True, state: SolveState | None = None, dev=None, stream=None):
+                    restart=True, state: SolveState | None = None, dev=None, stream=None, normal=False):
     """End-to-end solve from host (ideally pinned) tensors: copies in, iterates, copies x back.
 
     dev: optional dict of reusable device buffers {"b", "w", "x"}.
+    normal: as in mbir_solve (w_host must be None).
     """
     B = x_host.shape[0]
     for t, shp, nm in ((b_host, plan.sino_shape(B), "b_host"), (x_host, plan.image_shape(B), "x_host")):
@@ -370,9 +399,11 @@ def mbir_solve_host(plan: Plan, b_host, w_host, x_host, n_iter, step, prior: Pri
     if w_host is not None:
         dw = dev.setdefault("w", torch.empty(plan.sino_shape(B), device=plan.device))
     st = state if state is not None else SolveState(dx)
+    if normal and st.atb is None:
+        st.atb = torch.empty_like(dx)
     cs = st._c()
     pr = prior._c() if prior is not None else None
-    opts = _SolveOpts(int(n_iter), float(step), _restart_code(restart))
+    opts = _SolveOpts(int(n_iter), float(step), _restart_code(restart), int(bool(normal)))
     _check("mbir_solve_host", load().mbir_solve_host(
         plan.handle, _ptr(b_host), _ptr(w_host), _ptr(x_host), _ptr(db), _ptr(dw), _ptr(dx), B,
         ctypes.byref(pr) if pr is not None else None, ctypes.byref(opts), ctypes.byref(cs),

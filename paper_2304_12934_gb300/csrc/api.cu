@@ -48,29 +48,51 @@ int check_ptrs(std::initializer_list<const void *> req, std::initializer_list<co
     return TC_OK;
 }
 
-// grad = A^T W (A x - b) + lambda grad H(x); scal[SC_DATA], scal[SC_PRIOR] set.
+// scal[SC_DATA] and scal[SC_PRIOR] before the chunks add to them: zero, or
+// with the normal operator (atb given) 1/2 ||b||^2 and zero.
+int data_init(tc_plan *p, const float *atb, cudaStream_t s) {
+    TC_CUDA(cudaMemsetAsync(p->scal + SC_DATA, 0, 2 * sizeof(double), s));
+    if (atb) return launch_reduce_finalize(p->scal + SC_BB, 1, p->scal + SC_DATA, 0, 0.5, s);
+    return TC_OK;
+}
+
+// Data-term gradient of one chunk of nb slices: grad = A^T W (A x - b), its
+// value added to scal[SC_DATA].  With atb (= A^T b of the chunk, W = I), A^T A
+// comes from the Toeplitz-plus-Hankel embedding and the value is formed only
+// when want_value.
+int data_grad_chunk(tc_plan *p, const float *x, const float *b, const float *w, float *grad, int nb,
+                    const float *atb, bool want_value, cudaStream_t s) {
+    if (atb)
+        return launch_radon_normal_chunk(p, x, grad, nb, atb, want_value ? x : nullptr, p->scal + SC_DATA, s);
+    int rc = launch_radon_fwd_chunk(p, x, nullptr, nb, b, w, p->sr, p->scal + SC_DATA, s);
+    if (rc) return rc;
+    return launch_radon_adj_chunk(p, p->sr, grad, nb, s);
+}
+
+// grad = A^T W (A x - b) + lambda grad H(x); scal[SC_DATA], scal[SC_PRIOR] set
+// (with atb, the data value and the prior value only when want_value).
 // ready: optional per-chunk events the chunk's first kernel waits for (slabs
 // still being copied in on another stream).
 // dot_x: with a prior, the prior kernel also forms the restart-test inner
 // products <grad, x - dot_x> and <grad, grad>.
+// atb: A^T b of the whole batch for the normal-operator data term (W = I).
 int grad_impl(tc_plan *p, const float *x, const float *b, const float *w,
               const tc_prior *prior, float *grad, int batch, cudaStream_t s,
-              bool want_prior_value = true, const cudaEvent_t *ready = nullptr,
-              const float *dot_x = nullptr, double step = 0.0) {
-    TC_CUDA(cudaMemsetAsync(p->scal + SC_DATA, 0, 2 * sizeof(double), s));
+              bool want_value = true, const cudaEvent_t *ready = nullptr,
+              const float *dot_x = nullptr, double step = 0.0, const float *atb = nullptr) {
+    int rc = data_init(p, atb, s);
+    if (rc) return rc;
     const size_t ni = img_elems(p), ns = sino_elems(p);
     for (int c0 = 0; c0 < batch; c0 += p->chunk) {
         const int nb = batch - c0 < p->chunk ? batch - c0 : p->chunk;
         if (ready) TC_CUDA(cudaStreamWaitEvent(s, ready[c0 / p->chunk], 0));
-        int rc = launch_radon_fwd_chunk(p, x + c0 * ni, nullptr, nb, b ? b + c0 * ns : nullptr,
-                                        w ? w + c0 * ns : nullptr, p->sr, p->scal + SC_DATA, s);
-        if (rc) return rc;
-        rc = launch_radon_adj_chunk(p, p->sr, grad + c0 * ni, nb, s);
+        rc = data_grad_chunk(p, x + c0 * ni, b ? b + c0 * ns : nullptr, w ? w + c0 * ns : nullptr,
+                             grad + c0 * ni, nb, atb ? atb + c0 * ni : nullptr, want_value, s);
         if (rc) return rc;
     }
     if (prior && prior->lambda != 0.0) {
-        int rc = launch_prior_grad(p, x, grad, batch, prior,
-                                   want_prior_value ? p->scal + SC_PRIOR : nullptr, s, dot_x, 0, -1, step);
+        rc = launch_prior_grad(p, x, grad, batch, prior, want_value ? p->scal + SC_PRIOR : nullptr, s, dot_x,
+                               0, -1, step);
         if (rc) return rc;
     }
     return TC_OK;
@@ -197,6 +219,31 @@ int radon_adj(tc_plan *p, const float *y, float *x, int batch, void *stream) {
     return TC_OK;
 }
 
+int tc_plan_prepare_normal(tc_plan *p, void *stream) {
+    if (!p) return TC_ERR_INVALID_ARG;
+    DeviceGuard dg(p->device);
+    if (!dg.ok) return TC_ERR_CUDA;
+    return normal_prepare(p, (cudaStream_t)stream);
+}
+
+int radon_normal(tc_plan *p, const float *x, float *x_out, int batch, void *stream) {
+    if (!p || batch < 0) return TC_ERR_INVALID_ARG;
+    if (batch == 0) return TC_OK;
+    if (check_ptrs({x, x_out}, {})) return TC_ERR_INVALID_ARG;
+    DeviceGuard dg(p->device);
+    if (!dg.ok) return TC_ERR_CUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = normal_prepare(p, s);
+    if (rc) return rc;
+    const size_t ni = img_elems(p);
+    for (int c0 = 0; c0 < batch; c0 += p->chunk) {
+        const int nb = batch - c0 < p->chunk ? batch - c0 : p->chunk;
+        rc = launch_radon_normal_chunk(p, x + c0 * ni, x_out + c0 * ni, nb, nullptr, nullptr, nullptr, s);
+        if (rc) return rc;
+    }
+    return TC_OK;
+}
+
 int mbir_grad(tc_plan *p, const float *x, const float *b, const float *w,
               const tc_prior *prior, float *grad, double *obj, int batch, void *stream) {
     if (!p || batch < 0 || check_prior(prior)) return TC_ERR_INVALID_ARG;
@@ -266,8 +313,10 @@ struct HostOut {
 // x holds x_k and gb is the gradient buffer; on return x holds x_{k+1}.
 int last_iteration_streamed(tc_plan *p, const float *b, const float *w, float *x, float *gb, int batch,
                             const tc_prior *prior, const tc_solve_opts *opts, tc_solve_state *st,
-                            cudaStream_t s, const cudaEvent_t *ready, const HostOut &out) {
-    TC_CUDA(cudaMemsetAsync(p->scal + SC_DATA, 0, 2 * sizeof(double), s));
+                            cudaStream_t s, const cudaEvent_t *ready, const HostOut &out,
+                            const float *atb) {
+    int rc0 = data_init(p, atb, s);
+    if (rc0) return rc0;
     const size_t ni = img_elems(p), ns = sino_elems(p);
     const int nslab = (batch + p->chunk - 1) / p->chunk;
     auto finish = [&](int j) -> int {
@@ -288,9 +337,8 @@ int last_iteration_streamed(tc_plan *p, const float *b, const float *w, float *x
     for (int c = 0; c < nslab; ++c) {
         const int c0 = c * p->chunk, nb = batch - c0 < p->chunk ? batch - c0 : p->chunk;
         if (ready) TC_CUDA(cudaStreamWaitEvent(s, ready[c], 0));
-        int rc = launch_radon_fwd_chunk(p, st->z + c0 * ni, nullptr, nb, b + c0 * ns,
-                                        w ? w + c0 * ns : nullptr, p->sr, p->scal + SC_DATA, s);
-        if (!rc) rc = launch_radon_adj_chunk(p, p->sr, gb + c0 * ni, nb, s);
+        int rc = data_grad_chunk(p, st->z + c0 * ni, b + c0 * ns, w ? w + c0 * ns : nullptr, gb + c0 * ni, nb,
+                                 atb ? atb + c0 * ni : nullptr, true, s);
         if (!rc && c > 0) rc = finish(c - 1);  // slab c holds the upper halo of slab c - 1
         if (rc) return rc;
     }
@@ -312,6 +360,20 @@ int solve_loop(tc_plan *p, const float *b, const float *w, float *x, int batch,
         if ((rc = launch_fill_scalars_fresh(p, st->t, (double)st->k, (double)st->n_restarts,
                                             opts->step, s)))
             return rc;
+    }
+    const float *atb = nullptr;
+    if (opts->normal) {
+        // A^T b and ||b||^2 once per call; the chunks wait for their slabs here
+        if ((rc = normal_prepare(p, s))) return rc;
+        const size_t ns = sino_elems(p), ni = img_elems(p);
+        for (int c0 = 0; c0 < batch; c0 += p->chunk) {
+            const int nb = batch - c0 < p->chunk ? batch - c0 : p->chunk;
+            if (ready) TC_CUDA(cudaStreamWaitEvent(s, ready[c0 / p->chunk], 0));
+            if ((rc = launch_radon_adj_chunk(p, b + c0 * ns, st->atb + c0 * ni, nb, s))) return rc;
+        }
+        if ((rc = launch_dot(p, b, b, ns * batch, p->scal + SC_BB, s))) return rc;
+        atb = st->atb;
+        ready = nullptr;
     }
     if (opts->restart == 2) {
         // Monotone variant.  Phi(x_k) is recomputed at the start of every call
@@ -340,14 +402,14 @@ int solve_loop(tc_plan *p, const float *b, const float *w, float *x, int batch,
         const bool fused = prior && prior->lambda != 0.0;  // dots inside the prior kernel
         if (out && fused && it == opts->n_iter - 1) {
             if ((rc = last_iteration_streamed(p, b, w, xa, xb, batch, prior, opts, st, s,
-                                              it == 0 ? ready : nullptr, *out)))
+                                              it == 0 ? ready : nullptr, *out, atb)))
                 return rc;
             continue;
         }
         // fused: the prior kernel also forms the restart dots and leaves
         // x_{k+1} = z_k - step g in xb; otherwise separate dots and update
         if ((rc = grad_impl(p, st->z, b, w, prior, xb, batch, s, it == opts->n_iter - 1,
-                            it == 0 ? ready : nullptr, fused ? xa : nullptr, opts->step)))
+                            it == 0 ? ready : nullptr, fused ? xa : nullptr, opts->step, atb)))
             return rc;
         if (!fused && (rc = launch_dots_gzx_gg(p, xb, st->z, xa, n, s))) return rc;
         if ((rc = launch_solver_scalar(p, opts->restart, s))) return rc;
@@ -384,9 +446,10 @@ int solve_loop(tc_plan *p, const float *b, const float *w, float *x, int batch,
 int check_solve(tc_plan *p, int batch, const tc_prior *prior, const tc_solve_opts *opts,
                 const tc_solve_state *st) {
     if (!p || !opts || !st || batch < 1 || opts->n_iter < 0 || !(opts->step > 0) ||
-        opts->restart < 0 || opts->restart > 2 || check_prior(prior))
+        opts->restart < 0 || opts->restart > 2 || opts->normal < 0 || opts->normal > 1 || check_prior(prior))
         return TC_ERR_INVALID_ARG;
     if (check_ptrs({st->z, st->g}, {})) return TC_ERR_INVALID_ARG;
+    if (opts->normal && (opts->restart == 2 || check_ptrs({st->atb}, {}))) return TC_ERR_INVALID_ARG;
     return TC_OK;
 }
 
@@ -469,7 +532,7 @@ int mbir_solve(tc_plan *p, const float *b, const float *w, float *x, int batch,
                const tc_prior *prior, const tc_solve_opts *opts, tc_solve_state *st,
                void *stream) {
     if (check_solve(p, batch, prior, opts, st)) return TC_ERR_INVALID_ARG;
-    if (check_ptrs({b, x}, {w})) return TC_ERR_INVALID_ARG;
+    if (check_ptrs({b, x}, {w}) || (opts->normal && w)) return TC_ERR_INVALID_ARG;
     DeviceGuard dg(p->device);
     if (!dg.ok) return TC_ERR_CUDA;
     return solve_loop(p, b, w, x, batch, prior, opts, st, (cudaStream_t)stream, true, nullptr);
@@ -480,7 +543,8 @@ int mbir_solve_host(tc_plan *p, const float *b_host, const float *w_host, float 
                     const tc_prior *prior, const tc_solve_opts *opts,
                     tc_solve_state *st, void *stream) {
     if (check_solve(p, batch, prior, opts, st)) return TC_ERR_INVALID_ARG;
-    if (!b_host || !x_host || (w_host && !dev_w) || check_ptrs({dev_b, dev_x}, {dev_w}))
+    if (!b_host || !x_host || (w_host && !dev_w) || check_ptrs({dev_b, dev_x}, {dev_w}) ||
+        (opts->normal && w_host))
         return TC_ERR_INVALID_ARG;
     DeviceGuard dg(p->device);
     if (!dg.ok) return TC_ERR_CUDA;

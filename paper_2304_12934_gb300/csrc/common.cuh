@@ -82,6 +82,17 @@ struct tc_plan {
     int threads_col, threads_row, threads_det;
     size_t smem_col, smem_row_fwd, smem_row_adj, smem_det;
     size_t smem_col_tma;  // forward column pass with its image strip staged by TMA (0: not used)
+    // normal operator A^T A by Toeplitz-plus-Hankel embedding (normal.cu),
+    // tables built on first use
+    double *cs64;         // [A][2] cos, sin of the angles as given (FP64)
+    double delta;         // rotation-axis offset
+    int nrm_ready;
+    KArgs kn;             // column passes of the embedding: rows 0..N, unit deapodisation
+    float *nrm_t;         // [N+1][2N] T^ / G^2 (rows 1..N-1 doubled), cell layout [t][j], c = 2j + t
+    float2 *nrm_h;        // [N+1][2N] H^ / G^2, same layout
+    float *nrm_one;       // [N] ones
+    float2 *nrm_tu;       // [MB][N+1][N] grid rows when tu holds fewer than N+1 rows (else null)
+    double *nrm_part;     // [MB * N/2] FP64 partials of the fused data term
 };
 
 // Extra shared memory of the TMA forward column pass: 128 bytes of alignment
@@ -176,6 +187,7 @@ enum {
     SC_DATA_X,       // data term at the accepted iterate x_k
     SC_PRIOR_X,      // lambda H(x_k)
     SC_ACCEPT,       // 1: this iteration's candidate was accepted
+    SC_BB,           // 1/2 ||b||^2 of a normal-operator solve
     SC_COUNT = 16
 };
 
@@ -185,6 +197,13 @@ int launch_radon_fwd_chunk(tc_plan *p, const float *x, float *y, int nb,
                            double *obj_acc, cudaStream_t s);
 int launch_radon_adj_chunk(tc_plan *p, const float *y, float *x, int nb,
                            cudaStream_t s);
+// out = A^T A x by the Toeplitz-plus-Hankel embedding (tables from
+// normal_prepare).  With sub: out = A^T A x - sub; with xdot as well,
+// *obj_acc += 1/2 <xdot, out - sub>.
+int launch_radon_normal_chunk(tc_plan *p, const float *x, float *out, int nb, const float *sub,
+                              const float *xdot, double *obj_acc, cudaStream_t s);
+// Builds the embedding's tables once per plan (synchronous on s).
+int normal_prepare(tc_plan *p, cudaStream_t s);
 // g += lambda grad H(x); h_acc (or NULL) = lambda H(x); with dot_x, also
 // scal[SC_DOT_GZX] = <g, x - dot_x>, scal[SC_DOT_GG] = <g, g> of the final g,
 // and g then receives x - step g (the solver's next iterate) instead.

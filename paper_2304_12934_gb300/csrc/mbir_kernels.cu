@@ -360,10 +360,12 @@ __global__ void k_dots_gzx_gg(const float4 *__restrict__ g, const float4 *__rest
     }
 }
 
-__global__ void k_dot(const float4 *__restrict__ a, const float4 *__restrict__ b, size_t n4,
+// n elements; the n % 4 after the last float4 are summed by block 0
+__global__ void k_dot(const float4 *__restrict__ a, const float4 *__restrict__ b, size_t n,
                       double *__restrict__ part) {
     __shared__ double red[32];
     double acc = 0.0;
+    const size_t n4 = n / 4;
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4;
          i += (size_t)gridDim.x * blockDim.x) {
         const float4 u = a[i], v = b[i];
@@ -372,6 +374,10 @@ __global__ void k_dot(const float4 *__restrict__ a, const float4 *__restrict__ b
         d = fmaf(u.z, v.z, d);
         d = fmaf(u.w, v.w, d);
         acc += (double)d;
+    }
+    if (blockIdx.x == 0 && threadIdx.x < n - 4 * n4) {
+        const size_t i = 4 * n4 + threadIdx.x;
+        acc += (double)(reinterpret_cast<const float *>(a)[i] * reinterpret_cast<const float *>(b)[i]);
     }
     const double t = block_sum_f64(acc, red);
     if (threadIdx.x == 0) part[blockIdx.x] = t;
@@ -643,7 +649,7 @@ int launch_dot(tc_plan *p, const float *a, const float *b, size_t n,
     double *part = p->partials + (size_t)2 * p->slot;
     TC_PROFILED(TCK_DOT, s,
                 k_dot<<<blocks, TC_RED_THREADS, 0, s>>>(reinterpret_cast<const float4 *>(a),
-                                            reinterpret_cast<const float4 *>(b), n4, part));
+                                            reinterpret_cast<const float4 *>(b), n, part));
     TC_LAUNCHED("k_dot");
     return launch_reduce_finalize(part, blocks, out_acc, 0, 1.0, s);
 }

@@ -207,7 +207,8 @@ void tc_plan_free(tc_plan *p) {
     if (!p) return;
     void *ptrs[] = {p->dea64, p->dea, p->twN, p->twG, p->twD, p->row_off, p->ent, p->rec, p->rec_off,
                     p->tu, p->pv, p->sr, p->partials, p->scal, p->dev_err, p->angle_flip, p->shiftD,
-                    p->chirp, p->bhat, p->twL};
+                    p->chirp, p->bhat, p->twL, p->cs64, p->nrm_t, p->nrm_h, p->nrm_one, p->nrm_tu,
+                    p->nrm_part};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     delete p;
@@ -242,7 +243,7 @@ int tc_plan_build(const tc_geom *geom, int max_batch, tc_plan **out) {
     const int G = k.G;
 
     // angles reduced to [0, pi); a flipped angle uses conj symmetry of real data
-    std::vector<double> th(A);
+    std::vector<double> th(A), cs64(2 * (size_t)A);
     std::vector<unsigned char> flip(A, 0);
     for (int a = 0; a < A; ++a) {
         double t = geom->angles ? geom->angles[a] : a * kPi / A;
@@ -250,6 +251,8 @@ int tc_plan_build(const tc_geom *geom, int max_batch, tc_plan **out) {
             tc_plan_free(p);
             return TC_ERR_INVALID_ARG;
         }
+        cs64[2 * a] = std::cos(t);  // the angle as given (normal-operator tables)
+        cs64[2 * a + 1] = std::sin(t);
         t = std::fmod(t, 2.0 * kPi);
         if (t < 0.0) t += 2.0 * kPi;
         if (t >= kPi) {
@@ -491,7 +494,9 @@ int tc_plan_build(const tc_geom *geom, int max_batch, tc_plan **out) {
     UP(p->chirp, chirp);
     UP(p->bhat, bhat);
     UP(p->twL, twL);
+    UP(p->cs64, cs64);
 #undef UP
+    p->delta = delta;
     k.dea = p->dea;
     k.twN = p->twN;
     k.twG = p->twG;

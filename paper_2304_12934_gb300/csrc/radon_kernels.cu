@@ -354,9 +354,16 @@ __global__ void __launch_bounds__(512) k_adj_row(const float2 *__restrict__ V, f
     }
 }
 
-template <int LOGN>
+// Epilogues of the inverse column pass.
+#define COL_DEAPOD 0  // adjoint: x = Re(.) / (psi(x) psi(y))
+#define COL_PLAIN 1   // normal operator: out = Re(.)
+#define COL_GRAD 2    // normal-operator gradient: out = Re(.) - sub; with xdot, the
+                      // block's FP64 partial of <xdot, out - sub> in part
+
+template <int LOGN, int EPI>
 __global__ void __launch_bounds__(512) k_adj_col(const float2 *__restrict__ U, float *__restrict__ x,
-                          const KArgs g, int CP) {
+                          const KArgs g, int CP, const float *__restrict__ sub,
+                          const float *__restrict__ xdot, double *__restrict__ part) {
     extern __shared__ float2 sm[];  // 2CP transforms (stride ts)
     constexpr int N = 1 << LOGN, G = 2 * N, ts = fft_tstride(N);
     const int b = blockIdx.y;
@@ -381,19 +388,93 @@ __global__ void __launch_bounds__(512) k_adj_col(const float2 *__restrict__ U, f
     }
     __syncthreads();
     fft_ct<+1, LOGN>(sm, 2 * CP, g.twN);
-    float *xb = x + (size_t)b * N * N;
+    const size_t sb = (size_t)b * N * N;
     // blockDim.x is a multiple of CP, so a thread keeps its column pair
     const int pp = threadIdx.x % CP, xc = x0base + 2 * pp;
-    const float dx0 = g.dea[xc], dx1 = g.dea[xc + 1];
+    float dx0 = 1.f, dx1 = 1.f;
+    if constexpr (EPI == COL_DEAPOD) {
+        dx0 = g.dea[xc];
+        dx1 = g.dea[xc + 1];
+    }
+    double acc = 0.0;
 #pragma unroll 4
     for (int idx = threadIdx.x; idx < N * CP; idx += blockDim.x) {
         const int iy = idx / CP;
         const int q = (iy - N / 2) & (N - 1);
         const float2 v = cadd(sm[(pp * 2) * ts + spad(q)],
                               cmul(sm[(pp * 2 + 1) * ts + spad(q)], cconj(g.twG[iy])));
-        const float dy = g.dea[iy];
-        *reinterpret_cast<float2 *>(xb + (size_t)iy * N + xc) =
-            make_float2(v.x * dx0 * dy, v.y * dx1 * dy);
+        const size_t off = sb + (size_t)iy * N + xc;
+        float2 o = v;
+        if constexpr (EPI == COL_DEAPOD) {
+            const float dy = g.dea[iy];
+            o = make_float2(v.x * dx0 * dy, v.y * dx1 * dy);
+        }
+        if constexpr (EPI == COL_GRAD) {
+            const float2 r = *reinterpret_cast<const float2 *>(sub + off);
+            o = make_float2(v.x - r.x, v.y - r.y);
+            if (xdot) {
+                const float2 xv = *reinterpret_cast<const float2 *>(xdot + off);
+                acc += (double)fmaf(xv.y, o.y - r.y, xv.x * (o.x - r.x));
+            }
+        }
+        *reinterpret_cast<float2 *>(x + off) = o;
+    }
+    if constexpr (EPI == COL_GRAD) {
+        if (xdot) {  // uniform over the grid
+            __shared__ double red[32];
+            const double tot = block_sum_f64(acc, red);
+            if (threadIdx.x == 0) part[(size_t)blockIdx.y * gridDim.x + blockIdx.x] = tot;
+        }
+    }
+}
+
+// Row pass of the normal operator A^T A on the 2N-periodic grid (Toeplitz
+// plus Hankel embedding; the derivation is in normal.cu).  One grid row ky of
+// the column spectra per CTA, in place: FFT_G along x (G outputs from the N
+// non-zero inputs, as two N-point FFTs), the embedded kernels applied as
+// Y = T^ F + H^ conj(F) (the image is real, so F(-k) = conj F(k)), and the
+// inverse FFT_G evaluated at the N image columns.
+template <int LOGN>
+__global__ void __launch_bounds__(512) k_nrm_row(float2 *__restrict__ U, const float *__restrict__ tt,
+                          const float2 *__restrict__ th, const KArgs g) {
+    extern __shared__ float2 sm[];  // 2 transforms (stride ts)
+    constexpr int N = 1 << LOGN, ts = fft_tstride(N);
+    const int r = blockIdx.x, b = blockIdx.y;
+    float2 *Ur = U + ((size_t)b * g.R + r) * N;
+#pragma unroll 8
+    for (int ix = threadIdx.x; ix < N; ix += blockDim.x) {
+        const float2 v = Ur[ix];
+        const int q = (ix - N / 2) & (N - 1);
+        sm[spad(q)] = v;
+        sm[ts + spad(q)] = cmul(v, g.twG[ix]);
+    }
+    __syncthreads();
+    fft_ct<-1, LOGN>(sm, 2, g.twN);
+    // cell c = 2j + t of the row sits in transform t at j; the tables use the same order
+    const float *tr = tt + (size_t)r * 2 * N;
+    const float2 *hr = th + (size_t)r * 2 * N;
+#pragma unroll 4
+    for (int i = threadIdx.x; i < 2 * N; i += blockDim.x) {
+        float2 &z = sm[(i >> LOGN) * ts + spad(i & (N - 1))];
+        const float2 f = z, h = hr[i];
+        const float t = tr[i];
+        z = make_float2(fmaf(t, f.x, fmaf(h.x, f.x, h.y * f.y)), fmaf(t, f.y, fmaf(h.y, f.x, -h.x * f.y)));
+    }
+    __syncthreads();
+    if constexpr (LOGN % 4 == 3) {
+        if (blockDim.x == N / 8) {  // the last FFT stage writes the row directly
+            fft_ct_pair_emit<+1, LOGN>(sm, g.twN, [&](int q, float2 x0, float2 x1) {
+                const int ix = (q + N / 2) & (N - 1);
+                Ur[ix] = cadd(x0, cmul(x1, cconj(g.twG[ix])));
+            });
+            return;
+        }
+    }
+    fft_ct<+1, LOGN>(sm, 2, g.twN);
+#pragma unroll 4
+    for (int ix = threadIdx.x; ix < N; ix += blockDim.x) {
+        const int q = (ix - N / 2) & (N - 1);
+        Ur[ix] = cadd(sm[spad(q)], cmul(sm[ts + spad(q)], cconj(g.twG[ix])));
     }
 }
 
@@ -495,8 +576,44 @@ int launch_radon_adj_chunk(tc_plan *p, const float *y, float *x, int nb,
         constexpr int LG = decltype(L)::value;
         TC_PROFILED(TCK_ADJ_ROW, s, k_adj_row<LG><<<gr, p->threads_row, p->smem_row_adj, s>>>(p->pv, p->tu, g));
         TC_LAUNCHED("k_adj_row");
-        TC_PROFILED(TCK_ADJ_COL, s, k_adj_col<LG><<<gc, p->threads_col, p->smem_col, s>>>(p->tu, x, g, p->cp_col));
+        TC_PROFILED(TCK_ADJ_COL, s, k_adj_col<LG, COL_DEAPOD><<<gc, p->threads_col, p->smem_col, s>>>(
+                                        p->tu, x, g, p->cp_col, nullptr, nullptr, nullptr));
         TC_LAUNCHED("k_adj_col");
+        return TC_OK;
+    });
+}
+
+int launch_radon_normal_chunk(tc_plan *p, const float *x, float *out, int nb, const float *sub,
+                              const float *xdot, double *obj_acc, cudaStream_t s) {
+    const KArgs &kn = p->kn;
+    float2 *tu = p->nrm_tu ? p->nrm_tu : p->tu;
+    dim3 gc(kn.N / (2 * p->cp_col), nb);
+    dim3 gr(kn.R, nb);
+    CUtensorMap tmx;
+    std::memset(&tmx, 0, sizeof(tmx));
+    const bool use_tma = p->smem_col_tma > 0 &&
+                         tma_encode_f32_3d(&tmx, x, kn.N, kn.N, nb, 2 * p->cp_col, kn.N < 256 ? kn.N : 256) == TC_OK;
+    const bool dot = sub && xdot && obj_acc;
+    return with_logn(kn.log2N, [&](auto L) {
+        constexpr int LG = decltype(L)::value;
+        if (use_tma)
+            TC_PROFILED(TCK_NRM_COL_FWD, s, k_fwd_col<LG, true><<<gc, p->threads_col, p->smem_col_tma, s>>>(
+                                                x, tu, kn, p->cp_col, tmx, p->dev_err));
+        else
+            TC_PROFILED(TCK_NRM_COL_FWD, s, k_fwd_col<LG, false><<<gc, p->threads_col, p->smem_col, s>>>(
+                                                x, tu, kn, p->cp_col, tmx, p->dev_err));
+        TC_LAUNCHED("k_fwd_col (normal)");
+        TC_PROFILED(TCK_NRM_ROW, s, k_nrm_row<LG><<<gr, p->threads_row, p->smem_row_fwd, s>>>(
+                                        tu, p->nrm_t, p->nrm_h, kn));
+        TC_LAUNCHED("k_nrm_row");
+        if (sub)
+            TC_PROFILED(TCK_NRM_COL_ADJ, s, k_adj_col<LG, COL_GRAD><<<gc, p->threads_col, p->smem_col, s>>>(
+                                                tu, out, kn, p->cp_col, sub, dot ? xdot : nullptr, p->nrm_part));
+        else
+            TC_PROFILED(TCK_NRM_COL_ADJ, s, k_adj_col<LG, COL_PLAIN><<<gc, p->threads_col, p->smem_col, s>>>(
+                                                tu, out, kn, p->cp_col, nullptr, nullptr, nullptr));
+        TC_LAUNCHED("k_adj_col (normal)");
+        if (dot) return launch_reduce_finalize(p->nrm_part, (int)(gc.x * gc.y), obj_acc, 1, 0.5, s);
         return TC_OK;
     });
 }
@@ -524,7 +641,11 @@ int radon_configure_kernels(tc_plan *p) {
     int rc = with_logn(p->k.log2N, [&](auto L) {
         constexpr int LG = decltype(L)::value;
         int e;
-        if ((e = raise_smem_limit(k_fwd_col<LG, false>, col_max)) || (e = raise_smem_limit(k_adj_col<LG>, col_max)) ||
+        if ((e = raise_smem_limit(k_fwd_col<LG, false>, col_max)) ||
+            (e = raise_smem_limit(k_adj_col<LG, COL_DEAPOD>, col_max)) ||
+            (e = raise_smem_limit(k_adj_col<LG, COL_PLAIN>, col_max)) ||
+            (e = raise_smem_limit(k_adj_col<LG, COL_GRAD>, col_max)) ||
+            (e = raise_smem_limit(k_nrm_row<LG>, p->smem_row_fwd)) ||
             (p->smem_col_tma && (e = raise_smem_limit(k_fwd_col<LG, true>, tma_max))) ||
             (e = raise_smem_limit(k_fwd_row<LG>, p->smem_row_fwd)) ||
             (e = raise_smem_limit(k_adj_row<LG>, p->smem_row_adj)))
