@@ -291,6 +291,42 @@ __device__ __forceinline__ void fft_ct(float2 *s, int cnt, const float2 *__restr
     }
 }
 
+// The first (radix-16) stage of fft_ct with map(t, k, v) applied to every
+// input element v = s[t][k] (k in natural order) as it is loaded, so an
+// elementwise product needs no pass of its own over the buffer.  The other
+// stages follow with fft_ct<SIGN, LOGN, 4> (or fft_ct_pair_emit<..., 4>).
+// Requires LOGN >= 4 and blockDim.x >= cnt * n / 16.
+template <int SIGN, int LOGN, class Map>
+__device__ __forceinline__ void fft_ct_first_mapped(float2 *s, int cnt, Map &&map) {
+    static_assert(LOGN >= 4, "the first stage is radix 16");
+    constexpr int R = 16, LOGR = 4, LOGPER = LOGN - LOGR, PER = 1 << LOGPER;
+    constexpr int TS = fft_tstride(1 << LOGN);
+    constexpr int LSTRIDE = PER + PER / 16;
+    const int it = threadIdx.x;
+    const bool act = it < (cnt << LOGPER);
+    const int tr = it >> LOGPER, j = it & (PER - 1);
+    float2 v[R];
+    if (act) {
+        const float2 *src = s + tr * TS;
+        if constexpr (PER % 16 == 0) {
+            const float2 *sj = src + spad(j);
+#pragma unroll
+            for (int q = 0; q < R; ++q) v[q] = map(tr, j + q * PER, sj[q * LSTRIDE]);
+        } else {
+#pragma unroll
+            for (int q = 0; q < R; ++q) v[q] = map(tr, j + q * PER, src[spad(j + q * PER)]);
+        }
+    }
+    __syncthreads();
+    if (act) {
+        dft_reg<SIGN, R>(v);
+        float2 *dst = s + tr * TS + spad(j << LOGR);  // Ns = 1: outputs 16 j .. 16 j + 15
+#pragma unroll
+        for (int q = 0; q < R; ++q) dst[q] = v[q];
+    }
+    __syncthreads();
+}
+
 // A pair of transforms (cnt = 2) of length 2^LOGN, LOGN = 3 (mod 4), run with
 // blockDim.x == n / 8: the last (radix-8) stage then gives each thread one
 // butterfly of each transform at the same index, and instead of storing it

@@ -432,14 +432,19 @@ __global__ void __launch_bounds__(512) k_adj_col(const float2 *__restrict__ U, f
 // plus Hankel embedding; the derivation is in normal.cu).  One grid row ky of
 // the column spectra per CTA, in place: FFT_G along x (G outputs from the N
 // non-zero inputs, as two N-point FFTs), the embedded kernels applied as
-// Y = T^ F + H^ conj(F) (the image is real, so F(-k) = conj F(k)), and the
-// inverse FFT_G evaluated at the N image columns.
+// Y = T^ F + H^ conj(F) (the image is real, so F(-k) = conj F(k)) while the
+// inverse transform's first stage loads F, and the inverse FFT_G evaluated at
+// the N image columns.  The grid runs over slices fastest (blockIdx.x = slice,
+// blockIdx.y = row), so the CTAs in flight share a few table rows in L2.
+// For N = 2048 the row passes run N/8 = 256 threads: four CTAs per SM fit in
+// 64 registers a thread.
 template <int LOGN>
-__global__ void __launch_bounds__(512) k_nrm_row(float2 *__restrict__ U, const float *__restrict__ tt,
+__global__ void __launch_bounds__(LOGN == 11 ? 256 : 512, LOGN == 11 ? 4 : 1)
+    k_nrm_row(float2 *__restrict__ U, const float *__restrict__ tt,
                           const float2 *__restrict__ th, const KArgs g) {
     extern __shared__ float2 sm[];  // 2 transforms (stride ts)
     constexpr int N = 1 << LOGN, ts = fft_tstride(N);
-    const int r = blockIdx.x, b = blockIdx.y;
+    const int b = blockIdx.x, r = blockIdx.y;
     float2 *Ur = U + ((size_t)b * g.R + r) * N;
 #pragma unroll 8
     for (int ix = threadIdx.x; ix < N; ix += blockDim.x) {
@@ -453,24 +458,22 @@ __global__ void __launch_bounds__(512) k_nrm_row(float2 *__restrict__ U, const f
     // cell c = 2j + t of the row sits in transform t at j; the tables use the same order
     const float *tr = tt + (size_t)r * 2 * N;
     const float2 *hr = th + (size_t)r * 2 * N;
-#pragma unroll 4
-    for (int i = threadIdx.x; i < 2 * N; i += blockDim.x) {
-        float2 &z = sm[(i >> LOGN) * ts + spad(i & (N - 1))];
-        const float2 f = z, h = hr[i];
-        const float t = tr[i];
-        z = make_float2(fmaf(t, f.x, fmaf(h.x, f.x, h.y * f.y)), fmaf(t, f.y, fmaf(h.y, f.x, -h.x * f.y)));
-    }
-    __syncthreads();
+    fft_ct_first_mapped<+1, LOGN>(sm, 2, [&](int t, int j, float2 f) {
+        const int i = t * N + j;
+        const float2 h = hr[i];
+        const float a = tr[i];
+        return make_float2(fmaf(a, f.x, fmaf(h.x, f.x, h.y * f.y)), fmaf(a, f.y, fmaf(h.y, f.x, -h.x * f.y)));
+    });
     if constexpr (LOGN % 4 == 3) {
         if (blockDim.x == N / 8) {  // the last FFT stage writes the row directly
-            fft_ct_pair_emit<+1, LOGN>(sm, g.twN, [&](int q, float2 x0, float2 x1) {
+            fft_ct_pair_emit<+1, LOGN, 4>(sm, g.twN, [&](int q, float2 x0, float2 x1) {
                 const int ix = (q + N / 2) & (N - 1);
                 Ur[ix] = cadd(x0, cmul(x1, cconj(g.twG[ix])));
             });
             return;
         }
     }
-    fft_ct<+1, LOGN>(sm, 2, g.twN);
+    fft_ct<+1, LOGN, 4>(sm, 2, g.twN);
 #pragma unroll 4
     for (int ix = threadIdx.x; ix < N; ix += blockDim.x) {
         const int q = (ix - N / 2) & (N - 1);
@@ -588,7 +591,7 @@ int launch_radon_normal_chunk(tc_plan *p, const float *x, float *out, int nb, co
     const KArgs &kn = p->kn;
     float2 *tu = p->nrm_tu ? p->nrm_tu : p->tu;
     dim3 gc(kn.N / (2 * p->cp_col), nb);
-    dim3 gr(kn.R, nb);
+    dim3 gr(nb, kn.R);  // slices fastest: the CTAs in flight share table rows
     CUtensorMap tmx;
     std::memset(&tmx, 0, sizeof(tmx));
     const bool use_tma = p->smem_col_tma > 0 &&
