@@ -370,8 +370,11 @@ __global__ void __launch_bounds__(512) k_adj_col(const float2 *__restrict__ U, f
     const int x0base = blockIdx.x * CP * 2;
     const float2 *Ub = U + (size_t)b * g.R * N;
     const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll 8
-    for (int idx = threadIdx.x; idx < G * CP; idx += blockDim.x) {
+    // cells jy and G - jy (jy = 0..N) come from the same two grid rows: one
+    // pair of loads gives both (the second cell's Hermitian parts are the
+    // conjugates of the first's)
+#pragma unroll 4
+    for (int idx = threadIdx.x; idx < (N + 1) * CP; idx += blockDim.x) {
         const int pp = idx % CP, jy = idx / CP;
         const int xc = x0base + 2 * pp;
         const int jn = (G - jy) & (G - 1);
@@ -385,6 +388,7 @@ __global__ void __launch_bounds__(512) k_adj_col(const float2 *__restrict__ U, f
         const float h0x = 0.5f * (up.x + un.x), h0y = 0.5f * (up.y - un.y);
         const float h1x = 0.5f * (up.z + un.z), h1y = 0.5f * (up.w - un.w);
         sm[cell_slot(pp * 2, ts, jy)] = make_float2(h0x - h1y, h0y + h1x);
+        if (jn != jy) sm[cell_slot(pp * 2, ts, jn)] = make_float2(h0x + h1y, h1x - h0y);
     }
     __syncthreads();
     fft_ct<+1, LOGN>(sm, 2 * CP, g.twN);
