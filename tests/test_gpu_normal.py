@@ -146,6 +146,25 @@ def test_normal_solve_matches_oracle_and_gridded(api, dims):
     assert abs(st.obj[1] - sg.obj[1]) <= 1e-4 * sg.obj[1]
 
 
+@pytest.mark.parametrize("restart", [True, False])
+def test_normal_solve_without_prior(api, restart):
+    """No prior: the solver takes the separate restart-dot and update kernels."""
+    B = 2
+    b = _data(B)
+    step = _step(0.0)
+    xo, log = oracle.mbir_solve(b, None, N, 15, step, lam=0.0, dims=2, restart=restart, return_log=True)
+    with api.Plan(N, A, D, max_batch=2) as plan:
+        x = torch.zeros((B, N, N), device="cuda:0")
+        st = api.mbir_solve(plan, t32(b), None, x, 15, step, None, restart=restart, normal=True)
+        xg = torch.zeros((B, N, N), device="cuda:0")
+        sg = api.mbir_solve(plan, t32(b), None, xg, 15, step, None, restart=restart)
+    assert st.k == 15 and st.obj[1] == 0.0
+    assert st.n_restarts == sum(e["restart"] for e in log)
+    assert rel(np64(x), xo) <= 1e-3
+    assert rel(np64(x), np64(xg)) <= 1e-4
+    assert abs(st.obj[0] - sg.obj[0]) <= 2e-6 * 0.5 * float(np.sum(b * b))
+
+
 def test_normal_solve_resume_equals_uninterrupted_bitwise(api):
     b = _data(2)
     step = _step(1e-3)
