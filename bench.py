@@ -52,6 +52,8 @@ def parse():
                     help="slices of the unweighted 1024^2 solve comparing the Toeplitz-plus-Hankel "
                          "normal operator with the gridded operators (0: skip)")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--power-iter", type=int, default=30,
+                    help="power iterations of the library-derived step (first, untimed call)")
     ap.add_argument("--uneven-slices", type=int, default=512,
                     help="slices of the uneven-size batching measurement (0 skips it)")
     ap.add_argument("--cpu-angles", type=int, default=16,
@@ -339,8 +341,11 @@ def normal_operator(api, synth, dev, n_slices, iters=3):
         t0 = time.perf_counter()
         plan.prepare_normal()
         out["prepare_s"] = round(time.perf_counter() - t0, 3)
-        v = torch.tensor(synth.random_start((4, N, N), 17), dtype=torch.float32, device=dev)
-        step = 1.0 / (1.05 * api.mbir_power_norm(plan, v, None, n_iter=15) + api.prior_lipschitz(prior))
+        x0 = torch.zeros((n_slices, N, N), device=dev)
+        st0 = api.SolveState(x0)
+        api.mbir_solve(plan, b, None, x0, 0, None, prior, state=st0, power_iter=15)
+        step = st0.step
+        del st0, x0
         xs, prof = {}, {}
         for mode in (False, True):
             x = torch.zeros((n_slices, N, N), device=dev)
@@ -421,17 +426,16 @@ def run_ours(args):
     prior = api.Prior(lam=1e-2, dims=3)
     plan = api.Plan(N, A, D, max_batch=MB, device=dev)
 
-    # step size: power iteration on 4 slices (the normal operator is block
-    # diagonal over slices) plus the prior curvature bound
-    v = torch.tensor(synth.random_start((4, N, N), seed + 2), dtype=torch.float32, device=dev)
-    lam_max = api.mbir_power_norm(plan, v, wgt[:4].contiguous(), n_iter=15)
-    step = 1.0 / (1.05 * lam_max + api.prior_lipschitz(prior))
-    del v
-
     x = torch.zeros((B, N, N), device=dev)
     st = api.SolveState(x)
 
-    # ---- warm-up
+    # ---- warm-up; the first call derives the step inside the library (power
+    # iteration over the whole volume plus the prior's curvature bound)
+    t_step = time.perf_counter()
+    api.mbir_solve(plan, b, wgt, x, 0, None, prior, state=st, power_iter=args.power_iter)
+    torch.cuda.synchronize()
+    t_step = time.perf_counter() - t_step
+    step = st.step
     api.mbir_solve(plan, b, wgt, x, args.warmup, step, prior, state=st)
     torch.cuda.synchronize()
 
@@ -557,7 +561,8 @@ def run_ours(args):
                 "e2e": e2e, "cpu_baseline": cpu, "gpu_launches": int(gpu_launches),
                 "uneven_batch": uneven, "normal_operator": normal,
                 "clocks": clk.summary(), "solver": {"step": step, "restarts": st.n_restarts,
-                                                    "obj": list(st.obj)}}
+                                                    "obj": list(st.obj),
+                                                    "step_derivation_s": round(t_step, 2)}}
         print(json.dumps(line), flush=True)
     plan.close()
     if ws > 1:

@@ -205,14 +205,28 @@ int mbir_power_norm(tc_plan *plan, const float *w, float *v, float *work,
  * FP64 on the device; no host round trip inside the loop. */
 typedef struct {
     int n_iter;      /* iterations to run in this call (>= 0) */
-    double step;     /* constant step, 1/L with L >= ||A^T W A|| + lambda * 8/(sigma^2 c) */
+    double step;     /* > 0: the constant step 1/L, with L >= ||A^T W A|| + lambda * 8/(sigma^2 c).
+                        <= 0: the library derives it (reading of Sec. 3: a constant step 1/L):
+                        L = 1.05 lambda_max + lambda * 8 / (sigma^2 c), lambda_max the largest
+                        eigenvalue of A^T W A by power_iter power iterations over the whole batch
+                        from a seeded start (FP64 norms on the device), the prior term the bound
+                        4 max rho'' = 8 / (sigma^2 c) on the Hessian of H with unit-sum weights.
+                        The derivation runs when state->k == 0, using state->z and state->g as
+                        its work vectors before the iteration starts, and the step is returned
+                        in state->step; a resumed call (state->k > 0) with step <= 0 reuses
+                        state->step (TC_ERR_INVALID_ARG when that is not > 0). */
     int restart;     /* 0, 1 or 2 as above; anything else is TC_ERR_INVALID_ARG */
     int normal;      /* 1: unweighted data term (w must be NULL) through radon_normal's
                         embedding: grad = A^T A z - A^T b, with A^T b (in state->atb)
                         and ||b||^2 formed once per call.  Restart 0 or 1 only; the
                         reported data term 1/2 <z, A^T A z> - <z, A^T b> + 1/2 ||b||^2
-                        loses relative precision as the residual vanishes.  0: the
-                        gridded operators. */
+                        loses relative precision as the residual vanishes.  The first
+                        normal-mode call builds the embedding's tables (allocating and
+                        synchronising): call tc_plan_prepare_normal before capturing a
+                        normal-mode solve into a CUDA graph (inside a capture the
+                        unprepared call returns TC_ERR_UNSUPPORTED).  0: the gridded
+                        operators. */
+    int power_iter;  /* power iterations of a derived step (0: 30) */
 } tc_solve_opts;
 
 /* Solver state; resuming with the same state continues the iteration exactly.
@@ -233,6 +247,13 @@ typedef struct {
     int n_restarts;
     double obj[2];
     float *atb;
+    double step;     /* the step the iteration used (set on return; input for a resumed
+                        call whose opts->step <= 0) */
+    double dots[2];  /* set on return (restart 0 or 1; 0 for restart 2): the inner products
+                        of the last iteration's restart test, <grad Phi(z_k), z_k - x_k> and
+                        <grad Phi(z_k), grad Phi(z_k)>, reduced on the device from the FP32
+                        vectors with error-free products and compensated sums (as exact as
+                        an FP64 reduction of the same vectors) */
 } tc_solve_state;
 
 /* Run opts->n_iter iterations on device buffers.
@@ -254,6 +275,38 @@ int mbir_solve_host(tc_plan *plan, const float *b_host, const float *w_host,
                     float *x_host, float *dev_b, float *dev_w, float *dev_x,
                     int batch, const tc_prior *prior, const tc_solve_opts *opts,
                     tc_solve_state *state, void *stream);
+
+/* --------------------------------------------------------- checkpoints --- */
+/* Solver checkpoint on storage (no counterpart in the paper, whose solver
+ * state lives in host memory between partitions, Sec. 4; it lets a long solve
+ * stop and resume in another process).  One file: a one-line JSON header
+ * (ASCII, ending in a newline) naming the format, the geometry (n, n_angles,
+ * n_det), batch, the scalar state (k, t, n_restarts, step, obj, each double
+ * printed with 17 significant digits, which round-trips exactly), followed by
+ * the raw float32 arrays x then z, [batch][N][N] each, in the host's byte
+ * order (little-endian on the supported machines).
+ *   tc_checkpoint_save: x (DEVICE) and state->z are copied to the host in
+ *     bounded chunks and written to `path` (created or truncated).
+ *   tc_checkpoint_load: reads `path` back into x and state->z (DEVICE) and the
+ *     scalar fields of state; the header must match the plan's geometry and
+ *     batch, else TC_ERR_INVALID_ARG (checked before any device copy).
+ * A solve resumed from a loaded checkpoint continues exactly as the
+ * uninterrupted solve would (state->g and state->atb are scratch at the start
+ * of every call).  Both synchronise `stream`.  Host I/O failures return
+ * TC_ERR_INVALID_ARG (unreadable or malformed file) or TC_ERR_CUDA. */
+int tc_checkpoint_save(const char *path, const tc_plan *plan, const float *x, int batch,
+                       const tc_solve_state *state, void *stream);
+int tc_checkpoint_load(const char *path, const tc_plan *plan, float *x, int batch,
+                       tc_solve_state *state, void *stream);
+
+/* --------------------------------------------------------- testing hooks -- */
+/* Failure injection on the host (for tests of the error paths; no GPU fault
+ * is involved).  After `after` more host-to-device or device-to-host copies
+ * issued by mbir_solve_host, the next one is not issued and reports a CUDA
+ * failure instead, as if cudaMemcpyAsync had returned an error; the call then
+ * waits for the copies already in flight and returns TC_ERR_CUDA.  A negative
+ * value switches injection off (the default).  Process wide. */
+int tc_test_fail_copy_after(int after);
 
 /* ------------------------------------------------------------ profiling --- */
 /* Per-kernel device timing with CUDA events (no counterpart in the paper; it
@@ -301,8 +354,11 @@ int tc_selftest_wait_timeout(void *stream);
  * as the prior inside mbir_grad):
  *   grad += lambda * grad H(x)       (accumulated into the caller's grad)
  *   *h_out = lambda * H(x)           (h_out: DEVICE pointer to one double, or NULL)
- *   x, grad  DEVICE float32 [batch][n][n], 16-byte aligned, caller-owned
- *   1 <= n <= 4096, batch >= 1; anything larger returns TC_ERR_INVALID_ARG.
+ *   x, grad  DEVICE float32 [batch][n][n], 16-byte aligned, caller-owned;
+ *            they must not overlap (the kernel writes grad at one slice while
+ *            other blocks still read x at the slices above and below), else
+ *            TC_ERR_INVALID_ARG
+ *   1 <= n <= 4096, 1 <= batch <= 65535; anything else returns TC_ERR_INVALID_ARG.
  * Scratch: the per-block FP64 partial sums live in a fixed array of 65536
  * doubles (512 KiB) declared at file scope in the library's device code; every
  * GPU that loads the library holds it until the process exits.  The first call
@@ -312,7 +368,8 @@ int tc_selftest_wait_timeout(void *stream);
  * overwrites the part it uses (nothing has to start at zero), so calls that
  * overlap on the GPU (concurrent streams) race and must be serialised.
  * Asynchronous on `stream`; calls no cudaMalloc, cudaFree or allocating
- * library routine. */
+ * library routine, and records no profiler events (tc_profile_enable does not
+ * apply to it: its launches are counted by tc_launch_count only). */
 int tc_prior_grad_noalloc(const float *x, float *grad, int n, int batch,
                           const tc_prior *prior, double *h_out, void *stream);
 

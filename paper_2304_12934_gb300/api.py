@@ -42,13 +42,14 @@ class _Prior(ctypes.Structure):
 
 class _SolveOpts(ctypes.Structure):
     _fields_ = [("n_iter", ctypes.c_int), ("step", ctypes.c_double), ("restart", ctypes.c_int),
-                ("normal", ctypes.c_int)]
+                ("normal", ctypes.c_int), ("power_iter", ctypes.c_int)]
 
 
 class _SolveState(ctypes.Structure):
     _fields_ = [("z", ctypes.c_void_p), ("g", ctypes.c_void_p), ("t", ctypes.c_double),
                 ("k", ctypes.c_int), ("n_restarts", ctypes.c_int),
-                ("obj", ctypes.c_double * 2), ("atb", ctypes.c_void_p)]
+                ("obj", ctypes.c_double * 2), ("atb", ctypes.c_void_p), ("step", ctypes.c_double),
+                ("dots", ctypes.c_double * 2)]
 
 
 # every symbol the C header declares
@@ -57,7 +58,8 @@ SYMBOLS = ("tc_status_string", "tc_last_error_detail", "tc_plan_create", "tc_pla
            "mbir_power_norm", "mbir_solve", "mbir_solve_host", "tc_profile_enable",
            "tc_profile_collect", "tc_profile_kernel_name", "tc_launch_count",
            "tc_plan_autotune", "tc_plan_set_launch", "tc_prior_grad_noalloc",
-           "tc_plan_status", "tc_selftest_wait_timeout", "radon_normal", "tc_plan_prepare_normal")
+           "tc_plan_status", "tc_selftest_wait_timeout", "radon_normal", "tc_plan_prepare_normal",
+           "tc_checkpoint_save", "tc_checkpoint_load", "tc_test_fail_copy_after")
 
 
 def lib_path() -> str:
@@ -106,10 +108,14 @@ def load(build_if_missing: bool = True):
     L.tc_selftest_wait_timeout.argtypes = [vp]
     L.radon_normal.argtypes = [vp, vp, vp, i, vp]
     L.tc_plan_prepare_normal.argtypes = [vp, vp]
+    L.tc_checkpoint_save.argtypes = [ctypes.c_char_p, vp, vp, i, ctypes.POINTER(_SolveState), vp]
+    L.tc_checkpoint_load.argtypes = [ctypes.c_char_p, vp, vp, i, ctypes.POINTER(_SolveState), vp]
+    L.tc_test_fail_copy_after.argtypes = [i]
     for fn in ("tc_profile_enable", "tc_profile_collect", "tc_plan_create", "tc_plan_destroy",
                "radon_fwd", "radon_adj", "mbir_grad", "mbir_power_norm", "mbir_solve",
                "mbir_solve_host", "tc_plan_autotune", "tc_plan_set_launch",
-               "tc_prior_grad_noalloc", "radon_normal", "tc_plan_prepare_normal"):
+               "tc_prior_grad_noalloc", "radon_normal", "tc_plan_prepare_normal",
+               "tc_checkpoint_save", "tc_checkpoint_load", "tc_test_fail_copy_after"):
         getattr(L, fn).restype = i
     _LIB = L
     return L
@@ -316,13 +322,11 @@ def mbir_power_norm(plan: Plan, v, w=None, n_iter=30, work=None, stream=None) ->
     return lam.value
 
 
-def prior_lipschitz(prior: Prior) -> float:
-    """8 lam / (sigma^2 c): bound on the curvature of lam H (largest at zero difference)."""
-    return 8.0 * prior.lam / (prior.sigma ** 2 * prior.c)
-
-
 class SolveState:
-    """Resumable solver state: device z, g buffers plus FP64 scalars."""
+    """Resumable solver state: device z, g buffers plus FP64 scalars.
+
+    step: the step the iteration used (the caller's, or the one the library
+    derived on the first call when none was given)."""
 
     def __init__(self, x):
         self.z = torch.empty_like(x)
@@ -332,16 +336,21 @@ class SolveState:
         self.n_restarts = 0
         self.obj = (0.0, 0.0)
         self.atb = None  # A^T b, allocated by a normal-operator solve
+        self.step = 0.0
+        self.dots = (0.0, 0.0)  # restart-test inner products of the last iteration
 
     def _c(self):
         s = _SolveState(self.z.data_ptr(), self.g.data_ptr(), self.t, self.k, self.n_restarts)
         s.obj[0], s.obj[1] = self.obj
         s.atb = self.atb.data_ptr() if self.atb is not None else None
+        s.step = self.step
         return s
 
     def _load(self, s):
         self.t, self.k, self.n_restarts = s.t, s.k, s.n_restarts
         self.obj = (s.obj[0], s.obj[1])
+        self.step = s.step
+        self.dots = (s.dots[0], s.dots[1])
 
 
 def _restart_code(restart) -> int:
@@ -353,9 +362,13 @@ def _restart_code(restart) -> int:
     raise ValueError(f"restart must be True, False or 'monotone', not {restart!r}")
 
 
-def mbir_solve(plan: Plan, b, w, x, n_iter, step, prior: Prior | None = None, restart=True,
-               state: SolveState | None = None, stream=None, normal=False) -> SolveState:
+def mbir_solve(plan: Plan, b, w, x, n_iter, step=None, prior: Prior | None = None, restart=True,
+               state: SolveState | None = None, stream=None, normal=False, power_iter=0) -> SolveState:
     """Run n_iter accelerated-gradient iterations on device buffers (x in/out).
+
+    step: the constant step 1/L, or None for the library's own (a power
+    iteration of power_iter steps, 0 = 30, on the first call; state.step then
+    holds it and later calls with the same state reuse it).
 
     restart: True (gradient test), "monotone" (function-value test: Phi(x_k)
     never increases; state.obj is then the objective at the returned x) or
@@ -372,7 +385,8 @@ def mbir_solve(plan: Plan, b, w, x, n_iter, step, prior: Prior | None = None, re
         st.atb = torch.empty_like(x)
     cs = st._c()
     pr = prior._c() if prior is not None else None
-    opts = _SolveOpts(int(n_iter), float(step), _restart_code(restart), int(bool(normal)))
+    opts = _SolveOpts(int(n_iter), 0.0 if step is None else float(step), _restart_code(restart),
+                      int(bool(normal)), int(power_iter))
     _check("mbir_solve", load().mbir_solve(plan.handle, _ptr(b), _ptr(w), _ptr(x), B,
                                            ctypes.byref(pr) if pr is not None else None,
                                            ctypes.byref(opts), ctypes.byref(cs),
@@ -381,8 +395,9 @@ def mbir_solve(plan: Plan, b, w, x, n_iter, step, prior: Prior | None = None, re
     return st
 
 
-def mbir_solve_host(plan: Plan, b_host, w_host, x_host, n_iter, step, prior: Prior | None = None,
-                    restart=True, state: SolveState | None = None, dev=None, stream=None, normal=False):
+def mbir_solve_host(plan: Plan, b_host, w_host, x_host, n_iter, step=None, prior: Prior | None = None,
+                    restart=True, state: SolveState | None = None, dev=None, stream=None, normal=False,
+                    power_iter=0):
     """End-to-end solve from host (ideally pinned) tensors: copies in, iterates, copies x back.
 
     dev: optional dict of reusable device buffers {"b", "w", "x"}.
@@ -403,13 +418,41 @@ def mbir_solve_host(plan: Plan, b_host, w_host, x_host, n_iter, step, prior: Pri
         st.atb = torch.empty_like(dx)
     cs = st._c()
     pr = prior._c() if prior is not None else None
-    opts = _SolveOpts(int(n_iter), float(step), _restart_code(restart), int(bool(normal)))
+    opts = _SolveOpts(int(n_iter), 0.0 if step is None else float(step), _restart_code(restart),
+                      int(bool(normal)), int(power_iter))
     _check("mbir_solve_host", load().mbir_solve_host(
         plan.handle, _ptr(b_host), _ptr(w_host), _ptr(x_host), _ptr(db), _ptr(dw), _ptr(dx), B,
         ctypes.byref(pr) if pr is not None else None, ctypes.byref(opts), ctypes.byref(cs),
         _stream(stream, plan.device)))
     st._load(cs)
     return st
+
+
+def checkpoint_save(path, plan: Plan, x, state: SolveState, stream=None):
+    """Write x, state.z and the scalar state to `path` (tc_checkpoint_save)."""
+    B = x.shape[0]
+    _need(x, plan.image_shape(B), "x", plan.device)
+    cs = state._c()
+    _check("tc_checkpoint_save", load().tc_checkpoint_save(os.fsencode(path), plan.handle, _ptr(x), B,
+                                                           ctypes.byref(cs), _stream(stream, plan.device)))
+
+
+def checkpoint_load(path, plan: Plan, x, state: SolveState | None = None, stream=None) -> SolveState:
+    """Read a checkpoint into x (device, [B,N,N]) and a state (tc_checkpoint_load)."""
+    B = x.shape[0]
+    _need(x, plan.image_shape(B), "x", plan.device)
+    st = state if state is not None else SolveState(x)
+    cs = st._c()
+    _check("tc_checkpoint_load", load().tc_checkpoint_load(os.fsencode(path), plan.handle, _ptr(x), B,
+                                                           ctypes.byref(cs), _stream(stream, plan.device)))
+    st._load(cs)
+    return st
+
+
+def fail_copy_after(after: int):
+    """Testing hook: the copy of mbir_solve_host after `after` more copies
+    reports a CUDA failure instead of running (negative: off)."""
+    _check("tc_test_fail_copy_after", load().tc_test_fail_copy_after(int(after)))
 
 
 def profile_enable(on: bool = True):

@@ -1,6 +1,7 @@
 // C ABI entry points (include/nufft_radon.h): argument checks, chunking of
 // batches larger than the plan's scratch, and the MBIR driver loops.  All
 // compute runs in the kernels of radon_kernels.cu and mbir_kernels.cu.
+#include <atomic>
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
@@ -127,6 +128,51 @@ int take_dev_status(tc_plan *p, cudaStream_t s) {
     return st;
 }
 
+// Power iteration on A^T W A from v (nonzero): v := v/||v||, then n_iter times
+// u = A^T W A v, lambda = <v, u>, v := u/||u|| (FP64 norms and dots on the
+// device).  The last Rayleigh quotient is left in scal[SC_DOT_GZX].
+int power_impl(tc_plan *p, const float *w, float *v, float *work, int batch, int n_iter,
+               cudaStream_t s) {
+    const size_t n = img_elems(p) * batch;
+    int rc;
+    if ((rc = launch_dot(p, v, v, n, p->scal + SC_NORM, s))) return rc;
+    if ((rc = launch_scale_by_inv_sqrt(v, n, p->scal + SC_NORM, s))) return rc;
+    for (int it = 0; it < n_iter; ++it) {
+        if ((rc = grad_impl(p, v, nullptr, w, nullptr, work, batch, s))) return rc;
+        if ((rc = launch_dot(p, v, work, n, p->scal + SC_DOT_GZX, s))) return rc;
+        if ((rc = launch_dot(p, work, work, n, p->scal + SC_NORM, s))) return rc;
+        if ((rc = launch_copy(v, work, n, s))) return rc;
+        if ((rc = launch_scale_by_inv_sqrt(v, n, p->scal + SC_NORM, s))) return rc;
+    }
+    return TC_OK;
+}
+
+// Seed of the derived step's power-iteration start vector.
+constexpr unsigned long long kPowerSeed = 0x230412934ull;
+
+// The step 1/L of the solver (reading of Sec. 3: constant step):
+// L = 1.05 lambda_max(A^T W A) + lambda 8 / (sigma^2 c), lambda_max by n_iter
+// power iterations over the whole batch from a seeded start held in v (work:
+// the second vector).  Synchronises s (the host needs the step).
+int derive_step(tc_plan *p, const float *w, const tc_prior *prior, int batch, int n_iter, float *v,
+                float *work, cudaStream_t s, double *step_out) {
+    const size_t n = img_elems(p) * batch;
+    int rc = launch_fill_start(v, n, kPowerSeed, s);
+    if (!rc) rc = power_impl(p, w, v, work, batch, n_iter, s);
+    if (rc) return rc;
+    double lam = 0.0;
+    TC_CUDA(cudaMemcpyAsync(&lam, p->scal + SC_DOT_GZX, sizeof(double), cudaMemcpyDeviceToHost, s));
+    TC_CUDA(cudaStreamSynchronize(s));
+    double L = 1.05 * lam;
+    if (prior && prior->lambda != 0.0) L += prior->lambda * 8.0 / (prior->sigma * prior->sigma * prior->c);
+    if (!(L > 0.0) || !std::isfinite(L)) {
+        g_detail = "derived step: A^T W A has no positive eigenvalue and there is no prior";
+        return TC_ERR_INVALID_ARG;
+    }
+    *step_out = 1.0 / L;
+    return TC_OK;
+}
+
 int check_prior(const tc_prior *pr) {
     if (!pr) return TC_OK;
     if (!(pr->dims == 2 || pr->dims == 3) || !(pr->sigma > 0) || !(pr->c > 0) ||
@@ -144,6 +190,24 @@ int tc_cuda_fail(cudaError_t e, const char *where) {
         return TC_ERR_OOM;
     }
     return TC_ERR_CUDA;
+}
+
+namespace {
+// copies of the host-streamed solve still allowed before an injected failure
+// (negative: injection off)
+std::atomic<int> g_fail_copy_after{-1};
+}  // namespace
+
+int host_copy_async(void *dst, const void *src, size_t bytes, cudaMemcpyKind kind, cudaStream_t s) {
+    int left = g_fail_copy_after.load();
+    while (left >= 0 && !g_fail_copy_after.compare_exchange_weak(left, left - 1)) {
+    }
+    if (left == 0) {
+        g_detail = "cudaMemcpyAsync: failure injected by tc_test_fail_copy_after";
+        return TC_ERR_CUDA;
+    }
+    TC_CUDA(cudaMemcpyAsync(dst, src, bytes, kind, s));
+    return TC_OK;
 }
 
 extern "C" {
@@ -265,17 +329,8 @@ int mbir_power_norm(tc_plan *p, const float *w, float *v, float *work, int batch
     DeviceGuard dg(p->device);
     if (!dg.ok) return TC_ERR_CUDA;
     cudaStream_t s = (cudaStream_t)stream;
-    const size_t n = img_elems(p) * batch;
-    int rc;
-    if ((rc = launch_dot(p, v, v, n, p->scal + SC_NORM, s))) return rc;
-    if ((rc = launch_scale_by_inv_sqrt(v, n, p->scal + SC_NORM, s))) return rc;
-    for (int it = 0; it < n_iter; ++it) {
-        if ((rc = grad_impl(p, v, nullptr, w, nullptr, work, batch, s))) return rc;
-        if ((rc = launch_dot(p, v, work, n, p->scal + SC_DOT_GZX, s))) return rc;
-        if ((rc = launch_dot(p, work, work, n, p->scal + SC_NORM, s))) return rc;
-        if ((rc = launch_copy(v, work, n, s))) return rc;
-        if ((rc = launch_scale_by_inv_sqrt(v, n, p->scal + SC_NORM, s))) return rc;
-    }
+    int rc = power_impl(p, w, v, work, batch, n_iter, s);
+    if (rc) return rc;
     double lam = 0.0;
     TC_CUDA(cudaMemcpyAsync(&lam, p->scal + SC_DOT_GZX, sizeof(double), cudaMemcpyDeviceToHost, s));
     TC_CUDA(cudaStreamSynchronize(s));
@@ -312,7 +367,7 @@ struct HostOut {
 // result equals the in-place update bit for bit.
 // x holds x_k and gb is the gradient buffer; on return x holds x_{k+1}.
 int last_iteration_streamed(tc_plan *p, const float *b, const float *w, float *x, float *gb, int batch,
-                            const tc_prior *prior, const tc_solve_opts *opts, tc_solve_state *st,
+                            const tc_prior *prior, const tc_solve_opts *opts, double step, tc_solve_state *st,
                             cudaStream_t s, const cudaEvent_t *ready, const HostOut &out,
                             const float *atb) {
     int rc0 = data_init(p, atb, s);
@@ -323,16 +378,15 @@ int last_iteration_streamed(tc_plan *p, const float *b, const float *w, float *x
         const int z0 = j * p->chunk, z1 = z0 + p->chunk < batch ? z0 + p->chunk : batch;
         // the prior kernel leaves x_{k+1} = z - step g of the slab in gb
         int rc = launch_prior_grad(p, st->z, gb, batch, prior, p->scal + SC_PRIOR, s, x, z0, z1,
-                                   opts->step);
+                                   step);
         if (rc) return rc;
         cudaEvent_t e = nullptr;
         TC_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
         out.ev->push_back(e);
         TC_CUDA(cudaEventRecord(e, s));
         TC_CUDA(cudaStreamWaitEvent(out.cs, e, 0));
-        TC_CUDA(cudaMemcpyAsync(out.x_host + z0 * ni, gb + z0 * ni, (size_t)(z1 - z0) * ni * sizeof(float),
-                                cudaMemcpyDeviceToHost, out.cs));
-        return TC_OK;
+        return host_copy_async(out.x_host + z0 * ni, gb + z0 * ni, (size_t)(z1 - z0) * ni * sizeof(float),
+                               cudaMemcpyDeviceToHost, out.cs);
     };
     for (int c = 0; c < nslab; ++c) {
         const int c0 = c * p->chunk, nb = batch - c0 < p->chunk ? batch - c0 : p->chunk;
@@ -353,12 +407,25 @@ int solve_loop(tc_plan *p, const float *b, const float *w, float *x, int batch,
                cudaStream_t s, bool fresh_z, const cudaEvent_t *ready, const HostOut *out = nullptr) {
     const size_t n = img_elems(p) * batch;
     int rc;
+    // the step: given, derived now (fresh solves only: z and g are free), or
+    // the one a previous call derived
+    double step = opts->step;
+    if (!(step > 0.0)) {
+        if (st->k == 0) {
+            const int pit = opts->power_iter > 0 ? opts->power_iter : 30;
+            if ((rc = derive_step(p, opts->normal ? nullptr : w, prior, batch, pit, st->z, st->g, s, &step)))
+                return rc;
+        } else {
+            step = st->step;
+        }
+    }
+    st->step = step;
     if (st->k == 0) {
         if (fresh_z && (rc = launch_copy(st->z, x, n, s))) return rc;
-        if ((rc = launch_fill_scalars_fresh(p, 1.0, 0.0, 0.0, opts->step, s))) return rc;
+        if ((rc = launch_fill_scalars_fresh(p, 1.0, 0.0, 0.0, step, s))) return rc;
     } else {
         if ((rc = launch_fill_scalars_fresh(p, st->t, (double)st->k, (double)st->n_restarts,
-                                            opts->step, s)))
+                                            step, s)))
             return rc;
     }
     const float *atb = nullptr;
@@ -401,7 +468,7 @@ int solve_loop(tc_plan *p, const float *b, const float *w, float *x, int batch,
         // the prior's value H is only reported for the last gradient point
         const bool fused = prior && prior->lambda != 0.0;  // dots inside the prior kernel
         if (out && fused && it == opts->n_iter - 1) {
-            if ((rc = last_iteration_streamed(p, b, w, xa, xb, batch, prior, opts, st, s,
+            if ((rc = last_iteration_streamed(p, b, w, xa, xb, batch, prior, opts, step, st, s,
                                               it == 0 ? ready : nullptr, *out, atb)))
                 return rc;
             continue;
@@ -409,7 +476,7 @@ int solve_loop(tc_plan *p, const float *b, const float *w, float *x, int batch,
         // fused: the prior kernel also forms the restart dots and leaves
         // x_{k+1} = z_k - step g in xb; otherwise separate dots and update
         if ((rc = grad_impl(p, st->z, b, w, prior, xb, batch, s, it == opts->n_iter - 1,
-                            it == 0 ? ready : nullptr, fused ? xa : nullptr, opts->step, atb)))
+                            it == 0 ? ready : nullptr, fused ? xa : nullptr, step, atb)))
             return rc;
         if (!fused && (rc = launch_dots_gzx_gg(p, xb, st->z, xa, n, s))) return rc;
         if ((rc = launch_solver_scalar(p, opts->restart, s))) return rc;
@@ -432,6 +499,8 @@ int solve_loop(tc_plan *p, const float *b, const float *w, float *x, int batch,
     st->t = sc[SC_T];
     st->k = (int)sc[SC_K];
     st->n_restarts = (int)sc[SC_RESTARTS];
+    st->dots[0] = opts->restart == 2 ? 0.0 : sc[SC_DOT_GZX];
+    st->dots[1] = opts->restart == 2 ? 0.0 : sc[SC_DOT_GG];
     if (opts->n_iter > 0 && opts->restart == 2) {  // the objective at the returned x
         st->obj[0] = sc[SC_DATA_X];
         st->obj[1] = sc[SC_PRIOR_X];
@@ -445,7 +514,9 @@ int solve_loop(tc_plan *p, const float *b, const float *w, float *x, int batch,
 
 int check_solve(tc_plan *p, int batch, const tc_prior *prior, const tc_solve_opts *opts,
                 const tc_solve_state *st) {
-    if (!p || !opts || !st || batch < 1 || opts->n_iter < 0 || !(opts->step > 0) ||
+    if (!p || !opts || !st || batch < 1 || opts->n_iter < 0 || std::isnan(opts->step) ||
+        std::isinf(opts->step) || opts->power_iter < 0 ||
+        (!(opts->step > 0) && st->k > 0 && !(st->step > 0)) ||
         opts->restart < 0 || opts->restart > 2 || opts->normal < 0 || opts->normal > 1 || check_prior(prior))
         return TC_ERR_INVALID_ARG;
     if (check_ptrs({st->z, st->g}, {})) return TC_ERR_INVALID_ARG;
@@ -554,46 +625,68 @@ int mbir_solve_host(tc_plan *p, const float *b_host, const float *w_host, float 
     CopyStream cp;
     TC_CUDA(cudaStreamCreateWithFlags(&cp.cs, cudaStreamNonBlocking));
     cp.ev.assign(nslab, nullptr);
-    // the copy stream must not overtake work already queued on the caller's stream
-    cudaEvent_t start = nullptr;
-    TC_CUDA(cudaEventCreateWithFlags(&start, cudaEventDisableTiming));
-    cp.ev.push_back(start);
-    TC_CUDA(cudaEventRecord(start, s));
-    TC_CUDA(cudaStreamWaitEvent(cp.cs, start, 0));
-    // slab c of b, w and x goes in on the copy stream; the first iteration's
-    // chunk c starts once its slab is resident
-    for (int c = 0; c < nslab; ++c) {
-        const size_t s0 = (size_t)c * p->chunk;
-        const size_t nb = (size_t)(batch - (int)s0 < p->chunk ? batch - (int)s0 : p->chunk);
-        TC_CUDA(cudaMemcpyAsync(dev_b + s0 * ns, b_host + s0 * ns, nb * ns * sizeof(float),
-                                cudaMemcpyHostToDevice, cp.cs));
-        if (w_host)
-            TC_CUDA(cudaMemcpyAsync(dev_w + s0 * ns, w_host + s0 * ns, nb * ns * sizeof(float),
-                                    cudaMemcpyHostToDevice, cp.cs));
-        TC_CUDA(cudaMemcpyAsync(dev_x + s0 * ni, x_host + s0 * ni, nb * ni * sizeof(float),
-                                cudaMemcpyHostToDevice, cp.cs));
-        if (st->k == 0)
-            TC_CUDA(cudaMemcpyAsync(st->z + s0 * ni, dev_x + s0 * ni, nb * ni * sizeof(float),
-                                    cudaMemcpyDeviceToDevice, cp.cs));
-        TC_CUDA(cudaEventCreateWithFlags(&cp.ev[c], cudaEventDisableTiming));
-        TC_CUDA(cudaEventRecord(cp.ev[c], cp.cs));
+    // a step still to be derived needs the whole batch resident (and z, g as
+    // its work vectors) before the first iteration
+    const bool derive = st->k == 0 && !(opts->step > 0);
+    auto body = [&]() -> int {
+        // the copy stream must not overtake work already queued on the caller's stream
+        cudaEvent_t start = nullptr;
+        TC_CUDA(cudaEventCreateWithFlags(&start, cudaEventDisableTiming));
+        cp.ev.push_back(start);
+        TC_CUDA(cudaEventRecord(start, s));
+        TC_CUDA(cudaStreamWaitEvent(cp.cs, start, 0));
+        // slab c of b, w and x goes in on the copy stream; the first iteration's
+        // chunk c starts once its slab is resident
+        int rc;
+        for (int c = 0; c < nslab; ++c) {
+            const size_t s0 = (size_t)c * p->chunk;
+            const size_t nb = (size_t)(batch - (int)s0 < p->chunk ? batch - (int)s0 : p->chunk);
+            if ((rc = host_copy_async(dev_b + s0 * ns, b_host + s0 * ns, nb * ns * sizeof(float),
+                                      cudaMemcpyHostToDevice, cp.cs)))
+                return rc;
+            if (w_host && (rc = host_copy_async(dev_w + s0 * ns, w_host + s0 * ns, nb * ns * sizeof(float),
+                                                cudaMemcpyHostToDevice, cp.cs)))
+                return rc;
+            if ((rc = host_copy_async(dev_x + s0 * ni, x_host + s0 * ni, nb * ni * sizeof(float),
+                                      cudaMemcpyHostToDevice, cp.cs)))
+                return rc;
+            if (st->k == 0 && !derive)
+                TC_CUDA(cudaMemcpyAsync(st->z + s0 * ni, dev_x + s0 * ni, nb * ni * sizeof(float),
+                                        cudaMemcpyDeviceToDevice, cp.cs));
+            TC_CUDA(cudaEventCreateWithFlags(&cp.ev[c], cudaEventDisableTiming));
+            TC_CUDA(cudaEventRecord(cp.ev[c], cp.cs));
+        }
+        // the first iteration's chunk c waits for slab c only; the full-volume
+        // kernels that follow the chunk loop then see every slab
+        const bool overlap = opts->n_iter > 0 && !derive;
+        if (!overlap)
+            for (int c = 0; c < nslab; ++c) TC_CUDA(cudaStreamWaitEvent(s, cp.ev[c], 0));
+        // the last gradient-restart iteration with a prior sends x back slab by
+        // slab while it runs; otherwise x goes back after the solve
+        const bool stream_out = opts->n_iter > 0 && opts->restart != 2 && prior && prior->lambda != 0.0;
+        const HostOut out{x_host, cp.cs, &cp.out_ev};
+        rc = solve_loop(p, dev_b, w_host ? dev_w : nullptr, dev_x, batch, prior, opts, st, s, derive,
+                        overlap ? cp.ev.data() : nullptr, stream_out ? &out : nullptr);
+        if (rc) return rc;
+        if (!stream_out &&
+            (rc = host_copy_async(x_host, dev_x, (size_t)batch * ni * sizeof(float), cudaMemcpyDeviceToHost, s)))
+            return rc;
+        TC_CUDA(cudaStreamSynchronize(s));
+        TC_CUDA(cudaStreamSynchronize(cp.cs));
+        return TC_OK;
+    };
+    const int rc = body();
+    if (rc) {
+        // copies already issued still read or write the caller's host buffers:
+        // let them finish before the caller regains those buffers
+        cudaStreamSynchronize(cp.cs);
+        cudaStreamSynchronize(s);
     }
-    // the first iteration's chunk c waits for slab c only; the full-volume
-    // kernels that follow the chunk loop then see every slab
-    const bool overlap = opts->n_iter > 0;
-    if (!overlap)
-        for (int c = 0; c < nslab; ++c) TC_CUDA(cudaStreamWaitEvent(s, cp.ev[c], 0));
-    // the last gradient-restart iteration with a prior sends x back slab by
-    // slab while it runs; otherwise x goes back after the solve
-    const bool stream_out = overlap && opts->restart != 2 && prior && prior->lambda != 0.0;
-    const HostOut out{x_host, cp.cs, &cp.out_ev};
-    int rc = solve_loop(p, dev_b, w_host ? dev_w : nullptr, dev_x, batch, prior, opts, st, s,
-                        false, overlap ? cp.ev.data() : nullptr, stream_out ? &out : nullptr);
-    if (rc) return rc;
-    if (!stream_out)
-        TC_CUDA(cudaMemcpyAsync(x_host, dev_x, (size_t)batch * ni * sizeof(float), cudaMemcpyDeviceToHost, s));
-    TC_CUDA(cudaStreamSynchronize(s));
-    TC_CUDA(cudaStreamSynchronize(cp.cs));
+    return rc;
+}
+
+int tc_test_fail_copy_after(int after) {
+    g_fail_copy_after.store(after < 0 ? -1 : after);
     return TC_OK;
 }
 

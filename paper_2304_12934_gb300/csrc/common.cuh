@@ -238,6 +238,11 @@ int launch_scale_by_inv_sqrt(float *v, size_t n, const double *sq, cudaStream_t 
 int launch_copy(float *dst, const float *src, size_t n, cudaStream_t s);
 int launch_fill_scalars_fresh(tc_plan *p, double t, double k, double restarts,
                               double step, cudaStream_t s);
+// v[i] uniform in [-1, 1) from a counter-based generator (power-iteration start)
+int launch_fill_start(float *v, size_t n, unsigned long long seed, cudaStream_t s);
+// Host-to-device / device-to-host copy of the host-streamed solve, with the
+// failure-injection hook of tc_test_fail_copy_after (api.cu).
+int host_copy_async(void *dst, const void *src, size_t bytes, cudaMemcpyKind kind, cudaStream_t s);
 
 // Error plumbing (api.cu).
 int tc_cuda_fail(cudaError_t e, const char *where);

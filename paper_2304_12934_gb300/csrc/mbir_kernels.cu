@@ -504,6 +504,19 @@ __global__ void k_fill_scalars(double *sc, double t, double k, double restarts, 
     }
 }
 
+// Seeded start vector of the step's power iteration: element i is uniform in
+// [-1, 1), taken from the splitmix64 output (Steele, Lea and Flood 2014) for
+// counter i of the given seed.
+__global__ void k_fill_start(float *__restrict__ v, size_t n, unsigned long long seed) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        unsigned long long z = seed + (i + 1) * 0x9E3779B97F4A7C15ull;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        v[i] = (float)(z >> 40) * (1.0f / 8388608.0f) - 1.0f;  // 24 bits: exact in float
+    }
+}
+
 int grid_for(size_t n4) {
     size_t b = (n4 + TC_RED_THREADS - 1) / TC_RED_THREADS;
     return (int)(b < TC_RED_BLOCKS ? (b ? b : 1) : TC_RED_BLOCKS);
@@ -682,6 +695,12 @@ int launch_scale_by_inv_sqrt(float *v, size_t n, const double *sq, cudaStream_t 
 
 int launch_copy(float *dst, const float *src, size_t n, cudaStream_t s) {
     TC_CUDA(cudaMemcpyAsync(dst, src, n * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    return TC_OK;
+}
+
+int launch_fill_start(float *v, size_t n, unsigned long long seed, cudaStream_t s) {
+    TC_PROFILED(TCK_FILL, s, k_fill_start<<<grid_for(n / 4 + 1), TC_RED_THREADS, 0, s>>>(v, n, seed));
+    TC_LAUNCHED("k_fill_start");
     return TC_OK;
 }
 

@@ -124,6 +124,12 @@ int dev_alloc(void **ptr, size_t bytes, tc_plan *p) {
 
 int normal_prepare(tc_plan *p, cudaStream_t s) {
     if (p->nrm_ready) return TC_OK;
+    // Building the tables allocates and synchronises, which a stream capture
+    // cannot record: refuse before touching the stream, so the capture stays
+    // valid and the caller learns to prepare the plan first.
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    TC_CUDA(cudaStreamIsCapturing(s, &cap));
+    if (cap != cudaStreamCaptureStatusNone) return TC_ERR_UNSUPPORTED;
     const KArgs &k = p->k;
     const int N = k.N, G = 2 * N, logG = k.log2N + 1, R = N + 1;
     const size_t MB = (size_t)p->max_batch;

@@ -52,9 +52,13 @@ int noalloc_scratch(double **out) {
 
 extern "C" int tc_prior_grad_noalloc(const float *x, float *grad, int n, int batch,
                                      const tc_prior *prior, double *h_out, void *stream) {
-    if (!x || !grad || !prior || n < 1 || n > 4096 || batch < 1) return TC_ERR_INVALID_ARG;
+    if (!x || !grad || !prior || n < 1 || n > 4096 || batch < 1 || batch > 65535) return TC_ERR_INVALID_ARG;
     if ((reinterpret_cast<uintptr_t>(x) & 15u) || (reinterpret_cast<uintptr_t>(grad) & 15u))
         return TC_ERR_INVALID_ARG;
+    // grad is written at one slice while other blocks still read x around it
+    const uintptr_t bytes = (uintptr_t)batch * n * n * sizeof(float);
+    const uintptr_t xa = reinterpret_cast<uintptr_t>(x), ga = reinterpret_cast<uintptr_t>(grad);
+    if (xa < ga + bytes && ga < xa + bytes) return TC_ERR_INVALID_ARG;
     if (!(prior->dims == 2 || prior->dims == 3) || !(prior->sigma > 0) || !(prior->c > 0) ||
         !(prior->p >= 1.0 && prior->p <= 2.0) || !(prior->lambda >= 0))
         return TC_ERR_INVALID_ARG;

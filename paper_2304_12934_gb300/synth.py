@@ -243,3 +243,13 @@ def poisson_measurement_torch(p_true, i0: float, seed: int):
     g.manual_seed(seed)
     counts = torch.poisson((i0 * torch.exp(-p_true.double())), generator=g).clamp_(min=1.0)
     return (-torch.log(counts / i0)).float(), (counts / i0).float()
+
+
+# ------------------------------------------------- platform-exact fields ----
+def uniform_field(shape, seed: int, lo: float = 0.0, hi: float = 1.0) -> np.ndarray:
+    """Seeded float32 array, uniform in [lo, hi).  The draw uses only integer
+    generator output and exact scaling (no libm), so it is bit-identical on
+    every platform: stored expected values computed on one machine stay valid
+    on another."""
+    u = np.random.default_rng(seed).random(shape)
+    return (lo + (hi - lo) * u).astype(np.float32)

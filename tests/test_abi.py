@@ -75,3 +75,37 @@ def test_restart_modes_map_to_the_abi_codes():
     assert api._restart_code("monotone") == 2
     with pytest.raises(ValueError):
         api._restart_code("sometimes")
+
+
+def test_checkpoint_reader_rejects_bad_files_before_any_device_work(tmp_path):
+    """A missing file, a foreign format and a truncated header are refused on
+    the host (TC_ERR_INVALID_ARG) before the plan or a device buffer is used."""
+    from paper_2304_12934_gb300 import api
+    L = api.load()
+    fake_plan = ctypes.create_string_buffer(1 << 16)   # never dereferenced on these paths
+    st = api._SolveState()
+    st.z = ctypes.addressof(ctypes.create_string_buffer(64))
+    x = ctypes.create_string_buffer(64)
+    bad = tmp_path / "bad.ckpt"
+    for content in (None, b'{"format": "something-else", "version": 1}\n', b'{"format": "tc-mbir-ch'):
+        if content is not None:
+            bad.write_bytes(content)
+        path = str(bad if content is not None else tmp_path / "missing.ckpt").encode()
+        rc = L.tc_checkpoint_load(path, ctypes.addressof(fake_plan), ctypes.addressof(x), 1,
+                                  ctypes.byref(st), None)
+        assert rc == -1
+    assert L.tc_checkpoint_save(None, None, None, 1, None, None) == -1
+
+
+def test_solver_options_layout_matches_the_header():
+    """The binding's mirror of tc_solve_opts / tc_solve_state has the fields
+    the header declares, in order (a mismatch would shift every field)."""
+    from paper_2304_12934_gb300 import api
+    src = open(os.path.join(ROOT, "include", "nufft_radon.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    for cname, py in (("tc_solve_opts", api._SolveOpts), ("tc_solve_state", api._SolveState),
+                      ("tc_geom", api._Geom), ("tc_prior", api._Prior)):
+        body = re.search(r"typedef struct \{([^}]*)\}\s*" + cname + ";", src).group(1)
+        names = re.findall(r"(\w+)\s*(?:\[\d+\])?\s*;", body)
+        py_names = [f[0] for f in py._fields_]
+        assert [n if n != "lambda" else "lam" for n in names] == py_names, (cname, names, py_names)

@@ -56,3 +56,44 @@ def test_backward_matches_finite_differences_and_oracle(api):
     _, go = oracle.data_grad(xo, b.astype(np.float32).astype(np.float64),
                              w.astype(np.float32).astype(np.float64))
     assert float(np.linalg.norm(g.cpu().numpy() - go) / np.linalg.norm(go)) <= 1e-4
+
+
+def test_backward_at_the_differentiation_workload_size(api):
+    """One slice of the differentiation workload: 1024^2, 360 angles, 1448
+    bins.  The radon_fwd backward (the A^T kernel) against central finite
+    differences (step 1e-3) on 32 seeded directions, and the gradient of
+    1/2 sum W (A x - b)^2 against the FP64 oracle at 512 sampled pixels stored
+    by tests/golden/make_oracle_golden.py (relative L2 over the sample <= 1e-4,
+    as above), with the loss itself within 1e-5."""
+    import make_oracle_golden as mk
+    c = mk.AUTOGRAD
+    N, A, D = c["N"], c["A"], c["D"]
+    ref = np.load(mk.autograd_path())
+    x0, b, w = mk.autograd_inputs()
+    dev = torch.device("cuda:0")
+    bt = torch.tensor(b[None], device=dev)
+    wt = torch.tensor(w[None], device=dev)
+    with api.Plan(N, A, D, max_batch=1) as plan:
+        def loss(xt):
+            y = api.radon(xt, plan)
+            r = (y - bt).double()
+            return 0.5 * (wt.double() * r * r).sum()
+
+        x = torch.tensor(x0[None], device=dev, requires_grad=True)
+        L = loss(x)
+        L.backward()
+        g = x.grad.double()
+        assert abs(float(L) - float(ref["loss"])) <= 1e-5 * float(ref["loss"])
+        gs = g[0].flatten()[torch.as_tensor(ref["pix"], dtype=torch.long, device=dev)].cpu().numpy()
+        err = float(np.linalg.norm(gs - ref["g"]) / np.linalg.norm(ref["g"]))
+        assert err <= 1e-4, err
+        rng = np.random.default_rng(1448)
+        h = 1e-3
+        gn = float(g.norm())
+        with torch.no_grad():
+            for _ in range(32):
+                d = torch.tensor(rng.standard_normal((1, N, N)), dtype=torch.float32, device=dev)
+                d = d / d.norm()
+                fd = (loss(x + h * d) - loss(x - h * d)) / (2 * h)
+                an = (g * d.double()).sum()
+                assert abs(float(fd - an)) <= 1e-3 * gn, (float(fd), float(an))

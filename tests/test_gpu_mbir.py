@@ -279,3 +279,239 @@ def test_monotone_rejects_an_overshooting_step(api):
     assert torch.count_nonzero(x) == 0
     assert abs(st.obj[0] - 0.5 * float(np.sum(b * b))) <= 1e-5 * 0.5 * float(np.sum(b * b))
     assert st.obj[1] == 0.0
+
+
+# --------------------------------------- noisy 512^2 workload (stored oracle) ----
+def test_noisy_512_weighted_solve_matches_oracle(api):
+    """The noisy workload's geometry: one 512^2 slice, 180 angles, 724 bins,
+    Poisson data at I0 = 1e4 with count weights (Sec. 5, b = -log(I/I0)),
+    8-neighbour qGGMRF with lambda = 1e-2, gradient restart.  10 and 50
+    iterations against the FP64 oracle's iterates stored by
+    tests/golden/make_oracle_golden.py (same b, w and step): relative L2
+    <= 1e-3 and the same number of restarts."""
+    import make_oracle_golden as mk
+    c = mk.NOISY
+    ref = np.load(mk.noisy_path())
+    prior = api.Prior(lam=c["lam"], dims=c["dims"])
+    with api.Plan(c["N"], c["A"], c["D"], max_batch=1) as plan:
+        b, w = t32(ref["b"]), t32(ref["w"])
+        for iters, key, rkey in ((10, "x10", "restarts10"), (c["iters"], "x", "restarts")):
+            x = torch.zeros((1, c["N"], c["N"]), device="cuda:0")
+            st = api.mbir_solve(plan, b, w, x, iters, float(ref["step"]), prior)
+            assert st.k == iters
+            assert st.n_restarts == int(ref[rkey])
+            err = rel(np64(x)[0], ref[key].astype(np.float64))
+            assert err <= 1e-3, (iters, err)
+        # the objective terms at the last gradient point z_49 of the 50-iteration solve
+        assert abs(st.obj[0] - float(ref["data"][-1])) <= 1e-4 * float(ref["data"][-1])
+        assert abs(st.obj[1] - float(ref["prior"][-1])) <= 1e-4 * float(ref["prior"][-1])
+
+
+# ------------------------------------------------- step size in the library ----
+def test_library_step_matches_oracle_step(api):
+    """opts.step <= 0: the library derives 1/L, L = 1.05 lambda_max(A^T W A)
+    + lambda 8/(sigma^2 c) (reading of Sec. 3), by power iteration over the
+    batch.  Against the oracle's power iteration from its own start (both
+    converged): relative 1e-5.  The host-streamed solve derives the same step
+    bit for bit, and a resumed call reuses it."""
+    B = 2
+    _, b = _data(B)
+    rng = np.random.default_rng(44)
+    w = rng.uniform(0.3, 1.0, b.shape).astype(np.float32).astype(np.float64)
+    lam = 1e-3
+    prior = api.Prior(lam=lam, dims=3)
+    v0 = synth.random_start((B, N, N), 45)
+    L = 1.05 * oracle.power_norm(N, A, D, w, v0, 60) + lam * oracle.prior_lipschitz(**oracle.PAPER_PRIOR)
+    with api.Plan(N, A, D, max_batch=2) as plan:
+        x = torch.zeros((B, N, N), device="cuda:0")
+        st = api.mbir_solve(plan, t32(b), t32(w), x, 3, None, prior, power_iter=60)
+        assert abs(st.step * L - 1.0) <= 1e-5, st.step * L
+        x2 = torch.zeros((B, N, N), device="cuda:0")
+        s2 = api.mbir_solve(plan, t32(b), t32(w), x2, 3, st.step, prior)
+        assert torch.equal(x, x2)
+        api.mbir_solve(plan, t32(b), t32(w), x, 2, None, prior, state=st)   # resumes with st.step
+        api.mbir_solve(plan, t32(b), t32(w), x2, 2, None, prior, state=s2)
+        assert torch.equal(x, x2)
+        bh = torch.tensor(b, dtype=torch.float32).pin_memory()
+        wh = torch.tensor(w, dtype=torch.float32).pin_memory()
+        xh = torch.zeros((B, N, N), dtype=torch.float32).pin_memory()
+        sh = api.mbir_solve_host(plan, bh, wh, xh, 3, None, prior, power_iter=60)
+        assert sh.step == st.step
+        with pytest.raises(api.TcError):   # a resumed state with no step to reuse
+            bad = api.SolveState(x)
+            bad.k = 1
+            api.mbir_solve(plan, t32(b), t32(w), x, 1, None, prior, state=bad)
+
+
+# ------------------------------------------------ the headline geometry ----
+def _headline_inputs(B, dev):
+    n, a, d = 2048, 128, 2896
+    theta = oracle.default_angles(a)
+    p = synth.ellipsoid_sinogram_torch(n, B, theta, d, dev, scale=1.0 / n, seed=synth.BASE_SEED + 77)
+    b, w = synth.poisson_measurement_torch(p, 1e4, synth.BASE_SEED + 78)
+    return n, a, d, b.contiguous(), w.contiguous()
+
+
+def test_headline_first_iterate_matches_oracle(api):
+    """2048^2, 128 angles, 2896 bins, Poisson weights, 26-neighbour prior: from
+    x_0 = 0 the first iterate is x_1 = step A^T (W b) (the prior's gradient
+    vanishes on a constant image).  1024 sampled pixels per slice against the
+    oracle's closed-form adjoint: relative L2 <= 2e-5."""
+    dev = torch.device("cuda:0")
+    B = 2
+    n, a, d, b, w = _headline_inputs(B, dev)
+    step = 3.75e-6
+    prior = api.Prior(lam=1e-2, dims=3)
+    with api.Plan(n, a, d, max_batch=2) as plan:
+        x = torch.zeros((B, n, n), device=dev)
+        api.mbir_solve(plan, b, w, x, 1, step, prior)
+        xs = np64(x)
+    wb = np64(w) * np64(b)
+    rng = np.random.default_rng(2896)
+    for k in range(B):
+        pix = rng.integers(0, n * n, 1024)
+        ref = step * oracle.radon_adj_at(wb[k], n, pix)
+        assert rel(xs[k].ravel()[pix], ref) <= 2e-5
+
+
+def test_headline_prior_matches_oracle(api):
+    """The 26-neighbour prior gradient and value on three 2048^2 slices (tiles
+    inside the volume and at its border, at the full side) against the
+    oracle: relative L2 1e-5, value 1e-5."""
+    n, B = 2048, 3
+    f = np.stack([synth.rasterize(n, synth.random_ellipses(n, synth.BASE_SEED + 90 + k, scale=1.0 / n))
+                  for k in range(B)])
+    f += synth.uniform_field(f.shape, 91, 0.0, 2e-4).astype(np.float64)
+    f = f.astype(np.float32).astype(np.float64)
+    prior = api.Prior(lam=1e-2, dims=3)
+    with api.Plan(n, 8, 2896, max_batch=B) as plan:
+        z = torch.zeros((B, 8, 2896), device="cuda:0")
+        g, obj = api.mbir_grad(plan, t32(f), z, z, prior)
+    Hv, gh = oracle.prior_value_grad(f, 3, **oracle.PAPER_PRIOR)
+    assert rel(np64(g), prior.lam * gh) <= 1e-5
+    assert abs(float(obj[1]) - prior.lam * Hv) <= 1e-5 * prior.lam * Hv
+
+
+def test_restart_dots_on_the_full_volume_match_fp64(api):
+    """The restart test's inner products <g, z - x> and <g, g> on the whole
+    2048^2 x 1024 volume (128 angles, 2896 bins, Poisson weights, 26-neighbour
+    prior), against an FP64 reduction of the same FP32 vectors: the gradient
+    g = grad Phi(z_k) recomputed by mbir_grad (the same kernels, bit for bit),
+    z_k and x_k saved before the iteration.  Bound: 1e-10 of the sum of the
+    terms' magnitudes (an FP64 reduction's own error is of that order)."""
+    dev = torch.device("cuda:0")
+    B = 1024
+    n, a, d, b, w = _headline_inputs(B, dev)
+    prior = api.Prior(lam=1e-2, dims=3)
+    with api.Plan(n, a, d, max_batch=64) as plan:
+        x = torch.zeros((B, n, n), device=dev)
+        st = api.mbir_solve(plan, b, w, x, 2, 3.75e-6, prior)   # from iteration 2 on, z != x
+        xk, zk = x.clone(), st.z.clone()
+        api.mbir_solve(plan, b, w, x, 1, 3.75e-6, prior, state=st)
+        g, _ = api.mbir_grad(plan, zk, b, w, prior)
+        gzx = gg = mag = 0.0
+        for s0 in range(0, B, 64):
+            gd = g[s0:s0 + 64].double()
+            t = gd * (zk[s0:s0 + 64].double() - xk[s0:s0 + 64].double())
+            gzx += float(t.sum())
+            mag += float(t.abs().sum())
+            gg += float((gd * gd).sum())
+            del gd, t
+    assert abs(st.dots[1] - gg) <= 1e-10 * gg, (st.dots[1], gg)
+    assert abs(st.dots[0] - gzx) <= 1e-10 * mag, (st.dots[0], gzx, mag)
+
+
+# ------------------------------------------------ checkpoints and failures ----
+def test_checkpoint_on_storage_resumes_bitwise(api, tmp_path):
+    """10 iterations, checkpoint to a file (JSON header + raw x and z), load
+    into fresh buffers and a fresh state, 10 more: bit for bit the
+    uninterrupted 20-iteration solve (derived step, 3D prior, weights)."""
+    B = 3
+    _, b = _data(B)
+    w = np.random.default_rng(12).uniform(0.4, 1.0, b.shape)
+    prior = api.Prior(lam=1e-3, dims=3)
+    path = str(tmp_path / "solve.ckpt")
+    with api.Plan(N, A, D, max_batch=2) as plan:
+        bt, wt = t32(b), t32(w)
+        x1 = torch.zeros((B, N, N), device="cuda:0")
+        s1 = api.mbir_solve(plan, bt, wt, x1, 20, None, prior)
+        x2 = torch.zeros((B, N, N), device="cuda:0")
+        s2 = api.mbir_solve(plan, bt, wt, x2, 10, None, prior)
+        api.checkpoint_save(path, plan, x2, s2)
+        del x2, s2
+        x3 = torch.full((B, N, N), 7.0, device="cuda:0")
+        s3 = api.checkpoint_load(path, plan, x3)
+        assert s3.k == 10 and s3.step == s1.step
+        api.mbir_solve(plan, bt, wt, x3, 10, None, prior, state=s3)
+        with open(path, "rb") as fh:
+            head = fh.readline().decode()
+        with pytest.raises(api.TcError):   # geometry mismatch: rejected before any copy
+            with api.Plan(64, A, D) as other:
+                api.checkpoint_load(path, other, torch.zeros((B, 64, 64), device="cuda:0"))
+    assert s3.k == 20 and s3.n_restarts == s1.n_restarts
+    assert torch.equal(x3, x1)
+    assert torch.equal(s3.z, s1.z)
+    assert '"format": "tc-mbir-checkpoint"' in head and f'"k": 10' in head
+
+
+@pytest.mark.parametrize("after", [0, 2, 7])
+def test_injected_copy_failure_is_reported_and_the_plan_stays_usable(api, after):
+    """A host-to-device or device-to-host copy of the host-streamed solve that
+    fails (injected on the host: the copy is not issued and reports an error)
+    gives TC_ERR_CUDA after the copies in flight finish; the next solve on the
+    same plan runs normally and matches the resident solve bit for bit.
+    Five slices in slabs of two: copies 0..8 are inbound (b, w, x per slab),
+    the rest return x slab by slab."""
+    B = 5
+    _, b = _data(B)
+    w = np.random.default_rng(13).uniform(0.5, 1.0, b.shape)
+    step = _step(1e-3)
+    prior = api.Prior(lam=1e-3, dims=3)
+    with api.Plan(N, A, D, max_batch=2) as plan:
+        x = torch.zeros((B, N, N), device="cuda:0")
+        api.mbir_solve(plan, t32(b), t32(w), x, 3, step, prior)
+        bh = torch.tensor(b, dtype=torch.float32).pin_memory()
+        wh = torch.tensor(w, dtype=torch.float32).pin_memory()
+        xh = torch.zeros((B, N, N), dtype=torch.float32).pin_memory()
+        api.fail_copy_after(after)
+        try:
+            with pytest.raises(api.TcError) as e:
+                api.mbir_solve_host(plan, bh, wh, xh, 3, step, prior)
+        finally:
+            api.fail_copy_after(-1)
+        assert e.value.code == -3 and "injected" in str(e.value)
+        xh.zero_()
+        api.mbir_solve_host(plan, bh, wh, xh, 3, step, prior)
+    assert torch.equal(xh, x.cpu())
+
+
+def test_plan_that_cannot_fit_returns_oom_and_frees_everything(api):
+    """Scratch for 60000 slices of 2048^2 cannot be allocated: tc_plan_create
+    returns TC_ERR_OOM and the tables it had already uploaded are released."""
+    with api.Plan(2048, 128, 2896, max_batch=1):
+        pass   # kernel attributes and the context's lazy state set up once
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    with pytest.raises(api.TcError) as e:
+        api.Plan(2048, 128, 2896, max_batch=60000)
+    assert e.value.code == -2
+    torch.cuda.synchronize()
+    assert abs(torch.cuda.mem_get_info()[0] - free0) <= (2 << 20)
+
+
+def test_host_solve_argument_checks(api):
+    """NULL host buffers are rejected by the C ABI before any copy; the
+    binding rejects mis-sized host tensors."""
+    L = api.load()
+    import ctypes
+    with api.Plan(N, A, D) as plan:
+        x = torch.zeros((1, N, N), device="cuda:0")
+        st = api.SolveState(x)
+        cs = st._c()
+        opts = api._SolveOpts(2, 1e-4, 1, 0, 0)
+        db = torch.zeros((1, A, D), device="cuda:0")
+        rc = L.mbir_solve_host(plan.handle, None, None, None, api._ptr(db), None, api._ptr(x), 1, None,
+                               ctypes.byref(opts), ctypes.byref(cs), None)
+        assert rc == -1
+        with pytest.raises(ValueError):
+            api.mbir_solve_host(plan, torch.zeros((1, A, D - 2)), None, torch.zeros((1, N, N)), 2, 1e-4)

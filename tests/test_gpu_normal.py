@@ -211,3 +211,47 @@ def test_normal_solve_rejections(api):
         with pytest.raises(api.TcError) as e:
             api.mbir_solve(plan, t32(b), None, x, 2, 1e-3, None, restart="monotone", normal=True)
         assert e.value.code == -1
+
+
+def test_normal_largest_side_against_gridded(api):
+    """N = 4096, the largest side: the only size whose table build runs the
+    FP64 FFT at G = 8192 (128 KB of shared memory a CTA) and whose row pass
+    runs k_nrm_row<12>.  Few angles (A = 8, D = 5792) keep the gridded check
+    A^T (A x) affordable; the two agree within 2e-5 relative L2."""
+    n, a, d = 4096, 8, 5792
+    x = torch.tensor(synth.uniform_field((1, n, n), 4096), device="cuda:0")
+    with api.Plan(n, a, d, max_batch=1) as plan:
+        nx = api.radon_normal(plan, x)
+        gx = api.radon_adj(plan, api.radon_fwd(plan, x))
+        torch.cuda.synchronize()
+        assert float((nx - gx).norm() / gx.norm()) <= 2e-5
+
+
+def test_unprepared_normal_inside_a_capture_is_refused(api):
+    """The first normal-operator call builds tables (allocation, synchronisation),
+    which a CUDA-graph capture cannot record: inside a capture the unprepared
+    call returns TC_ERR_UNSUPPORTED without touching the stream; once prepared,
+    the captured call replays and matches the eager result."""
+    n, a, d = 64, 30, 92
+    x = torch.tensor(synth.uniform_field((2, n, n), 64), device="cuda:0")
+    out = torch.empty_like(x)
+    with api.Plan(n, a, d, max_batch=2) as plan:
+        api.radon_fwd(plan, x)   # kernels loaded before any capture
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        codes = []
+        with torch.cuda.graph(g):
+            try:
+                api.radon_normal(plan, x, out=out)
+            except api.TcError as e:
+                codes.append(e.code)
+        assert codes == [-5]
+        plan.prepare_normal()
+        eager = api.radon_normal(plan, x).clone()
+        g2 = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g2):
+            api.radon_normal(plan, x, out=out)
+        out.zero_()
+        g2.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(out, eager)

@@ -62,5 +62,45 @@ def test_noalloc_rejects_sizes_beyond_its_scratch(api):
     L = api.load()
     pc = api.Prior(dims=3)._c()
     x = torch.zeros((1, 16, 16), device="cuda:0")
-    rc = L.tc_prior_grad_noalloc(x.data_ptr(), x.data_ptr(), 8192, 1, ctypes.byref(pc), None, None)
+    g = torch.zeros_like(x)
+    rc = L.tc_prior_grad_noalloc(x.data_ptr(), g.data_ptr(), 8192, 1, ctypes.byref(pc), None, None)
     assert rc == -1
+
+
+def test_noalloc_rejects_overlapping_input_and_output(api):
+    """grad is written at one slice while other blocks still read x above and
+    below it, so x and grad must not overlap (in place or shifted)."""
+    L = api.load()
+    pc = api.Prior(dims=3)._c()
+    v = torch.zeros((4, 16, 16), device="cuda:0")
+    for xo, go in ((0, 0), (0, 1), (1, 0)):
+        rc = L.tc_prior_grad_noalloc(v[xo].data_ptr(), v[go].data_ptr(), 16, 3, ctypes.byref(pc), None, None)
+        assert rc == -1
+
+
+@pytest.mark.parametrize("n,batch", [(100, 5), (3, 4)])
+@pytest.mark.parametrize("dims", [2, 3])
+def test_noalloc_at_sides_the_plans_never_use(api, n, batch, dims):
+    """Sides that are not powers of two, smaller than a prior tile or not a
+    multiple of it (only border tiles, masked pairs) against the FP64 oracle's
+    qGGMRF value and gradient, on two calls in a row."""
+    import oracle
+    L = api.load()
+    prior = api.Prior(lam=0.5, dims=dims)
+    stream = torch.cuda.current_stream()
+    pd = dict(p=prior.p, sigma=prior.sigma, c=prior.c)
+    for call in range(2):
+        rng = np.random.default_rng(7 * n + call)
+        f = rng.uniform(0, 1, (batch, n, n)).astype(np.float32)
+        x = torch.tensor(f, device="cuda:0")
+        g = torch.zeros_like(x)
+        h = torch.full((1,), -1.0, dtype=torch.float64, device="cuda:0")
+        pc = prior._c()
+        rc = L.tc_prior_grad_noalloc(x.data_ptr(), g.data_ptr(), n, batch, ctypes.byref(pc),
+                                     h.data_ptr(), ctypes.c_void_p(stream.cuda_stream))
+        torch.cuda.synchronize()
+        assert rc == 0
+        Hv, gh = oracle.prior_value_grad(f.astype(np.float64), dims, **pd)
+        gd = g.double().cpu().numpy()
+        assert float(np.linalg.norm(gd - prior.lam * gh) / np.linalg.norm(prior.lam * gh)) <= TOL
+        assert abs(float(h[0]) - prior.lam * Hv) <= TOL * prior.lam * Hv
