@@ -213,8 +213,10 @@ int normal_prepare(tc_plan *p, cudaStream_t s);
 int launch_prior_grad(tc_plan *p, const float *x, float *g, int nb,
                       const tc_prior *pr, double *h_acc, cudaStream_t s,
                       const float *dot_x = nullptr, int z0 = 0, int z1 = -1, double step = 0.0);
-// CTAs (and FP64 partial sums) of one prior launch on N x N slices.
+// Tiles of one prior launch on N x N slices, and the FP64 partial-sum slots
+// its z-chunked grid may use.
 int prior_tile_count(int n);
+int prior_block_slots(int n);
 // h_acc = lambda H(x) only (no gradient).
 int launch_prior_value(tc_plan *p, const float *x, int nb, const tc_prior *pr,
                        double *h_acc, cudaStream_t s);

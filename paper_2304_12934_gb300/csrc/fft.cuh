@@ -327,6 +327,54 @@ __device__ __forceinline__ void fft_ct_first_mapped(float2 *s, int cnt, Map &&ma
     __syncthreads();
 }
 
+// exp(-2 pi i q / 32) times -1 for q >= 8, q = 0..15: the factor by which the
+// G = 2n grid twiddle exp(-2 pi i (ix - n/2) / G) of input j + ((q + 8) mod 16) n/16
+// differs from that of input j + n/2 (see fft_first_from_row).
+__device__ __forceinline__ float2 w32_signed(int q) {
+    const float c[9] = {1.0f, 0.98078528040323044913f, 0.92387953251128675613f, 0.83146961230254523708f,
+                        0.70710678118654752440f, 0.55557023301960222474f, 0.38268343236508977173f,
+                        0.19509032201612826785f, 0.0f};
+    // cos(q pi/16), sin(q pi/16) for q = 0..15 from the first quadrant
+    const float cr = q <= 8 ? c[q] : -c[16 - q];
+    const float si = q <= 8 ? c[8 - q] : c[q - 8];
+    const float sg = q >= 8 ? -1.0f : 1.0f;
+    return make_float2(sg * cr, -sg * si);
+}
+
+// The first (radix-16) stage of the even/odd pair of transforms that give the
+// G = 2n point DFT of one row of n samples (n = 2^LOGN): transform 0 takes
+// x[(k + n/2) mod n] at FFT index k, transform 1 the same times the grid
+// twiddle tw[(k + n/2) mod n], tw[i] = exp(-2 pi i (i - n/2) / G).  The
+// inputs come straight from global memory (row: n contiguous values) into
+// registers, so the row is never staged in shared memory; thread t runs
+// butterfly t mod n/16 of transform t / (n/16), writes its 16 outputs to
+// the padded buffer (transform stride fft_tstride(n)) and the block
+// synchronises.  The remaining stages follow with fft_ct<SIGN, LOGN, 4>.
+// Requires blockDim.x >= n / 8.
+template <int SIGN, int LOGN>
+__device__ __forceinline__ void fft_first_from_row(float2 *s, const float2 *__restrict__ row,
+                                                   const float2 *__restrict__ tw) {
+    static_assert(LOGN >= 4, "the first stage is radix 16");
+    constexpr int N = 1 << LOGN, PER = N / 16, TS = fft_tstride(N);
+    const int t = threadIdx.x;
+    if (t < 2 * PER) {
+        const int tr = t / PER, j = t % PER;
+        float2 v[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) v[q] = row[j + ((q + 8) & 15) * PER];
+        if (tr == 1) {
+            const float2 wj = tw[j + N / 2];  // exp(-2 pi i j / G)
+#pragma unroll
+            for (int q = 0; q < 16; ++q) v[q] = cmul(v[q], q == 0 ? wj : cmul(wj, w32_signed(q)));
+        }
+        dft_reg<SIGN, 16>(v);
+        float2 *dst = s + tr * TS + spad(j << 4);  // Ns = 1: outputs 16 j .. 16 j + 15
+#pragma unroll
+        for (int q = 0; q < 16; ++q) dst[q] = v[q];
+    }
+    __syncthreads();
+}
+
 // A pair of transforms (cnt = 2) of length 2^LOGN, LOGN = 3 (mod 4), run with
 // blockDim.x == n / 8: the last (radix-8) stage then gives each thread one
 // butterfly of each transform at the same index, and instead of storing it

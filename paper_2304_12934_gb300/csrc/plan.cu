@@ -533,7 +533,7 @@ int tc_plan_build(const tc_geom *geom, int max_batch, tc_plan **out) {
     // scratch
     const size_t MB = (size_t)max_batch;
     p->slot = std::max(std::max(TC_RED_BLOCKS, (int)(((A + 1) / 2) * MB)),
-                       prior_tile_count(N));
+                       prior_block_slots(N));
     if ((rc = alloc_dev((void **)&p->tu, MB * R * N * sizeof(float2), bytes)) ||
         (rc = alloc_dev((void **)&p->pv, MB * w * (size_t)k.AM * sizeof(float2), bytes)) ||
         (rc = alloc_dev((void **)&p->sr, MB * (size_t)A * D * sizeof(float), bytes)) ||

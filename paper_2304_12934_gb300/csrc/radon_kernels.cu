@@ -107,21 +107,14 @@ __global__ void __launch_bounds__(512) k_fwd_col(const float *__restrict__ x, fl
 }
 
 template <int LOGN>
-__global__ void __launch_bounds__(512) k_fwd_row(const float2 *__restrict__ T, float2 *__restrict__ P,
-                          const KArgs g) {
+__global__ void __launch_bounds__(LOGN == 11 ? 256 : 512, LOGN == 11 ? 5 : 1)
+    k_fwd_row(const float2 *__restrict__ T, float2 *__restrict__ P, const KArgs g) {
     extern __shared__ float2 sm[];  // 2 transforms (stride ts)
     constexpr int N = 1 << LOGN, ts = fft_tstride(N);
     const int r = blockIdx.x, b = blockIdx.y;
     const float2 *Tr = T + ((size_t)b * g.R + r) * N;
-#pragma unroll 8
-    for (int ix = threadIdx.x; ix < N; ix += blockDim.x) {
-        const float2 v = Tr[ix];
-        const int q = (ix - N / 2) & (N - 1);
-        sm[spad(q)] = v;
-        sm[ts + spad(q)] = cmul(v, g.twG[ix]);
-    }
-    __syncthreads();
-    fft_ct<-1, LOGN>(sm, 2, g.twN);
+    fft_first_from_row<-1, LOGN>(sm, Tr, g.twG);
+    fft_ct<-1, LOGN, 4>(sm, 2, g.twN);
     float2 *Pb = P + (size_t)b * g.w * g.AM;
     const int e1 = g.row_off[r + 1];
     constexpr int Gm = 2 * N - 1;
@@ -294,13 +287,17 @@ __device__ __forceinline__ float2 spread_record(const float4 *__restrict__ ce, i
 // (the few wrap-around duplicates at the spectrum edge are flagged and added
 // serially), so no two threads touch a cell and every cell's summation order
 // is fixed: atomic-free and bit-reproducible.
+#ifndef TC_ADJ_ROW_SLICES_FASTEST
+#define TC_ADJ_ROW_SLICES_FASTEST 0
+#endif
 template <int LOGN>
 __global__ void __launch_bounds__(512) k_adj_row(const float2 *__restrict__ V, float2 *__restrict__ U,
                           const KArgs g) {
     extern __shared__ float2 sm[];
     constexpr int N = 1 << LOGN, G = 2 * N;
     constexpr int ts = fft_tstride(N), hsz = 2 * ts;              // grid row: 2 transforms
-    const int r = blockIdx.x, b = blockIdx.y;
+    const int r = TC_ADJ_ROW_SLICES_FASTEST ? blockIdx.y : blockIdx.x;
+    const int b = TC_ADJ_ROW_SLICES_FASTEST ? blockIdx.x : blockIdx.y;
     // staged entries: (u = phi_y V[p], key, -ex / h); hsz is even, so 16-byte aligned
     float4 *ce = reinterpret_cast<float4 *>(sm + hsz);             // [SPREAD_CHUNK]
     const int e0 = g.row_off[r], e1 = g.row_off[r + 1];
@@ -450,15 +447,8 @@ __global__ void __launch_bounds__(LOGN == 11 ? 256 : 512, LOGN == 11 ? 4 : 1)
     constexpr int N = 1 << LOGN, ts = fft_tstride(N);
     const int b = blockIdx.x, r = blockIdx.y;
     float2 *Ur = U + ((size_t)b * g.R + r) * N;
-#pragma unroll 8
-    for (int ix = threadIdx.x; ix < N; ix += blockDim.x) {
-        const float2 v = Ur[ix];
-        const int q = (ix - N / 2) & (N - 1);
-        sm[spad(q)] = v;
-        sm[ts + spad(q)] = cmul(v, g.twG[ix]);
-    }
-    __syncthreads();
-    fft_ct<-1, LOGN>(sm, 2, g.twN);
+    fft_first_from_row<-1, LOGN>(sm, Ur, g.twG);
+    fft_ct<-1, LOGN, 4>(sm, 2, g.twN);
     // cell c = 2j + t of the row sits in transform t at j; the tables use the same order
     const float *tr = tt + (size_t)r * 2 * N;
     const float2 *hr = th + (size_t)r * 2 * N;
@@ -577,7 +567,7 @@ int launch_radon_adj_chunk(tc_plan *p, const float *y, float *x, int nb,
     else
         TC_PROFILED(TCK_ADJ_DET, s, k_adj_det<false><<<gd, p->threads_det, p->smem_det, s>>>(y, p->pv, g));
     TC_LAUNCHED("k_adj_det");
-    dim3 gr(g.R, nb);
+    const dim3 gr = TC_ADJ_ROW_SLICES_FASTEST ? dim3(nb, g.R) : dim3(g.R, nb);
     dim3 gc(g.N / (2 * p->cp_col), nb);
     return with_logn(g.log2N, [&](auto L) {
         constexpr int LG = decltype(L)::value;
