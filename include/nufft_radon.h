@@ -276,6 +276,37 @@ int mbir_solve_host(tc_plan *plan, const float *b_host, const float *w_host,
                     int batch, const tc_prior *prior, const tc_solve_opts *opts,
                     tc_solve_state *state, void *stream);
 
+/* ------------------------------------------------------- plan groups ------ */
+/* Uneven batches (an engineering addition for batches of slices whose image
+ * side, angle count or detector width differ; the paper reconstructs one
+ * geometry at a time).  A group holds one plan per geometry, sized for all of
+ * that geometry's slices (counts[i] slices of geoms[i]), and a work list per
+ * pipeline stage over every (geometry, slice, tile) item.  Each stage runs as
+ * one persistent launch: as many CTAs as fit on the GPU take items from an
+ * atomic ticket until the list is empty, largest geometries first.  Stage
+ * boundaries are kernel boundaries (no CTA waits for another).  Results are
+ * bit for bit those of the per-geometry plans.
+ * Arrays of a group are the geometries' slices concatenated in the order
+ * given: images geoms[0] x counts[0] slices of N0 x N0, then geoms[1]'s, ...;
+ * sinograms likewise with A_i x D_i.  Calls are asynchronous, capturable into
+ * a CUDA graph once the group exists, and not thread safe per group.
+ * tc_plan_group_create allocates (synchronous); 1 <= n_geoms <= 256 and
+ * 1 <= counts[i] <= 65535, each geometry as for tc_plan_create. */
+typedef struct tc_plan_group tc_plan_group;
+int tc_plan_group_create(const tc_geom *geoms, const int *counts, int n_geoms, tc_plan_group **out);
+int tc_plan_group_destroy(tc_plan_group *group);
+long long tc_plan_group_device_bytes(const tc_plan_group *group);
+/* y = A x and x = A^T y for every slice of the group (concatenated layouts). */
+int radon_fwd_group(tc_plan_group *group, const float *x, float *y, void *stream);
+int radon_adj_group(tc_plan_group *group, const float *y, float *x, void *stream);
+/* grad = A^T W (A x - b) + lambda grad H(x) for every slice, the prior over
+ * each geometry's slices as one volume (dims = 3) or slice by slice (dims =
+ * 2); w may be NULL (W = I), prior may be NULL.  obj: DEVICE pointer to
+ * 2 n_geoms doubles or NULL: obj[2 i] = 1/2 sum W (A x - b)^2 and
+ * obj[2 i + 1] = lambda H(x) of geometry i. */
+int mbir_grad_group(tc_plan_group *group, const float *x, const float *b, const float *w,
+                    const tc_prior *prior, float *grad, double *obj, void *stream);
+
 /* --------------------------------------------------------- checkpoints --- */
 /* Solver checkpoint on storage (no counterpart in the paper, whose solver
  * state lives in host memory between partitions, Sec. 4; it lets a long solve

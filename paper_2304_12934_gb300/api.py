@@ -59,7 +59,9 @@ SYMBOLS = ("tc_status_string", "tc_last_error_detail", "tc_plan_create", "tc_pla
            "tc_profile_collect", "tc_profile_kernel_name", "tc_launch_count",
            "tc_plan_autotune", "tc_plan_set_launch", "tc_prior_grad_noalloc",
            "tc_plan_status", "tc_selftest_wait_timeout", "radon_normal", "tc_plan_prepare_normal",
-           "tc_checkpoint_save", "tc_checkpoint_load", "tc_test_fail_copy_after")
+           "tc_checkpoint_save", "tc_checkpoint_load", "tc_test_fail_copy_after",
+           "tc_plan_group_create", "tc_plan_group_destroy", "tc_plan_group_device_bytes",
+           "radon_fwd_group", "radon_adj_group", "mbir_grad_group")
 
 
 def lib_path() -> str:
@@ -111,11 +113,20 @@ def load(build_if_missing: bool = True):
     L.tc_checkpoint_save.argtypes = [ctypes.c_char_p, vp, vp, i, ctypes.POINTER(_SolveState), vp]
     L.tc_checkpoint_load.argtypes = [ctypes.c_char_p, vp, vp, i, ctypes.POINTER(_SolveState), vp]
     L.tc_test_fail_copy_after.argtypes = [i]
+    L.tc_plan_group_create.argtypes = [ctypes.POINTER(_Geom), ctypes.POINTER(i), i, ctypes.POINTER(vp)]
+    L.tc_plan_group_destroy.argtypes = [vp]
+    L.tc_plan_group_device_bytes.argtypes = [vp]
+    L.tc_plan_group_device_bytes.restype = ctypes.c_longlong
+    L.radon_fwd_group.argtypes = [vp, vp, vp, vp]
+    L.radon_adj_group.argtypes = [vp, vp, vp, vp]
+    L.mbir_grad_group.argtypes = [vp, vp, vp, vp, ctypes.POINTER(_Prior), vp, vp, vp]
     for fn in ("tc_profile_enable", "tc_profile_collect", "tc_plan_create", "tc_plan_destroy",
                "radon_fwd", "radon_adj", "mbir_grad", "mbir_power_norm", "mbir_solve",
                "mbir_solve_host", "tc_plan_autotune", "tc_plan_set_launch",
                "tc_prior_grad_noalloc", "radon_normal", "tc_plan_prepare_normal",
-               "tc_checkpoint_save", "tc_checkpoint_load", "tc_test_fail_copy_after"):
+               "tc_checkpoint_save", "tc_checkpoint_load", "tc_test_fail_copy_after",
+           "tc_plan_group_create", "tc_plan_group_destroy", "tc_plan_group_device_bytes",
+           "radon_fwd_group", "radon_adj_group", "mbir_grad_group"):
         getattr(L, fn).restype = i
     _LIB = L
     return L
@@ -230,6 +241,131 @@ class Plan:
 
     def sino_shape(self, batch):
         return (batch, self.n_angles, self.n_det)
+
+
+class PlanGroup:
+    """Several geometries in one batch (tc_plan_group_create): geoms is a list of
+    (n, n_angles, n_det) or dicts with the Plan keywords; counts the slices of
+    each.  Arrays are the geometries' slices concatenated in that order
+    (flat float32 CUDA tensors, see image_numel / sino_numel)."""
+
+    def __init__(self, geoms, counts, device=None):
+        L = load()
+        self.device = torch.device("cuda", torch.cuda.current_device()) if device is None \
+            else torch.device(device)
+        self._keep = []
+        cg = (_Geom * len(geoms))()
+        self.geoms = []
+        for k, gm in enumerate(geoms):
+            d = dict(gm) if isinstance(gm, dict) else dict(zip(("n", "n_angles", "n_det"), gm))
+            aptr = ctypes.POINTER(ctypes.c_double)()
+            if d.get("angles") is not None:
+                import numpy as np
+                arr = np.ascontiguousarray(d["angles"], dtype=np.float64)
+                self._keep.append(arr)
+                aptr = arr.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+            cg[k] = _Geom(int(d["n"]), int(d["n_angles"]), int(d["n_det"]), aptr, int(d.get("oversample", 2)),
+                          int(d.get("kernel_width", 7)), float(d.get("center_offset", 0.0)))
+            self.geoms.append((int(d["n"]), int(d["n_angles"]), int(d["n_det"])))
+        self.counts = [int(c) for c in counts]
+        cc = (ctypes.c_int * len(self.counts))(*self.counts)
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            _check("tc_plan_group_create", L.tc_plan_group_create(cg, cc, len(self.geoms), ctypes.byref(h)))
+        self._h = h
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise RuntimeError("plan group is closed")
+        return self._h
+
+    @property
+    def image_numel(self):
+        return sum(c * n * n for (n, _, _), c in zip(self.geoms, self.counts))
+
+    @property
+    def sino_numel(self):
+        return sum(c * a * d for (_, a, d), c in zip(self.geoms, self.counts))
+
+    def split_images(self, flat):
+        """Views [counts[i], N_i, N_i] of a concatenated image array."""
+        out, o = [], 0
+        for (n, _, _), c in zip(self.geoms, self.counts):
+            out.append(flat[o:o + c * n * n].view(c, n, n))
+            o += c * n * n
+        return out
+
+    def split_sinos(self, flat):
+        out, o = [], 0
+        for (_, a, d), c in zip(self.geoms, self.counts):
+            out.append(flat[o:o + c * a * d].view(c, a, d))
+            o += c * a * d
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            load().tc_plan_group_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def _need_flat(t, numel, name, device):
+    if t.dtype != torch.float32 or not t.is_cuda or not t.is_contiguous() or t.numel() != numel:
+        raise ValueError(f"{name} must be a contiguous CUDA float32 tensor of {numel} elements")
+    if t.device != device:
+        raise ValueError(f"{name} is on {t.device}, group is on {device}")
+
+
+def radon_fwd_group(group: PlanGroup, x, y=None, stream=None):
+    """y = A x for every slice of the group (concatenated layouts)."""
+    _need_flat(x, group.image_numel, "x", group.device)
+    if y is None:
+        y = torch.empty(group.sino_numel, device=group.device, dtype=torch.float32)
+    _need_flat(y, group.sino_numel, "y", group.device)
+    _check("radon_fwd_group", load().radon_fwd_group(group.handle, _ptr(x), _ptr(y), _stream(stream, group.device)))
+    return y
+
+
+def radon_adj_group(group: PlanGroup, y, x=None, stream=None):
+    """x = A^T y for every slice of the group (concatenated layouts)."""
+    _need_flat(y, group.sino_numel, "y", group.device)
+    if x is None:
+        x = torch.empty(group.image_numel, device=group.device, dtype=torch.float32)
+    _need_flat(x, group.image_numel, "x", group.device)
+    _check("radon_adj_group", load().radon_adj_group(group.handle, _ptr(y), _ptr(x), _stream(stream, group.device)))
+    return x
+
+
+def mbir_grad_group(group: PlanGroup, x, b, w=None, prior: Prior | None = None, grad=None, obj=None,
+                    stream=None):
+    """grad = A^T W (A x - b) + lam grad H(x) over the group; obj (device float64
+    [n_geoms, 2]) = (data, lam H) per geometry."""
+    _need_flat(x, group.image_numel, "x", group.device)
+    _need_flat(b, group.sino_numel, "b", group.device)
+    if w is not None:
+        _need_flat(w, group.sino_numel, "w", group.device)
+    if grad is None:
+        grad = torch.empty_like(x)
+    _need_flat(grad, group.image_numel, "grad", group.device)
+    if obj is None:
+        obj = torch.zeros((len(group.counts), 2), dtype=torch.float64, device=group.device)
+    pr = prior._c() if prior is not None else None
+    _check("mbir_grad_group", load().mbir_grad_group(group.handle, _ptr(x), _ptr(b), _ptr(w),
+                                                     ctypes.byref(pr) if pr is not None else None,
+                                                     _ptr(grad), _ptr(obj), _stream(stream, group.device)))
+    return grad, obj
 
 
 def _need(t, shape, name, device):

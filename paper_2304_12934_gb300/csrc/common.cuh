@@ -147,7 +147,9 @@ __device__ __forceinline__ float es_kernel_fast(float z, float beta_l2) {
 }
 
 // Entries of one grid row staged per chunk by the spreading kernel.
+#ifndef SPREAD_CHUNK
 #define SPREAD_CHUNK 512
+#endif
 
 // Block-wide FP64 sum of one float per thread; thread 0 gets the total.
 __device__ __forceinline__ double block_sum_f64(double d, double *red) {

@@ -80,7 +80,6 @@ struct PriorArgs {
     unsigned long long one2;     // 1
     unsigned long long gscale2;  // 2 lambda / (sigma^2 c)
     unsigned long long nstep2;   // DOTS: minus the solver's step (g receives f - step grad)
-    unsigned long long w12, w22, w32;  // weights at distance 1, sqrt 2, sqrt 3
 };
 
 __device__ __forceinline__ float lg2a(float x) {
@@ -99,25 +98,6 @@ __device__ __forceinline__ float rcpa(float x) {
     return r;
 }
 
-// One pair direction for both cells of a lane: d = fm - fn, returns
-// e = d i (p + q i) (sigma^2 c rho'(d)); dh = d^2 i (sigma^2 c rho(d)) when
-// wanted.  keep: per-cell validity (border tiles), folded in through d i.
-template <bool MASK, bool WANT_H>
-__device__ __forceinline__ float2 pair_eval(float2 fm, float2 fn, const PriorArgs &a, bool k0, bool k1,
-                                            float2 &dh) {
-    const float2 d = sub2(fm, fn);
-    const float2 t = fma2kk(make_float2(lg2a(fabsf(d.x)), lg2a(fabsf(d.y))), a.q2, a.lk2);
-    const float2 den = add2k(make_float2(ex2a(t.x), ex2a(t.y)), a.one2);
-    const float2 inv = make_float2(rcpa(den.x), rcpa(den.y));
-    float2 di = mul2(d, inv);
-    if (MASK) {
-        di.x = k0 ? di.x : 0.f;
-        di.y = k1 ? di.y : 0.f;
-    }
-    if (WANT_H) dh = mul2(d, di);
-    return mul2(di, fma2kk(inv, a.q2, a.p2));
-}
-
 // direction u of the z+1 pairs: dx = u % 3 - 1, dy = u / 3 - 1
 __host__ __device__ constexpr int udx(int u) { return u % 3 - 1; }
 __host__ __device__ constexpr int udy(int u) { return u / 3 - 1; }
@@ -125,13 +105,55 @@ __host__ __device__ constexpr int udy(int u) { return u / 3 - 1; }
 __host__ __device__ constexpr int pdx(int q) { return q == 0 ? 1 : (q == 1 ? -1 : (q == 2 ? 0 : 1)); }
 __host__ __device__ constexpr int pdy(int q) { return q == 0 ? 0 : 1; }
 
-__device__ __forceinline__ unsigned long long wt_up(const PriorArgs &a, int u) {
-    const int dx = udx(u), dy = udy(u);
-    return (dx == 0 && dy == 0) ? a.w12 : ((dx == 0 || dy == 0) ? a.w22 : a.w32);
-}
-
 // 8-byte shared load of ring cells (c, c+1) at float index i (i even)
 __device__ __forceinline__ float2 lds2(const float *s, int i) { return *reinterpret_cast<const float2 *>(s + i); }
+
+// Global accesses under a predicate, without a branch (zeros when off).
+__device__ __forceinline__ float2 ldg2_if(const float *p, bool c) {
+    float2 v;
+    asm("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %3, 0;\n\tmov.b32 %0, 0;\n\tmov.b32 %1, 0;\n\t"
+        "@q ld.global.v2.f32 {%0, %1}, [%2];\n\t}"
+        : "=f"(v.x), "=f"(v.y) : "l"(p), "r"((int)c));
+    return v;
+}
+__device__ __forceinline__ float ldg1_if(const float *p, bool c) {
+    float v;
+    asm("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %2, 0;\n\tmov.b32 %0, 0;\n\t@q ld.global.f32 %0, [%1];\n\t}"
+        : "=f"(v) : "l"(p), "r"((int)c));
+    return v;
+}
+__device__ __forceinline__ void stg2_if(float *p, float2 v, bool c) {
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %3, 0;\n\t@q st.global.v2.f32 [%0], {%1, %2};\n\t}"
+                 ::"l"(p), "f"(v.x), "f"(v.y), "r"((int)c) : "memory");
+}
+__device__ __forceinline__ void stg1_if(float *p, float v, bool c) {
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %2, 0;\n\t@q st.global.f32 [%0], %1;\n\t}"
+                 ::"l"(p), "f"(v), "r"((int)c) : "memory");
+}
+__device__ __forceinline__ void prefetch_l2_if(const float *p, bool c) {
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %1, 0;\n\t@q prefetch.global.L2 [%0];\n\t}" ::"l"(p), "r"((int)c));
+}
+
+// Neighbour weights 1/||m - n|| normalised over the 26 (3D) or 8 (2D)
+// neighbours, at distance 1, sqrt 2, sqrt 3.
+template <int DIMS>
+struct Wts;
+template <>
+struct Wts<3> {  // Z = 6 + 12/sqrt(2) + 8/sqrt(3)
+    static constexpr float w1 = (float)(1.0 / 19.104083527755576), w2 = (float)(0.70710678118654752 / 19.104083527755576),
+                           w3 = (float)(0.57735026918962576 / 19.104083527755576);
+};
+template <>
+struct Wts<2> {  // Z = 4 + 4/sqrt(2)
+    static constexpr float w1 = (float)(1.0 / 6.8284271247461901), w2 = (float)(0.70710678118654752 / 6.8284271247461901),
+                           w3 = 0.f;
+};
+
+// role of a ring row: interior rows, the bottom halo row (only pairs that reach
+// row 1) and the top halo row (only the z+1 pairs that reach row TY)
+constexpr int ROLE_IN = 0, ROLE_BOT = 1, ROLE_TOP = 2;
+__host__ __device__ constexpr unsigned up_dirs(int role) { return role == ROLE_IN ? 0x1ffu : (role == ROLE_BOT ? 0x1c0u : 0x007u); }
+__host__ __device__ constexpr unsigned pl_dirs(int role) { return role == ROLE_IN ? 0xfu : (role == ROLE_BOT ? 0xeu : 0x0u); }
 
 template <bool WANT_H, bool DOTS, bool GRAD, int DIMS, bool EVEN>
 __global__ void __launch_bounds__(THREADS, MIN_BLOCKS)
@@ -174,25 +196,37 @@ __global__ void __launch_bounds__(THREADS, MIN_BLOCKS)
     const int zs = (DIMS == 3 && za > 0) ? za - 1 : za;
     const long long off = (long long)gy * N + gx;
     const int rs = wr * RX + 2 * lane;                       // own slot in a ring array
+    // constants of the pair evaluation, held once
+    const unsigned long long q2 = a.q2, lk2 = a.lk2, p2 = a.p2, one2 = a.one2;
+    const unsigned long long w1 = pack_splat(Wts<DIMS>::w1), w2 = pack_splat(Wts<DIMS>::w2),
+                             w3 = pack_splat(Wts<DIMS>::w3);
+    auto wup = [&](int u) { return (udx(u) == 0 && udy(u) == 0) ? w1 : ((udx(u) == 0 || udy(u) == 0) ? w2 : w3); };
 
     auto load_pair = [&](int z) -> float2 {
-        float2 v = make_float2(0.f, 0.f);
-        if (z < B) {
-            const float *src = f + (size_t)z * NN + off;
-            if (EVEN) {
-                if (in0) v = *reinterpret_cast<const float2 *>(src);
-            } else {
-                if (in0) v.x = src[0];
-                if (in1) v.y = src[1];
-            }
-        }
-        return v;
+        const float *src = f + (size_t)z * NN + off;
+        const bool c = z < B;
+        if (EVEN) return ldg2_if(src, c && in0);
+        return make_float2(ldg1_if(src, c && in0), ldg1_if(src + 1, c && in1));
     };
     // plane values into ring array pl: plain and shifted by one cell
     auto store_plane = [&](int pl, float2 v) {
         const float nx = __shfl_down_sync(0xffffffffu, v.x, 1);
         *reinterpret_cast<float2 *>(F + pl * PLANE + rs) = v;
         *reinterpret_cast<float2 *>(S + pl * PLANE + rs) = make_float2(v.y, nx);
+    };
+    // one pair direction for both cells: d = fm - fn, e = d i (p + q i); dh = d^2 i
+    auto pair_eval = [&](auto mk, float2 fm, float2 fn, bool k0, bool k1, float2 &dh) -> float2 {
+        const float2 d = sub2(fm, fn);
+        const float2 t = fma2kk(make_float2(lg2a(fabsf(d.x)), lg2a(fabsf(d.y))), q2, lk2);
+        const float2 den = add2k(make_float2(ex2a(t.x), ex2a(t.y)), one2);
+        const float2 inv = make_float2(rcpa(den.x), rcpa(den.y));
+        float2 di = mul2(d, inv);
+        if (decltype(mk)::value) {
+            di.x = k0 ? di.x : 0.f;
+            di.y = k1 ? di.y : 0.f;
+        }
+        if (WANT_H) dh = mul2(d, di);
+        return mul2(di, fma2kk(inv, q2, p2));
     };
     if (DIMS == 3) {
         for (int i = threadIdx.x; i < 9 * PLANE; i += THREADS) Eu[i] = 0.f;
@@ -211,27 +245,60 @@ __global__ void __launch_bounds__(THREADS, MIN_BLOCKS)
     ad2.zero();
     float2 h16 = make_float2(0.f, 0.f);
 
+    // phase B for one role and border mode: this plane's pairs of the lane's
+    // two cells, their forward shares in gs (and H terms in hs), the values
+    // stored for the voxels that close them
+    auto pairs = [&](auto role, auto mk, auto cur_c, bool up, float2 &gs, float2 &hs, float2 &e10) {
+        constexpr int ROLE = decltype(role)::value, cur = decltype(cur_c)::value, nxt = cur ^ 1;
+        if (DIMS == 3 && up) {
+#pragma unroll
+            for (int u = 0; u < 9; ++u) {
+                if (!((up_dirs(ROLE) >> u) & 1u)) continue;
+                const int dx = udx(u), dy = udy(u);
+                const int o = nxt * PLANE + (wr + dy) * RX + 2 * lane;
+                const float2 fn = dx == 0 ? lds2(F, o) : lds2(S, o + (dx > 0 ? 0 : -2));
+                float2 dh;
+                const float2 e = pair_eval(mk, fcur, fn, (km0 >> u) & 1, (km1 >> u) & 1, dh);
+                gs = fma2k(e, wup(u), gs);
+                if (WANT_H) hs = fma2k(dh, wup(u), hs);
+                if (GRAD) *reinterpret_cast<float2 *>(Eu + u * PLANE + rs) = e;
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (!((pl_dirs(ROLE) >> q) & 1u)) continue;
+            const int dx = pdx(q), dy = pdy(q);
+            const int o = cur * PLANE + (wr + dy) * RX + 2 * lane;
+            const float2 fn = dx == 0 ? lds2(F, o) : lds2(S, o + (dx > 0 ? 0 : -2));
+            float2 dh;
+            const float2 e = pair_eval(mk, fcur, fn, (km0 >> (9 + q)) & 1, (km1 >> (9 + q)) & 1, dh);
+            const unsigned long long wq = (dx != 0 && dy != 0) ? w2 : w1;
+            gs = fma2k(e, wq, gs);
+            if (WANT_H) hs = fma2k(dh, wq, hs);
+            if (q == 0) e10 = e;
+            else if (GRAD) *reinterpret_cast<float2 *>(Ep + (q - 1) * PLANE + rs) = e;
+        }
+    };
+
     auto step = [&](auto par, int z) {
         constexpr int cur = decltype(par)::value, nxt = cur ^ 1;
         const bool own = z >= za;
         const bool up = DIMS == 3 && z + 1 < B;
         const float2 fpf = load_pair(DIMS == 3 ? z + 2 : z + 1);   // the plane the next step stores
         const size_t i = (size_t)z * NN + off;
+        const bool mine0 = own && own0, mine1 = own && own1;       // this lane's cells get a gradient
         float2 gold = make_float2(0.f, 0.f), xold = make_float2(0.f, 0.f);
-        if (GRAD && own && iwarp && ilane) {
+        if (GRAD && own && iwarp) {
             if (EVEN) {
-                if (in0) {
-                    gold = *reinterpret_cast<const float2 *>(g + i);
-                    if (DOTS) xold = *reinterpret_cast<const float2 *>(xprev + i);
-                }
+                gold = ldg2_if(g + i, mine0);
+                if (DOTS) xold = ldg2_if(xprev + i, mine0);
             } else {
-                if (in0) gold.x = g[i], xold.x = DOTS ? xprev[i] : 0.f;
-                if (in1) gold.y = g[i + 1], xold.y = DOTS ? xprev[i + 1] : 0.f;
+                gold = make_float2(ldg1_if(g + i, mine0), ldg1_if(g + i + 1, mine1));
+                if (DOTS) xold = make_float2(ldg1_if(xprev + i, mine0), ldg1_if(xprev + i + 1, mine1));
             }
-            if (z + 2 < zb && in0) {  // the same lines two planes on, into L2
-                asm volatile("prefetch.global.L2 [%0];" ::"l"(g + i + 2 * NN));
-                if (DOTS) asm volatile("prefetch.global.L2 [%0];" ::"l"(xprev + i + 2 * NN));
-            }
+            // the same lines two planes on, into L2
+            prefetch_l2_if(g + i + 2 * NN, mine0 && z + 2 < zb);
+            if (DOTS) prefetch_l2_if(xprev + i + 2 * NN, mine0 && z + 2 < zb);
         }
         // ---- A: stage the next plane; close the z+1 pairs of the step before
         if (DIMS == 3) {
@@ -250,56 +317,23 @@ __global__ void __launch_bounds__(THREADS, MIN_BLOCKS)
                 if (dx == 0) v = lds2(e, 0);
                 else if (dx > 0) v = make_float2(e[-1], e[0]);
                 else v = make_float2(e[1], e[2]);
-                gc = fma2k(v, wt_up(a, u), gc);
+                gc = fma2k(v, wup(u), gc);
             }
         }
         __syncthreads();
-        // ---- B: this plane's pairs
+        // ---- B: this plane's pairs (one branch per warp role and border mode)
         float2 gs = make_float2(0.f, 0.f), hs = make_float2(0.f, 0.f), e10 = make_float2(0.f, 0.f);
-        const bool bot = wr == 0, top = wr == RY - 1;
-        if (GRAD || iwarp) {
-            auto up_pairs = [&](auto mk) {
-                constexpr bool MK = decltype(mk)::value;
-#pragma unroll
-                for (int u = 0; u < 9; ++u) {
-                    const int dx = udx(u), dy = udy(u);
-                    // the bottom halo row needs the pairs that reach row 1, the top one those reaching row TY
-                    if ((bot && dy != 1) || (top && dy != -1)) continue;
-                    const int o = nxt * PLANE + (wr + dy) * RX + 2 * lane;
-                    const float2 fn = dx == 0 ? lds2(F, o) : lds2(S, o + (dx > 0 ? 0 : -2));
-                    float2 dh;
-                    const float2 e = pair_eval<MK, WANT_H>(fcur, fn, a, (km0 >> u) & 1, (km1 >> u) & 1, dh);
-                    const unsigned long long wu = wt_up(a, u);
-                    gs = fma2k(e, wu, gs);
-                    if (WANT_H) hs = fma2k(dh, wu, hs);
-                    if (GRAD) *reinterpret_cast<float2 *>(Eu + u * PLANE + rs) = e;
-                }
-            };
-            auto plane_pairs = [&](auto mk) {
-                constexpr bool MK = decltype(mk)::value;
-                if (top) return;   // in-plane pairs of the top halo row reach no interior voxel
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int dx = pdx(q), dy = pdy(q);
-                    if (bot && dy != 1) continue;
-                    const int o = cur * PLANE + (wr + dy) * RX + 2 * lane;
-                    const float2 fn = dx == 0 ? lds2(F, o) : lds2(S, o + (dx > 0 ? 0 : -2));
-                    float2 dh;
-                    const float2 e = pair_eval<MK, WANT_H>(fcur, fn, a, (km0 >> (9 + q)) & 1,
-                                                           (km1 >> (9 + q)) & 1, dh);
-                    const unsigned long long wq = (dx != 0 && dy != 0) ? a.w22 : a.w12;
-                    gs = fma2k(e, wq, gs);
-                    if (WANT_H) hs = fma2k(dh, wq, hs);
-                    if (q == 0) e10 = e;
-                    else if (GRAD) *reinterpret_cast<float2 *>(Ep + (q - 1) * PLANE + rs) = e;
-                }
-            };
-            if (full) {
-                if (up) up_pairs(std::false_type{});
-                plane_pairs(std::false_type{});
+        using CUR = std::integral_constant<int, cur>;
+        if (iwarp) {
+            if (full) pairs(std::integral_constant<int, ROLE_IN>{}, std::false_type{}, CUR{}, up, gs, hs, e10);
+            else pairs(std::integral_constant<int, ROLE_IN>{}, std::true_type{}, CUR{}, up, gs, hs, e10);
+        } else if (GRAD) {
+            if (wr == 0) {
+                if (full) pairs(std::integral_constant<int, ROLE_BOT>{}, std::false_type{}, CUR{}, up, gs, hs, e10);
+                else pairs(std::integral_constant<int, ROLE_BOT>{}, std::true_type{}, CUR{}, up, gs, hs, e10);
             } else {
-                if (up) up_pairs(std::true_type{});
-                plane_pairs(std::true_type{});
+                if (full) pairs(std::integral_constant<int, ROLE_TOP>{}, std::false_type{}, CUR{}, up, gs, hs, e10);
+                else pairs(std::integral_constant<int, ROLE_TOP>{}, std::true_type{}, CUR{}, up, gs, hs, e10);
             }
         }
         __syncthreads();
@@ -307,39 +341,36 @@ __global__ void __launch_bounds__(THREADS, MIN_BLOCKS)
         if (own && iwarp) {
             if (GRAD) {
                 const float e10l = __shfl_up_sync(0xffffffffu, e10.y, 1);   // cell 2l - 1, lane l - 1
-                gc = fma2k(make_float2(e10l, e10.x), a.w12, gc);
+                gc = fma2k(make_float2(e10l, e10.x), w1, gc);
                 const float *r1 = Ep + (wr - 1) * RX + 2 * lane;
-                gc = fma2k(make_float2(r1[1], r1[2]), a.w22, gc);                    // (-1,1) from (c+1, y-1)
-                gc = fma2k(lds2(r1 + PLANE, 0), a.w12, gc);                          // (0,1) from (c, y-1)
-                gc = fma2k(make_float2(r1[2 * PLANE - 1], r1[2 * PLANE]), a.w22, gc);  // (1,1) from (c-1, y-1)
+                gc = fma2k(make_float2(r1[1], r1[2]), w2, gc);                       // (-1,1) from (c+1, y-1)
+                gc = fma2k(lds2(r1 + PLANE, 0), w1, gc);                             // (0,1) from (c, y-1)
+                gc = fma2k(make_float2(r1[2 * PLANE - 1], r1[2 * PLANE]), w2, gc);   // (1,1) from (c-1, y-1)
                 const float2 gn = fma2k(sub2(gs, gc), a.gscale2, gold);
                 const float2 out = DOTS ? fma2k(gn, a.nstep2, fcur) : gn;
-                if (ilane) {
-                    if (EVEN) {
-                        if (in0) *reinterpret_cast<float2 *>(g + i) = out;
-                    } else {
-                        if (in0) g[i] = out.x;
-                        if (in1) g[i + 1] = out.y;
-                    }
+                if (EVEN) {
+                    stg2_if(g + i, out, mine0);
+                } else {
+                    stg1_if(g + i, out.x, mine0);
+                    stg1_if(g + i + 1, out.y, mine1);
                 }
                 if (DOTS) {
-                    // <g, f - x_prev>: f - x_prev exactly as dd + de, then exact products
+                    // <g, f - x_prev>: f - x_prev exactly as dd + de, then exact products (TwoSum)
                     float2 de;
                     const float2 dd = two_sum2(fcur, make_float2(-xold.x, -xold.y), de);
-                    float2 gm = gn;
-                    if (!own0) gm.x = 0.f;
-                    if (!own1) gm.y = 0.f;
+                    const float2 gm = make_float2(mine0 ? gn.x : 0.f, mine1 ? gn.y : 0.f);
                     const float2 p1 = mul2(gm, dd);
                     ad1.add(p1, fma2(gm, de, fma2(gm, dd, make_float2(-p1.x, -p1.y))));
-                    const float2 p2 = mul2(gm, gm);
-                    ad2.add(p2, fma2(gm, gm, make_float2(-p2.x, -p2.y)));
+                    // <g, g>: non-negative terms, so the running sum dominates each new
+                    // term after the first and Fast2Sum is exact
+                    const float2 p2v = mul2(gm, gm);
+                    const float2 e2 = fma2(gm, gm, make_float2(-p2v.x, -p2v.y));
+                    const float2 s2 = add2(ad2.s, p2v);
+                    ad2.c = add2(ad2.c, add2(add2(sub2(ad2.s, s2), p2v), e2));
+                    ad2.s = s2;
                 }
             }
-            if (WANT_H) {
-                if (!own0) hs.x = 0.f;
-                if (!own1) hs.y = 0.f;
-                h16 = add2(h16, hs);
-            }
+            if (WANT_H) h16 = add2(h16, make_float2(mine0 ? hs.x : 0.f, mine1 ? hs.y : 0.f));
         }
         if (WANT_H && (z & 15) == 15) {
             ah.add(h16, make_float2(0.f, 0.f));
@@ -383,12 +414,6 @@ PriorArgs make_prior_args(int n, int nb, const tc_prior *pr, double step = 0.0) 
     a.one2 = pack_splat(1.0f);
     a.gscale2 = pack_splat((float)(2.0 * pr->lambda / (pr->sigma * pr->sigma * pr->c)));
     a.nstep2 = pack_splat((float)-step);
-    // w_mn proportional to 1/distance, normalised over the full neighbourhood
-    const double z = pr->dims == 3 ? 6.0 + 12.0 / std::sqrt(2.0) + 8.0 / std::sqrt(3.0)
-                                   : 4.0 + 4.0 / std::sqrt(2.0);
-    a.w12 = pack_splat((float)(1.0 / z));
-    a.w22 = pack_splat((float)(1.0 / (std::sqrt(2.0) * z)));
-    a.w32 = pack_splat((float)(1.0 / (std::sqrt(3.0) * z)));
     return a;
 }
 

@@ -88,3 +88,70 @@ def test_autotune_changes_launch_shape_not_results(api):
             assert torch.equal(api.radon_adj(p, y), a0)
         with pytest.raises(api.TcError):
             p.set_launch(b + 1, 0)
+
+
+# image sides 64..256 with mixed-radix and Bluestein detector lengths, angle
+# counts odd and even, one geometry with arbitrary angles and an axis offset
+GROUP_GEOMS = [dict(n=256, n_angles=48, n_det=362), dict(n=64, n_angles=33, n_det=92),
+               dict(n=128, n_angles=90, n_det=184), dict(n=32, n_angles=7, n_det=48, center_offset=1.5,
+                                                          angles=[0.1, 0.5, 1.1, 1.9, 2.4, 3.0, 3.9])]
+GROUP_COUNTS = [3, 5, 2, 4]
+
+
+def test_plan_group_equals_per_geometry_plans_bitwise(api):
+    """One persistent launch per stage over all geometries: A, A^T, and the
+    MBIR gradient with weights and the 26-neighbour prior (objective terms
+    included) equal those of one plan per geometry bit for bit, eagerly and
+    replayed from a CUDA graph."""
+    dev = torch.device("cuda:0")
+    rng = np.random.default_rng(9)
+    with api.PlanGroup(GROUP_GEOMS, GROUP_COUNTS, device=dev) as grp:
+        x = torch.tensor(rng.standard_normal(grp.image_numel), dtype=torch.float32, device=dev)
+        y = torch.tensor(rng.standard_normal(grp.sino_numel), dtype=torch.float32, device=dev)
+        w = torch.tensor(rng.uniform(0.3, 1.0, grp.sino_numel), dtype=torch.float32, device=dev)
+        prior = api.Prior(lam=2e-3, dims=3)
+        yg = api.radon_fwd_group(grp, x)
+        xg = api.radon_adj_group(grp, y)
+        gg, og = api.mbir_grad_group(grp, x, y, w, prior)
+        torch.cuda.synchronize()
+        ref_y, ref_x, ref_g, ref_o = [], [], [], []
+        for gm, c, xs, ys, ws in zip(GROUP_GEOMS, GROUP_COUNTS, grp.split_images(x), grp.split_sinos(y),
+                                     grp.split_sinos(w)):
+            kw = {k: v for k, v in gm.items() if k not in ("n", "n_angles", "n_det")}
+            if "angles" in kw:
+                kw["angles"] = np.array(kw["angles"])
+            with api.Plan(gm["n"], gm["n_angles"], gm["n_det"], max_batch=c, **kw) as p:
+                ref_y.append(api.radon_fwd(p, xs.contiguous()).flatten())
+                ref_x.append(api.radon_adj(p, ys.contiguous()).flatten())
+                g1, o1 = api.mbir_grad(p, xs.contiguous(), ys.contiguous(), ws.contiguous(), prior)
+                ref_g.append(g1.flatten())
+                ref_o.append(o1)
+                torch.cuda.synchronize()
+        assert torch.equal(yg, torch.cat(ref_y))
+        assert torch.equal(xg, torch.cat(ref_x))
+        assert torch.equal(gg, torch.cat(ref_g))
+        assert torch.equal(og, torch.stack(ref_o))
+        # the same work captured once and replayed
+        yo, xo, go = torch.empty_like(yg), torch.empty_like(xg), torch.empty_like(gg)
+        oo = torch.zeros_like(og)
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            api.radon_fwd_group(grp, x, yo)
+            api.radon_adj_group(grp, y, xo)
+            api.mbir_grad_group(grp, x, y, w, prior, grad=go, obj=oo)
+        for _ in range(2):
+            yo.zero_(), xo.zero_(), go.zero_(), oo.zero_()
+            graph.replay()
+            torch.cuda.synchronize()
+            assert torch.equal(yo, yg) and torch.equal(xo, xg) and torch.equal(go, gg) and torch.equal(oo, og)
+
+
+def test_plan_group_rejects_bad_arguments(api):
+    with pytest.raises(api.TcError):
+        api.PlanGroup([(64, 10, 92)], [0])
+    with pytest.raises(api.TcError):
+        api.PlanGroup([(64, 10, 92), (48, 10, 92)], [1, 1])   # side not a power of two
+    with api.PlanGroup([(64, 10, 92)], [2]) as grp:
+        with pytest.raises(ValueError):
+            api.radon_fwd_group(grp, torch.zeros(grp.image_numel + 1, device="cuda:0"))
