@@ -117,6 +117,25 @@ int tc_plan_autotune(tc_plan *plan, const float *x, float *y, int batch, int rep
  * (0 keeps the current value).  Returns TC_ERR_INVALID_ARG if unsupported. */
 int tc_plan_set_launch(tc_plan *plan, int chunk, int col_pairs);
 
+/* Entries per chunk of the spreading pass (A^T): 256, 512 or 1024 (the
+ * default).  Each grid row's key-sorted entries are staged in shared memory
+ * one chunk at a time, with one gather record per touched cell and chunk;
+ * larger chunks need fewer records and barriers, smaller ones less shared
+ * memory.  Rebuilds the record tables (host, then upload; synchronises the
+ * device).  A cell's contributions are summed chunk by chunk, so a different
+ * chunk regroups that FP32 sum: A^T changes at the rounding level only (each
+ * chunk size on its own is bit-reproducible).  TC_ERR_INVALID_ARG for other
+ * sizes. */
+int tc_plan_set_spread_chunk(tc_plan *plan, int entries);
+/* The plan's current spreading chunk (or TC_ERR_INVALID_ARG for NULL). */
+int tc_plan_get_spread_chunk(const tc_plan *plan);
+/* Autotuner of the spreading chunk: times radon_adj of y [batch][A][D] into
+ * x [batch][N][N] (DEVICE scratch, overwritten) reps times for each chunk
+ * size and keeps the fastest (reported in *chunk_out, HOST, may be NULL).
+ * Synchronous. */
+int tc_plan_autotune_spread(tc_plan *plan, const float *y, float *x, int batch, int reps,
+                            int *chunk_out, void *stream);
+
 /* --------------------------------------------------------------- operators */
 /* y = A x  (Sec. 2.2 NUFFT steps in reverse order).
  *   x  [batch][N][N] float32 in;  y [batch][A][D] float32 out (overwritten).

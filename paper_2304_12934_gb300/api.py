@@ -61,7 +61,8 @@ SYMBOLS = ("tc_status_string", "tc_last_error_detail", "tc_plan_create", "tc_pla
            "tc_plan_status", "tc_selftest_wait_timeout", "radon_normal", "tc_plan_prepare_normal",
            "tc_checkpoint_save", "tc_checkpoint_load", "tc_test_fail_copy_after",
            "tc_plan_group_create", "tc_plan_group_destroy", "tc_plan_group_device_bytes",
-           "radon_fwd_group", "radon_adj_group", "mbir_grad_group")
+           "radon_fwd_group", "radon_adj_group", "mbir_grad_group", "tc_plan_set_spread_chunk",
+           "tc_plan_get_spread_chunk", "tc_plan_autotune_spread")
 
 
 def lib_path() -> str:
@@ -120,13 +121,17 @@ def load(build_if_missing: bool = True):
     L.radon_fwd_group.argtypes = [vp, vp, vp, vp]
     L.radon_adj_group.argtypes = [vp, vp, vp, vp]
     L.mbir_grad_group.argtypes = [vp, vp, vp, vp, ctypes.POINTER(_Prior), vp, vp, vp]
+    L.tc_plan_set_spread_chunk.argtypes = [vp, i]
+    L.tc_plan_get_spread_chunk.argtypes = [vp]
+    L.tc_plan_autotune_spread.argtypes = [vp, vp, vp, i, i, ctypes.POINTER(i), vp]
     for fn in ("tc_profile_enable", "tc_profile_collect", "tc_plan_create", "tc_plan_destroy",
                "radon_fwd", "radon_adj", "mbir_grad", "mbir_power_norm", "mbir_solve",
                "mbir_solve_host", "tc_plan_autotune", "tc_plan_set_launch",
                "tc_prior_grad_noalloc", "radon_normal", "tc_plan_prepare_normal",
                "tc_checkpoint_save", "tc_checkpoint_load", "tc_test_fail_copy_after",
            "tc_plan_group_create", "tc_plan_group_destroy", "tc_plan_group_device_bytes",
-           "radon_fwd_group", "radon_adj_group", "mbir_grad_group"):
+           "radon_fwd_group", "radon_adj_group", "mbir_grad_group", "tc_plan_set_spread_chunk",
+           "tc_plan_get_spread_chunk", "tc_plan_autotune_spread"):
         getattr(L, fn).restype = i
     _LIB = L
     return L
@@ -231,6 +236,26 @@ class Plan:
         (otherwise the first radon_normal call does; needed before graph capture)."""
         _check("tc_plan_prepare_normal", load().tc_plan_prepare_normal(self.handle,
                                                                        _stream(stream, self.device)))
+
+    @property
+    def spread_chunk(self) -> int:
+        """Entries per spreading chunk of A^T (256, 512 or 1024)."""
+        return int(load().tc_plan_get_spread_chunk(self.handle))
+
+    @spread_chunk.setter
+    def spread_chunk(self, entries):
+        _check("tc_plan_set_spread_chunk", load().tc_plan_set_spread_chunk(self.handle, int(entries)))
+
+    def autotune_spread(self, batch=None, reps=2, stream=None) -> int:
+        """Pick the spreading chunk by timing radon_adj (tc_plan_autotune_spread)."""
+        B = self.max_batch if batch is None else int(batch)
+        y = torch.rand(self.sino_shape(B), device=self.device)
+        x = torch.empty(self.image_shape(B), device=self.device)
+        ch = ctypes.c_int()
+        _check("tc_plan_autotune_spread", load().tc_plan_autotune_spread(self.handle, _ptr(y), _ptr(x), B, int(reps),
+                                                                         ctypes.byref(ch),
+                                                                         _stream(stream, self.device)))
+        return ch.value
 
     def set_launch(self, chunk, col_pairs=0):
         """Slices per launch (1..max_batch) and column pairs per CTA (1, 2, 4; 0 keeps)."""

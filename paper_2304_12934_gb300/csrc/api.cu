@@ -14,6 +14,7 @@
 int tc_plan_build(const tc_geom *geom, int max_batch, tc_plan **out);
 void tc_plan_free(tc_plan *p);
 int plan_set_col_pairs(tc_plan *p, int cp);
+int plan_set_spread_chunk(tc_plan *p, int chunk);
 
 namespace {
 
@@ -589,6 +590,52 @@ int tc_plan_autotune(tc_plan *p, const float *x, float *y, int batch, int reps,
     p->chunk = best_chunk;
     if (chunk_out) *chunk_out = best_chunk;
     if (cp_out) *cp_out = best_cp;
+    return TC_OK;
+}
+
+int tc_plan_set_spread_chunk(tc_plan *p, int entries) {
+    if (!p) return TC_ERR_INVALID_ARG;
+    DeviceGuard dg(p->device);
+    if (!dg.ok) return TC_ERR_CUDA;
+    return plan_set_spread_chunk(p, entries);
+}
+
+int tc_plan_get_spread_chunk(const tc_plan *p) { return p ? p->k.chunk : TC_ERR_INVALID_ARG; }
+
+int tc_plan_autotune_spread(tc_plan *p, const float *y, float *x, int batch, int reps, int *chunk_out,
+                            void *stream) {
+    if (!p || batch < 1 || reps < 1 || check_ptrs({x, y}, {})) return TC_ERR_INVALID_ARG;
+    DeviceGuard dg(p->device);
+    if (!dg.ok) return TC_ERR_CUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    TC_CUDA(cudaEventCreate(&e0));
+    TC_CUDA(cudaEventCreate(&e1));
+    float best = -1.f;
+    int best_chunk = p->k.chunk, rc = TC_OK;
+    for (int ch : {256, 512, 1024}) {
+        if ((rc = plan_set_spread_chunk(p, ch))) break;
+        if ((rc = radon_adj(p, y, x, batch, stream))) break;
+        cudaEventRecord(e0, s);
+        for (int r = 0; r < reps && !rc; ++r) rc = radon_adj(p, y, x, batch, stream);
+        cudaEventRecord(e1, s);
+        if (rc) break;
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+            rc = tc_cuda_fail(cudaGetLastError(), "autotune (spread)");
+            break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (best < 0.f || ms < best) {
+            best = ms;
+            best_chunk = ch;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    if ((rc = plan_set_spread_chunk(p, best_chunk))) return rc;
+    if (chunk_out) *chunk_out = best_chunk;
     return TC_OK;
 }
 

@@ -41,6 +41,7 @@ struct KArgs {
     const int2 *rec;           // x: (signed cell - kmin) | seam << 15; y: lo | hi << 16
     const int *rec_off;        // [R][2 nch + 1] record ranges (regular, seam) per row and chunk
     int nch;                   // chunks per row (max over rows)
+    int chunk;                 // entries per spreading chunk (256, 512 or 1024)
     const unsigned char *angle_flip; // [A] 1: theta was in [pi, 2 pi), data conjugated
     const float2 *shiftD;      // [Mh] exp(-2 pi i m delta / D) (axis offset), or null for delta = 0
     RadixPlan rp;              // factorisation of D
@@ -52,7 +53,18 @@ struct KArgs {
     const float2 *twL;         // per-stage twiddle tables of the L-point FFT
 };
 
+#ifdef __cplusplus
+#include <vector>
+#endif
+// Host-side copies a plan keeps to rebuild its spreading records.
+struct PlanHost {
+    std::vector<int> keys;     // jx0 of every entry, key-sorted within each row
+    std::vector<int> row_off;  // [R + 1] first entry of each row
+    size_t n_rec = 0, n_roff = 0;
+};
+
 struct tc_plan {
+    PlanHost *host;       // host copies (see PlanHost)
     int device;
     int max_batch;
     int chunk;            // slices per launch (<= max_batch; set by tc_plan_autotune)
@@ -146,10 +158,9 @@ __device__ __forceinline__ float es_kernel_fast(float z, float beta_l2) {
     return q > 0.0f ? e : 0.0f;
 }
 
-// Entries of one grid row staged per chunk by the spreading kernel.
-#ifndef SPREAD_CHUNK
-#define SPREAD_CHUNK 512
-#endif
+// Entries of one grid row staged per chunk by the spreading kernel: a plan
+// chooses 256, 512 or 1024 (tc_plan_set_spread_chunk); this is the default.
+#define TC_SPREAD_CHUNK_DEFAULT 1024
 
 // Block-wide FP64 sum of one float per thread; thread 0 gets the total.
 __device__ __forceinline__ double block_sum_f64(double d, double *red) {

@@ -1,18 +1,21 @@
 // Batches of slices with uneven geometry (image side, angle count, detector
-// width) in one persistent launch per pipeline stage.
+// width) in persistent launches over work lists.
 //
 // A plan group holds one plan per geometry, sized for all of that geometry's
-// slices, and a work list per stage: every (geometry, slice, tile) item of
-// the stage -- column strips for the column passes, grid rows for the row
-// passes, angle pairs for the detector passes.  A stage runs as one launch of
-// as many CTAs as fit on the GPU at once; each CTA takes the next item from an
-// atomic ticket, runs the same pass body as the per-plan kernels
-// (radon_passes.cuh) with that item's geometry, and takes another until the
-// list is empty.  Items are listed largest geometry first, so the small ones
-// fill the tail.  Stage boundaries are kernel boundaries: no CTA ever waits
-// for another, so nothing can stall on a dependency.  Results equal the
-// per-plan path bit for bit (same bodies, same inputs; the data term's FP64
-// partials are summed in the same order).
+// slices.  Per pipeline stage, the geometries fall into classes that share a
+// launch shape: the image side for the column and row passes, the detector
+// transform (Bluestein length, or mixed radix) for the detector passes.  Each
+// (stage, class) runs as one persistent launch of as many CTAs as fit on the
+// GPU; every CTA takes the next (geometry, slice, tile) item of the class's
+// work list from an atomic ticket -- a column strip, a grid row or an angle
+// pair -- runs the same pass body as the per-plan kernels (radon_passes.cuh)
+// with that item's geometry, and takes another until the list is empty.
+// Items are listed largest geometry first, so the small ones fill the tail.
+// Stage boundaries are kernel boundaries: no CTA ever waits for another.
+// The arithmetic is the per-plan kernels'; results agree with the
+// per-geometry plans to FP32 rounding (separately compiled kernels may fuse a
+// multiply and an add differently), and the data term's FP64 partials are
+// summed in the per-plan order.
 #include <algorithm>
 #include <cstring>
 #include <numeric>
@@ -39,34 +42,137 @@ struct GroupGeom {
     int count;                // slices
     long long xoff, yoff;     // first element of its slices in the concatenated images / sinograms
     int tiles[GS_COUNT];      // items per slice of each stage
-    int start[GS_COUNT];      // first item of each stage's work list
 };
 
+// The persistent loop over the items [first, end) of one class: take tickets
+// until the list is exhausted; f runs item (geometry G, tile t, slice b) with
+// the whole block.  starts[pos] is the first item of the pos-th geometry of the
+// stage's list (geo[pos] its index in gg); the class's geometries begin at
+// position pos0.
 template <class F>
-__device__ __forceinline__ int with_logn_dev(int lg, F &&f) {
-    switch (lg) {
-        case 4: f(std::integral_constant<int, 4>{}); return 0;
-        case 5: f(std::integral_constant<int, 5>{}); return 0;
-        case 6: f(std::integral_constant<int, 6>{}); return 0;
-        case 7: f(std::integral_constant<int, 7>{}); return 0;
-        case 8: f(std::integral_constant<int, 8>{}); return 0;
-        case 9: f(std::integral_constant<int, 9>{}); return 0;
-        case 10: f(std::integral_constant<int, 10>{}); return 0;
-        case 11: f(std::integral_constant<int, 11>{}); return 0;
-        case 12: f(std::integral_constant<int, 12>{}); return 0;
-        default: return 1;
+__device__ __forceinline__ void run_items(const GroupGeom *__restrict__ gg, const int *__restrict__ starts,
+                                          const int *__restrict__ geo, int pos0, int stage, int first, int end,
+                                          int *__restrict__ ticket, F &&f) {
+    __shared__ int item_s;
+    for (;;) {
+        __syncthreads();  // the previous item is done with shared memory and item_s
+        if (threadIdx.x == 0) item_s = first + atomicAdd(ticket, 1);
+        __syncthreads();
+        const int item = item_s;
+        if (item >= end) return;
+        int pos = pos0;
+        while (item >= starts[pos + 1]) ++pos;
+        const GroupGeom &G = gg[geo[pos]];
+        const int local = item - starts[pos], nt = G.tiles[stage];
+        f(G, local % nt, local / nt);
     }
 }
 
-// Detector-pass dispatch: Bluestein at a compile-time length, Bluestein at a
-// run-time length, or the mixed-radix DFT.
+#define GK_ARGS const GroupGeom *__restrict__ gg, const int *__restrict__ starts, const int *__restrict__ geo, \
+                int pos0, int first, int end, int *__restrict__ ticket
+
+template <int LOGN>
+__global__ void __launch_bounds__(512) gk_fwd_col(GK_ARGS, const float *__restrict__ x) {
+    run_items(gg, starts, geo, pos0, GS_FWD_COL, first, end, ticket, [&](const GroupGeom &G, int t, int b) {
+        fwd_col_body<LOGN, false>(x + G.xoff, G.tu, G.k, G.cp, nullptr, nullptr, t, b);
+    });
+}
+
+template <int LOGN>
+__global__ void __launch_bounds__(LOGN == 11 ? 256 : 512, LOGN == 11 ? 5 : 1) gk_fwd_row(GK_ARGS) {
+    run_items(gg, starts, geo, pos0, GS_FWD_ROW, first, end, ticket,
+              [&](const GroupGeom &G, int t, int b) { fwd_row_body<LOGN>(G.tu, G.pv, G.k, t, b); });
+}
+
+// y (sinograms out, may be null), bs and ws (may be null): mode as k_fwd_det
+template <bool BLUE, int LOGL>
+__global__ void __launch_bounds__(512) gk_fwd_det(GK_ARGS, float *__restrict__ y, const float *__restrict__ bs,
+                                                  const float *__restrict__ ws, int mode) {
+    run_items(gg, starts, geo, pos0, GS_FWD_DET, first, end, ticket, [&](const GroupGeom &G, int t, int b) {
+        fwd_det_body<BLUE, LOGL>(G.pv, y ? y + G.yoff : nullptr, bs ? bs + G.yoff : nullptr,
+                                 ws ? ws + G.yoff : nullptr, G.sr, G.part, G.k, mode, t, b, G.tiles[GS_FWD_DET]);
+    });
+}
+
+// the adjoint's input: y (concatenated sinograms), or each geometry's residual when y is null
+template <bool BLUE, int LOGL>
+__global__ void __launch_bounds__(512) gk_adj_det(GK_ARGS, const float *__restrict__ y) {
+    run_items(gg, starts, geo, pos0, GS_ADJ_DET, first, end, ticket, [&](const GroupGeom &G, int t, int b) {
+        adj_det_body<BLUE, LOGL>(y ? y + G.yoff : G.sr, G.pv, G.k, t, b);
+    });
+}
+
+template <int LOGN>
+__global__ void __launch_bounds__(512) gk_adj_row(GK_ARGS) {
+    run_items(gg, starts, geo, pos0, GS_ADJ_ROW, first, end, ticket,
+              [&](const GroupGeom &G, int t, int b) { adj_row_body<LOGN>(G.pv, G.tu, G.k, t, b); });
+}
+
+template <int LOGN>
+__global__ void __launch_bounds__(512) gk_adj_col(GK_ARGS, float *__restrict__ x) {
+    run_items(gg, starts, geo, pos0, GS_ADJ_COL, first, end, ticket, [&](const GroupGeom &G, int t, int b) {
+        adj_col_body<LOGN, COL_DEAPOD>(G.tu, x + G.xoff, G.k, G.cp, nullptr, nullptr, nullptr, t, b,
+                                       G.tiles[GS_ADJ_COL]);
+    });
+}
+
+// obj[2 i] = the data term of geometry i (caller's order): its FP64 partials
+// summed in the order the per-plan reduction uses (k_reduce_finalize), one
+// block each.
+__global__ void gk_data_finalize(const GroupGeom *__restrict__ gg, double *__restrict__ obj) {
+    __shared__ double red[32];
+    const GroupGeom &G = gg[blockIdx.x];
+    const int n = G.count * G.tiles[GS_FWD_DET];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s += G.part[i];
+    const double tot = block_sum_f64(s, red);
+    if (threadIdx.x == 0) obj[2 * blockIdx.x] = 0.0 + 1.0 * tot;
+}
+
+}  // namespace
+
+// One persistent launch: the items [first, end) of one class of one stage.
+struct ClassLaunch {
+    int stage;
+    int key;        // log2 N (column / row passes); Bluestein log2 L, 0 run-time L, -1 mixed radix (detector)
+    int pos0;       // first position of the class in the stage's geometry order
+    int first, end; // item range
+    int grid, threads;
+    size_t smem;
+};
+
+struct tc_plan_group {
+    int device = 0, ng = 0;
+    std::vector<tc_plan *> plans;    // caller's order
+    std::vector<int> counts;
+    std::vector<long long> xoff, yoff;
+    GroupGeom *dgeoms = nullptr;     // caller's order
+    int *dstarts = nullptr;          // [GS_COUNT][ng + 1] first item of each position of the stage's order
+    int *dgeo = nullptr;             // [GS_COUNT][ng] position -> geometry
+    int *tickets = nullptr;          // one per class launch
+    std::vector<ClassLaunch> launches;
+    long long bytes = 0;
+};
+
+namespace {
+
+void group_free(tc_plan_group *g) {
+    if (!g) return;
+    for (tc_plan *p : g->plans) tc_plan_free(p);
+    for (void *q : {(void *)g->dgeoms, (void *)g->dstarts, (void *)g->dgeo, (void *)g->tickets})
+        if (q) cudaFree(q);
+    delete g;
+}
+
+int det_key(const KArgs &k) {
+    if (!k.blue) return -1;
+    return (k.log2L >= 8 && k.log2L <= 13) ? k.log2L : 0;
+}
+
 template <class F>
-__device__ __forceinline__ void with_det_dev(const KArgs &k, F &&f) {
-    if (!k.blue) {
-        f(std::false_type{}, std::integral_constant<int, 0>{});
-        return;
-    }
-    switch (k.log2L) {
+void with_det_key(int key, F &&f) {
+    switch (key) {
+        case -1: f(std::false_type{}, std::integral_constant<int, 0>{}); break;
         case 8: f(std::true_type{}, std::integral_constant<int, 8>{}); break;
         case 9: f(std::true_type{}, std::integral_constant<int, 9>{}); break;
         case 10: f(std::true_type{}, std::integral_constant<int, 10>{}); break;
@@ -77,167 +183,97 @@ __device__ __forceinline__ void with_det_dev(const KArgs &k, F &&f) {
     }
 }
 
-// The persistent loop: take tickets until the stage's list is exhausted; f
-// runs the item (geometry G, tile t, slice b) with the whole block.
+// The kernel of one class launch, handed to f as a function pointer.
 template <class F>
-__device__ __forceinline__ void run_items(const GroupGeom *__restrict__ gg, int ng, int stage, int total,
-                                          int *__restrict__ ticket, F &&f) {
-    __shared__ int item_s;
-    for (;;) {
-        __syncthreads();  // the previous item is done with shared memory and item_s
-        if (threadIdx.x == 0) item_s = atomicAdd(ticket, 1);
-        __syncthreads();
-        const int item = item_s;
-        if (item >= total) return;
-        int gi = 0;
-        while (gi + 1 < ng && item >= gg[gi + 1].start[stage]) ++gi;
-        const GroupGeom &G = gg[gi];
-        const int local = item - G.start[stage], nt = G.tiles[stage];
-        f(G, local % nt, local / nt);
+int with_class_kernel(int stage, int key, F &&f) {
+    int rc = TC_OK;
+    switch (stage) {
+        case GS_FWD_COL: return with_logn(key, [&](auto L) { return f(gk_fwd_col<decltype(L)::value>); });
+        case GS_FWD_ROW: return with_logn(key, [&](auto L) { return f(gk_fwd_row<decltype(L)::value>); });
+        case GS_ADJ_ROW: return with_logn(key, [&](auto L) { return f(gk_adj_row<decltype(L)::value>); });
+        case GS_ADJ_COL: return with_logn(key, [&](auto L) { return f(gk_adj_col<decltype(L)::value>); });
+        case GS_FWD_DET:
+            with_det_key(key, [&](auto blue, auto L) { rc = f(gk_fwd_det<decltype(blue)::value, decltype(L)::value>); });
+            return rc;
+        case GS_ADJ_DET:
+            with_det_key(key, [&](auto blue, auto L) { rc = f(gk_adj_det<decltype(blue)::value, decltype(L)::value>); });
+            return rc;
     }
+    return TC_ERR_INVALID_ARG;
 }
 
-__global__ void __launch_bounds__(512) gk_fwd_col(const GroupGeom *__restrict__ gg, int ng, int total,
-                                                  int *__restrict__ ticket, const float *__restrict__ x) {
-    run_items(gg, ng, GS_FWD_COL, total, ticket, [&](const GroupGeom &G, int t, int b) {
-        with_logn_dev(G.k.log2N, [&](auto L) {
-            fwd_col_body<decltype(L)::value, false>(x + G.xoff, G.tu, G.k, G.cp, nullptr, nullptr, t, b);
-        });
+// Occupancy-sized grid of one class launch (and its shared-memory opt-in).
+int class_config(ClassLaunch &c, int device) {
+    return with_class_kernel(c.stage, c.key, [&](auto *kern) -> int {
+        cudaFuncAttributes at;
+        TC_CUDA(cudaFuncGetAttributes(&at, kern));
+        if ((size_t)at.maxDynamicSharedSizeBytes < c.smem)
+            TC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem));
+        int per_sm = 0, sms = 0;
+        TC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, c.threads, c.smem));
+        TC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
+        if (per_sm < 1) return TC_ERR_UNSUPPORTED;
+        c.grid = std::max(1, std::min(c.end - c.first, per_sm * sms));
+        return TC_OK;
     });
 }
 
-__global__ void __launch_bounds__(512) gk_fwd_row(const GroupGeom *__restrict__ gg, int ng, int total,
-                                                  int *__restrict__ ticket) {
-    run_items(gg, ng, GS_FWD_ROW, total, ticket, [&](const GroupGeom &G, int t, int b) {
-        with_logn_dev(G.k.log2N, [&](auto L) { fwd_row_body<decltype(L)::value>(G.tu, G.pv, G.k, t, b); });
-    });
-}
-
-// y (images' sinograms, may be null), b and w (may be null): mode as k_fwd_det
-__global__ void __launch_bounds__(512) gk_fwd_det(const GroupGeom *__restrict__ gg, int ng, int total,
-                                                  int *__restrict__ ticket, float *__restrict__ y,
-                                                  const float *__restrict__ bs, const float *__restrict__ ws,
-                                                  int mode) {
-    run_items(gg, ng, GS_FWD_DET, total, ticket, [&](const GroupGeom &G, int t, int b) {
-        with_det_dev(G.k, [&](auto blue, auto L) {
-            fwd_det_body<decltype(blue)::value, decltype(L)::value>(
-                G.pv, y ? y + G.yoff : nullptr, bs ? bs + G.yoff : nullptr, ws ? ws + G.yoff : nullptr, G.sr,
-                G.part, G.k, mode, t, b, G.tiles[GS_FWD_DET]);
-        });
-    });
-}
-
-// the adjoint's input: y (concatenated sinograms), or each geometry's residual when y is null
-__global__ void __launch_bounds__(512) gk_adj_det(const GroupGeom *__restrict__ gg, int ng, int total,
-                                                  int *__restrict__ ticket, const float *__restrict__ y) {
-    run_items(gg, ng, GS_ADJ_DET, total, ticket, [&](const GroupGeom &G, int t, int b) {
-        with_det_dev(G.k, [&](auto blue, auto L) {
-            adj_det_body<decltype(blue)::value, decltype(L)::value>(y ? y + G.yoff : G.sr, G.pv, G.k, t, b);
-        });
-    });
-}
-
-__global__ void __launch_bounds__(512) gk_adj_row(const GroupGeom *__restrict__ gg, int ng, int total,
-                                                  int *__restrict__ ticket) {
-    run_items(gg, ng, GS_ADJ_ROW, total, ticket, [&](const GroupGeom &G, int t, int b) {
-        with_logn_dev(G.k.log2N, [&](auto L) { adj_row_body<decltype(L)::value>(G.pv, G.tu, G.k, t, b); });
-    });
-}
-
-__global__ void __launch_bounds__(512) gk_adj_col(const GroupGeom *__restrict__ gg, int ng, int total,
-                                                  int *__restrict__ ticket, float *__restrict__ x) {
-    run_items(gg, ng, GS_ADJ_COL, total, ticket, [&](const GroupGeom &G, int t, int b) {
-        with_logn_dev(G.k.log2N, [&](auto L) {
-            adj_col_body<decltype(L)::value, COL_DEAPOD>(G.tu, x + G.xoff, G.k, G.cp, nullptr, nullptr, nullptr, t,
-                                                         b, G.tiles[GS_ADJ_COL]);
-        });
-    });
-}
-
-// obj[2 gi] = the data term of geometry gi: its FP64 partials summed in the
-// order the per-plan reduction uses (k_reduce_finalize), one block each.
-__global__ void gk_data_finalize(const GroupGeom *__restrict__ gg, const int *__restrict__ caller_index,
-                                 double *__restrict__ obj) {
-    __shared__ double red[32];
-    const GroupGeom &G = gg[blockIdx.x];
-    const int n = G.count * G.tiles[GS_FWD_DET];
-    double s = 0.0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) s += G.part[i];
-    const double tot = block_sum_f64(s, red);
-    if (threadIdx.x == 0) obj[2 * caller_index[blockIdx.x]] = 0.0 + 1.0 * tot;
-}
-
-}  // namespace
-
-struct tc_plan_group {
-    int device = 0, ng = 0;
-    std::vector<tc_plan *> plans;    // caller's order
-    std::vector<int> counts;
-    std::vector<long long> xoff, yoff;
-    std::vector<int> order;          // work-list position -> caller index
-    GroupGeom *dgeoms = nullptr;     // work-list order
-    int *dorder = nullptr;           // work-list position -> caller index (device)
-    int *tickets = nullptr;          // [GS_COUNT]
-    int total[GS_COUNT] = {};
-    int grid[GS_COUNT] = {}, threads[GS_COUNT] = {};
-    size_t smem[GS_COUNT] = {};
-    long long bytes = 0;
-};
-
-namespace {
-
-void group_free(tc_plan_group *g) {
-    if (!g) return;
-    for (tc_plan *p : g->plans) tc_plan_free(p);
-    if (g->dgeoms) cudaFree(g->dgeoms);
-    if (g->dorder) cudaFree(g->dorder);
-    if (g->tickets) cudaFree(g->tickets);
-    delete g;
-}
-
-template <class K>
-int stage_config(tc_plan_group *g, int st, K *kern, int threads, size_t smem) {
-    cudaFuncAttributes at;
-    TC_CUDA(cudaFuncGetAttributes(&at, kern));
-    if ((size_t)at.maxDynamicSharedSizeBytes < smem)
-        TC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int per_sm = 0, sms = 0;
-    TC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
-    TC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device));
-    if (per_sm < 1) return TC_ERR_UNSUPPORTED;
-    g->threads[st] = threads;
-    g->smem[st] = smem;
-    g->grid[st] = std::max(1, std::min(g->total[st], per_sm * sms));
-    return TC_OK;
-}
-
+// Runs every class launch of one stage (x: images in; y: sinograms in or
+// out; b, w, mode: the forward detector pass's epilogue; xo: images out).
 int launch_stage(tc_plan_group *g, int st, cudaStream_t s, const float *x, float *y, const float *b,
                  const float *w, int mode, float *xo) {
-    const dim3 grid(g->grid[st]), blk(g->threads[st]);
-    const size_t sm = g->smem[st];
-    int *tk = g->tickets + st;
-    switch (st) {
-        case GS_FWD_COL:
-            TC_PROFILED(TCK_FWD_COL, s, gk_fwd_col<<<grid, blk, sm, s>>>(g->dgeoms, g->ng, g->total[st], tk, x));
-            break;
-        case GS_FWD_ROW:
-            TC_PROFILED(TCK_FWD_ROW, s, gk_fwd_row<<<grid, blk, sm, s>>>(g->dgeoms, g->ng, g->total[st], tk));
-            break;
-        case GS_FWD_DET:
-            TC_PROFILED(TCK_FWD_DET, s,
-                        gk_fwd_det<<<grid, blk, sm, s>>>(g->dgeoms, g->ng, g->total[st], tk, y, b, w, mode));
-            break;
-        case GS_ADJ_DET:
-            TC_PROFILED(TCK_ADJ_DET, s, gk_adj_det<<<grid, blk, sm, s>>>(g->dgeoms, g->ng, g->total[st], tk, y));
-            break;
-        case GS_ADJ_ROW:
-            TC_PROFILED(TCK_ADJ_ROW, s, gk_adj_row<<<grid, blk, sm, s>>>(g->dgeoms, g->ng, g->total[st], tk));
-            break;
-        case GS_ADJ_COL:
-            TC_PROFILED(TCK_ADJ_COL, s, gk_adj_col<<<grid, blk, sm, s>>>(g->dgeoms, g->ng, g->total[st], tk, xo));
-            break;
+    const int *starts = g->dstarts + (size_t)st * (g->ng + 1), *geo = g->dgeo + (size_t)st * g->ng;
+    for (size_t li = 0; li < g->launches.size(); ++li) {
+        const ClassLaunch &c = g->launches[li];
+        if (c.stage != st) continue;
+        int *tk = g->tickets + li;
+        const dim3 grid(c.grid), blk(c.threads);
+        const size_t sm = c.smem;
+#define GK_PASS g->dgeoms, starts, geo, c.pos0, c.first, c.end, tk
+        int rc = TC_OK;
+        switch (st) {
+            case GS_FWD_COL:
+                rc = with_logn(c.key, [&](auto L) {
+                    TC_PROFILED(TCK_FWD_COL, s, (gk_fwd_col<decltype(L)::value><<<grid, blk, sm, s>>>(GK_PASS, x)));
+                    return TC_OK;
+                });
+                break;
+            case GS_FWD_ROW:
+                rc = with_logn(c.key, [&](auto L) {
+                    TC_PROFILED(TCK_FWD_ROW, s, (gk_fwd_row<decltype(L)::value><<<grid, blk, sm, s>>>(GK_PASS)));
+                    return TC_OK;
+                });
+                break;
+            case GS_FWD_DET:
+                with_det_key(c.key, [&](auto blue, auto L) {
+                    TC_PROFILED(TCK_FWD_DET, s,
+                                (gk_fwd_det<decltype(blue)::value, decltype(L)::value>
+                                 <<<grid, blk, sm, s>>>(GK_PASS, y, b, w, mode)));
+                });
+                break;
+            case GS_ADJ_DET:
+                with_det_key(c.key, [&](auto blue, auto L) {
+                    TC_PROFILED(TCK_ADJ_DET, s,
+                                (gk_adj_det<decltype(blue)::value, decltype(L)::value><<<grid, blk, sm, s>>>(GK_PASS, y)));
+                });
+                break;
+            case GS_ADJ_ROW:
+                rc = with_logn(c.key, [&](auto L) {
+                    TC_PROFILED(TCK_ADJ_ROW, s, (gk_adj_row<decltype(L)::value><<<grid, blk, sm, s>>>(GK_PASS)));
+                    return TC_OK;
+                });
+                break;
+            case GS_ADJ_COL:
+                rc = with_logn(c.key, [&](auto L) {
+                    TC_PROFILED(TCK_ADJ_COL, s, (gk_adj_col<decltype(L)::value><<<grid, blk, sm, s>>>(GK_PASS, xo)));
+                    return TC_OK;
+                });
+                break;
+        }
+#undef GK_PASS
+        if (rc) return rc;
+        TC_LAUNCHED("grouped pass");
     }
-    TC_LAUNCHED("grouped pass");
     return TC_OK;
 }
 
@@ -266,13 +302,15 @@ int tc_plan_group_create(const tc_geom *geoms, const int *counts, int n_geoms, t
     for (int i = 0; i < n_geoms; ++i)
         if (counts[i] < 1 || counts[i] > 65535) return TC_ERR_INVALID_ARG;
     tc_plan_group *g = new tc_plan_group();
-    g->ng = n_geoms;
+    const int n = n_geoms;
+    g->ng = n;
     if (cudaGetDevice(&g->device) != cudaSuccess) {
         delete g;
         return TC_ERR_CUDA;
     }
     long long xo = 0, yo = 0;
-    for (int i = 0; i < n_geoms; ++i) {
+    std::vector<GroupGeom> hg(n);
+    for (int i = 0; i < n; ++i) {
         tc_plan *p = nullptr;
         const int rc = tc_plan_create(&geoms[i], counts[i], &p);
         if (rc) {
@@ -283,24 +321,7 @@ int tc_plan_group_create(const tc_geom *geoms, const int *counts, int n_geoms, t
         g->counts.push_back(counts[i]);
         g->xoff.push_back(xo);
         g->yoff.push_back(yo);
-        xo += (long long)counts[i] * p->k.N * p->k.N;
-        yo += (long long)counts[i] * p->k.A * p->k.D;
-        g->bytes += p->bytes;
-    }
-    // work list: largest geometries (by image work) first
-    g->order.resize(n_geoms);
-    std::iota(g->order.begin(), g->order.end(), 0);
-    std::stable_sort(g->order.begin(), g->order.end(), [&](int a, int b) {
-        const tc_plan *pa = g->plans[a], *pb = g->plans[b];
-        return (long long)pa->k.N * pa->k.N * g->counts[a] > (long long)pb->k.N * pb->k.N * g->counts[b];
-    });
-    std::vector<GroupGeom> hg(n_geoms);
-    int thr_col = 0, thr_row = 0, thr_det = 0;
-    size_t sm_col = 0, sm_rowf = 0, sm_rowa = 0, sm_det = 0;
-    for (int j = 0; j < n_geoms; ++j) {
-        const int i = g->order[j];
-        tc_plan *p = g->plans[i];
-        GroupGeom &G = hg[j];
+        GroupGeom &G = hg[i];
         std::memset(&G, 0, sizeof(G));
         G.k = p->k;
         G.tu = p->tu;
@@ -308,46 +329,79 @@ int tc_plan_group_create(const tc_geom *geoms, const int *counts, int n_geoms, t
         G.sr = p->sr;
         G.part = p->partials;
         G.cp = p->cp_col;
-        G.count = g->counts[i];
-        G.xoff = g->xoff[i];
-        G.yoff = g->yoff[i];
+        G.count = counts[i];
+        G.xoff = xo;
+        G.yoff = yo;
         const int col = p->k.N / (2 * p->cp_col), rows = p->k.R, det = (p->k.A + 1) / 2;
         const int tiles[GS_COUNT] = {col, rows, det, det, rows, col};
-        for (int st = 0; st < GS_COUNT; ++st) {
-            G.tiles[st] = tiles[st];
-            G.start[st] = g->total[st];
-            const long long t = (long long)g->total[st] + (long long)tiles[st] * G.count;
-            if (t >= (1LL << 31)) {
+        for (int st = 0; st < GS_COUNT; ++st) G.tiles[st] = tiles[st];
+        xo += (long long)counts[i] * p->k.N * p->k.N;
+        yo += (long long)counts[i] * p->k.A * p->k.D;
+        g->bytes += p->bytes;
+    }
+    // per stage: geometries ordered by class, then largest first; one launch per class
+    std::vector<int> starts((size_t)GS_COUNT * (n + 1)), geo((size_t)GS_COUNT * n);
+    for (int st = 0; st < GS_COUNT; ++st) {
+        const bool det = st == GS_FWD_DET || st == GS_ADJ_DET;
+        auto key = [&](int i) { return det ? det_key(g->plans[i]->k) : g->plans[i]->k.log2N; };
+        auto cost = [&](int i) { return (long long)hg[i].tiles[st] * hg[i].count; };
+        std::vector<int> ord(n);
+        std::iota(ord.begin(), ord.end(), 0);
+        std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) {
+            return key(a) != key(b) ? key(a) < key(b) : cost(a) > cost(b);
+        });
+        long long item = 0;
+        for (int pos = 0; pos < n; ++pos) {
+            geo[(size_t)st * n + pos] = ord[pos];
+            starts[(size_t)st * (n + 1) + pos] = (int)item;
+            item += cost(ord[pos]);
+            if (item >= (1LL << 31)) {
                 group_free(g);
                 return TC_ERR_UNSUPPORTED;
             }
-            g->total[st] = (int)t;
         }
-        thr_col = std::max(thr_col, p->threads_col);
-        thr_row = std::max(thr_row, p->threads_row);
-        thr_det = std::max(thr_det, p->threads_det);
-        sm_col = std::max(sm_col, p->smem_col);
-        sm_rowf = std::max(sm_rowf, p->smem_row_fwd);
-        sm_rowa = std::max(sm_rowa, p->smem_row_adj);
-        sm_det = std::max(sm_det, p->smem_det);
+        starts[(size_t)st * (n + 1) + n] = (int)item;
+        for (int p0 = 0; p0 < n;) {
+            int p1 = p0;
+            ClassLaunch c{};
+            c.stage = st;
+            c.key = key(ord[p0]);
+            c.pos0 = p0;
+            while (p1 < n && key(ord[p1]) == c.key) {
+                const tc_plan *p = g->plans[ord[p1]];
+                if (st == GS_FWD_COL || st == GS_ADJ_COL) {
+                    c.threads = std::max(c.threads, p->threads_col);
+                    c.smem = std::max(c.smem, p->smem_col);
+                } else if (st == GS_FWD_ROW || st == GS_ADJ_ROW) {
+                    c.threads = std::max(c.threads, p->threads_row);
+                    c.smem = std::max(c.smem, st == GS_FWD_ROW ? p->smem_row_fwd : p->smem_row_adj);
+                } else {
+                    c.threads = std::max(c.threads, p->threads_det);
+                    c.smem = std::max(c.smem, p->smem_det);
+                }
+                ++p1;
+            }
+            c.first = starts[(size_t)st * (n + 1) + p0];
+            c.end = starts[(size_t)st * (n + 1) + p1];
+            if (c.end > c.first) g->launches.push_back(c);
+            p0 = p1;
+        }
     }
     int rc = TC_OK;
-    if (cudaMalloc(&g->dgeoms, sizeof(GroupGeom) * n_geoms) != cudaSuccess ||
-        cudaMalloc(&g->dorder, sizeof(int) * n_geoms) != cudaSuccess ||
-        cudaMalloc(&g->tickets, sizeof(int) * GS_COUNT) != cudaSuccess) {
+    if (cudaMalloc(&g->dgeoms, sizeof(GroupGeom) * n) != cudaSuccess ||
+        cudaMalloc(&g->dstarts, sizeof(int) * starts.size()) != cudaSuccess ||
+        cudaMalloc(&g->dgeo, sizeof(int) * geo.size()) != cudaSuccess ||
+        cudaMalloc(&g->tickets, sizeof(int) * std::max<size_t>(1, g->launches.size())) != cudaSuccess) {
         cudaGetLastError();
         group_free(g);
         return TC_ERR_OOM;
     }
-    if (cudaMemcpy(g->dgeoms, hg.data(), sizeof(GroupGeom) * n_geoms, cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(g->dorder, g->order.data(), sizeof(int) * n_geoms, cudaMemcpyHostToDevice) != cudaSuccess)
+    if (cudaMemcpy(g->dgeoms, hg.data(), sizeof(GroupGeom) * n, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(g->dstarts, starts.data(), sizeof(int) * starts.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(g->dgeo, geo.data(), sizeof(int) * geo.size(), cudaMemcpyHostToDevice) != cudaSuccess)
         rc = tc_cuda_fail(cudaGetLastError(), "tc_plan_group_create");
-    if (!rc) rc = stage_config(g, GS_FWD_COL, gk_fwd_col, thr_col, sm_col);
-    if (!rc) rc = stage_config(g, GS_FWD_ROW, gk_fwd_row, thr_row, sm_rowf);
-    if (!rc) rc = stage_config(g, GS_FWD_DET, gk_fwd_det, thr_det, sm_det);
-    if (!rc) rc = stage_config(g, GS_ADJ_DET, gk_adj_det, thr_det, sm_det);
-    if (!rc) rc = stage_config(g, GS_ADJ_ROW, gk_adj_row, thr_row, sm_rowa);
-    if (!rc) rc = stage_config(g, GS_ADJ_COL, gk_adj_col, thr_col, sm_col);
+    for (ClassLaunch &c : g->launches)
+        if (!rc) rc = class_config(c, g->device);
     if (rc) {
         group_free(g);
         return rc;
@@ -371,7 +425,7 @@ int radon_fwd_group(tc_plan_group *g, const float *x, float *y, void *stream) {
     GroupDevice dg(g->device);
     if (!dg.ok) return TC_ERR_CUDA;
     cudaStream_t s = (cudaStream_t)stream;
-    TC_CUDA(cudaMemsetAsync(g->tickets, 0, sizeof(int) * GS_COUNT, s));
+    TC_CUDA(cudaMemsetAsync(g->tickets, 0, sizeof(int) * g->launches.size(), s));
     int rc;
     if ((rc = launch_stage(g, GS_FWD_COL, s, x, nullptr, nullptr, nullptr, 0, nullptr)) ||
         (rc = launch_stage(g, GS_FWD_ROW, s, nullptr, nullptr, nullptr, nullptr, 0, nullptr)) ||
@@ -385,7 +439,7 @@ int radon_adj_group(tc_plan_group *g, const float *y, float *x, void *stream) {
     GroupDevice dg(g->device);
     if (!dg.ok) return TC_ERR_CUDA;
     cudaStream_t s = (cudaStream_t)stream;
-    TC_CUDA(cudaMemsetAsync(g->tickets, 0, sizeof(int) * GS_COUNT, s));
+    TC_CUDA(cudaMemsetAsync(g->tickets, 0, sizeof(int) * g->launches.size(), s));
     int rc;
     if ((rc = launch_stage(g, GS_ADJ_DET, s, nullptr, const_cast<float *>(y), nullptr, nullptr, 0, nullptr)) ||
         (rc = launch_stage(g, GS_ADJ_ROW, s, nullptr, nullptr, nullptr, nullptr, 0, nullptr)) ||
@@ -404,7 +458,7 @@ int mbir_grad_group(tc_plan_group *g, const float *x, const float *b, const floa
     GroupDevice dg(g->device);
     if (!dg.ok) return TC_ERR_CUDA;
     cudaStream_t s = (cudaStream_t)stream;
-    TC_CUDA(cudaMemsetAsync(g->tickets, 0, sizeof(int) * GS_COUNT, s));
+    TC_CUDA(cudaMemsetAsync(g->tickets, 0, sizeof(int) * g->launches.size(), s));
     if (obj) TC_CUDA(cudaMemsetAsync(obj, 0, sizeof(double) * 2 * g->ng, s));
     const int mode = DET_RESID | (obj ? DET_OBJ : 0);
     int rc;
@@ -413,7 +467,7 @@ int mbir_grad_group(tc_plan_group *g, const float *x, const float *b, const floa
         (rc = launch_stage(g, GS_FWD_DET, s, nullptr, nullptr, b, w, mode, nullptr)))
         return rc;
     if (obj) {
-        TC_PROFILED(TCK_REDUCE, s, gk_data_finalize<<<g->ng, 256, 0, s>>>(g->dgeoms, g->dorder, obj));
+        TC_PROFILED(TCK_REDUCE, s, gk_data_finalize<<<g->ng, 256, 0, s>>>(g->dgeoms, obj));
         TC_LAUNCHED("gk_data_finalize");
     }
     if ((rc = launch_stage(g, GS_ADJ_DET, s, nullptr, nullptr, nullptr, nullptr, 0, nullptr)) ||

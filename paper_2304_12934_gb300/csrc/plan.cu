@@ -185,7 +185,106 @@ int alloc_dev(void **dst, size_t nb, long long &bytes) {
     return TC_OK;
 }
 
+// Spreading records of one chunk size.  Within each row the key-sorted
+// entries are cut into chunks of `chunk`; for every chunk and every signed cell
+// cs touched by one of its entries (cs in [key, key + w - 1]), the entries that
+// touch cs are those with key in [cs - w + 1, cs]: a contiguous range [lo, hi)
+// of the chunk.  A record (cs, lo, hi) lets one thread compute the chunk's
+// whole contribution to cell cs mod G.  When two signed cells of a chunk share
+// a physical cell (the spectrum edge wraps, cs and cs + G), the later record is
+// flagged "seam" and added serially.  Per row, roff holds [start_0, seam_0,
+// start_1, seam_1, ..., start_nch]; the seam records of chunk k are
+// [seam_k, start_{k+1}), after its regular ones.  Returns nch, the chunks per
+// row (the maximum over rows).
+int build_spread_records(const std::vector<int> &keys, const std::vector<int> &cnt, int R, int w, int G, int kmin,
+                         int chunk, std::vector<int2> &recs, std::vector<int> &roff) {
+    recs.clear();
+    int nch = 1;
+    for (int r = 0; r < R; ++r) nch = std::max(nch, (cnt[r + 1] - cnt[r] + chunk - 1) / chunk);
+    roff.assign((size_t)R * (2 * nch + 1), 0);
+    std::vector<int> last_use(G, -1);
+    std::vector<int2> seams;
+    int stamp = 0;
+    for (int r = 0; r < R; ++r) {
+        const int e0 = cnt[r], e1 = cnt[r + 1];
+        for (int kc = 0; kc <= nch; ++kc) {
+            int *ro = &roff[(size_t)r * (2 * nch + 1)];
+            ro[2 * kc] = (int)recs.size();
+            if (kc == nch) continue;
+            ro[2 * kc + 1] = (int)recs.size();
+            const int c0 = e0 + kc * chunk;
+            if (c0 >= e1) continue;
+            seams.clear();
+            const int n = std::min(chunk, e1 - c0);
+            ++stamp;
+            // signed cells touched, in increasing order: walk the sorted keys
+            int lo = 0, hi = 0;
+            int cs = keys[c0];
+            const int cs_end = keys[c0 + n - 1] + w - 1;
+            while (cs <= cs_end) {
+                while (lo < n && keys[c0 + lo] < cs - w + 1) ++lo;
+                while (hi < n && keys[c0 + hi] <= cs) ++hi;
+                if (hi > lo) {
+                    const int cp = cs & (G - 1);
+                    const int seam = last_use[cp] == stamp ? 1 : 0;
+                    last_use[cp] = stamp;
+                    int2 rc;
+                    rc.x = (cs - kmin) | (seam << 15);
+                    rc.y = lo | (hi << 16);
+                    (seam ? seams : recs).push_back(rc);
+                    ++cs;
+                } else {
+                    // no entry touches cs: jump to the next key's window
+                    cs = (lo < n) ? std::max(cs + 1, keys[c0 + lo]) : cs_end + 1;
+                }
+            }
+            // longest ranges first: the threads that take them start early
+            std::stable_sort(recs.begin() + ro[2 * kc], recs.end(), [](const int2 &u, const int2 &v) {
+                return ((u.y >> 16) - (u.y & 0xffff)) > ((v.y >> 16) - (v.y & 0xffff));
+            });
+            ro[2 * kc + 1] = (int)recs.size();
+            recs.insert(recs.end(), seams.begin(), seams.end());
+        }
+    }
+    return nch;
+}
+
 }  // namespace
+
+// Entries per spreading chunk: rebuild the record tables for `chunk` (256,
+// 512 or 1024) and replace them on the device (synchronous).
+int plan_set_spread_chunk(tc_plan *p, int chunk) {
+    if (!(chunk == 256 || chunk == 512 || chunk == 1024) || !p->host) return TC_ERR_INVALID_ARG;
+    if (chunk == p->k.chunk) return TC_OK;
+    KArgs &k = p->k;
+    std::vector<int2> recs;
+    std::vector<int> roff;
+    const int nch = build_spread_records(p->host->keys, p->host->row_off, k.R, k.w, k.G, k.kmin, chunk, recs, roff);
+    int2 *nrec = nullptr;
+    int *nroff = nullptr;
+    long long bytes = 0;
+    int rc = upload(&nrec, recs, bytes);
+    if (!rc) rc = upload(&nroff, roff, bytes);
+    if (rc) {
+        if (nrec) cudaFree(nrec);
+        return rc;
+    }
+    TC_CUDA(cudaDeviceSynchronize());  // no launch may still read the old tables
+    const long long old = (long long)((size_t)p->host->n_rec * sizeof(int2) + (size_t)p->host->n_roff * sizeof(int));
+    cudaFree(p->rec);
+    cudaFree(p->rec_off);
+    p->rec = nrec;
+    p->rec_off = nroff;
+    p->bytes += bytes - old;
+    p->host->n_rec = recs.size();
+    p->host->n_roff = roff.size();
+    k.rec = nrec;
+    k.rec_off = nroff;
+    k.nch = nch;
+    k.chunk = chunk;
+    p->smem_row_adj = p->smem_row_fwd + (size_t)chunk * sizeof(float4);
+    return radon_configure_kernels(p);
+}
 
 // Column pairs per CTA of the column passes: threads, shared memory (the
 // kernels' dynamic-smem limit is raised to the largest candidate at build).
@@ -211,6 +310,7 @@ void tc_plan_free(tc_plan *p) {
                     p->nrm_part};
     for (void *q : ptrs)
         if (q) cudaFree(q);
+    delete p->host;
     delete p;
 }
 
@@ -343,71 +443,20 @@ int tc_plan_build(const tc_geom *geom, int max_batch, tc_plan **out) {
     }
     p->n_entries = (long long)E;
 
-    // Spreading records.  Within each row the entries are cut into chunks of
-    // SPREAD_CHUNK; for every chunk and every signed cell cs touched by one of
-    // its entries (cs in [key, key + w - 1]), the entries that touch cs are
-    // those with key in [cs - w + 1, cs]: a contiguous range [lo, hi) of the
-    // key-sorted chunk.  A record (cs, lo, hi) lets one thread compute the
-    // chunk's whole contribution to cell cs mod G.  When two signed cells of a
-    // chunk share a physical cell (the spectrum edge wraps, cs and cs + G), the
-    // later record is flagged "seam" and added serially.
-    std::vector<int2> recs;
-    int nch = 1;
-    for (int r = 0; r < R; ++r) nch = std::max(nch, (cnt[r + 1] - cnt[r] + SPREAD_CHUNK - 1) / SPREAD_CHUNK);
-    // per row: [start_0, seam_0, start_1, seam_1, ..., start_nch]; the seam
-    // records of chunk k are [seam_k, start_{k+1}), after its regular ones
-    std::vector<int> roff((size_t)R * (2 * nch + 1), 0);
-    {
-        std::vector<int> last_use(G, -1);
-        std::vector<int2> seams;
-        int stamp = 0;
-        for (int r = 0; r < R; ++r) {
-            const int e0 = cnt[r], e1 = cnt[r + 1];
-            for (int kc = 0; kc <= nch; ++kc) {
-                int *ro = &roff[(size_t)r * (2 * nch + 1)];
-                ro[2 * kc] = (int)recs.size();
-                if (kc == nch) continue;
-                ro[2 * kc + 1] = (int)recs.size();
-                const int c0 = e0 + kc * SPREAD_CHUNK;
-                if (c0 >= e1) continue;
-                seams.clear();
-                const int n = std::min(SPREAD_CHUNK, e1 - c0);
-                ++stamp;
-                // signed cells touched, in increasing order: walk the sorted keys
-                int lo = 0, hi = 0;
-                int cs = ents[c0].key;
-                const int cs_end = ents[c0 + n - 1].key + w - 1;
-                while (cs <= cs_end) {
-                    while (lo < n && ents[c0 + lo].key < cs - w + 1) ++lo;
-                    while (hi < n && ents[c0 + hi].key <= cs) ++hi;
-                    if (hi > lo) {
-                        const int cp = cs & (G - 1);
-                        const int seam = last_use[cp] == stamp ? 1 : 0;
-                        last_use[cp] = stamp;
-                        int2 rc;
-                        rc.x = (cs - kmin) | (seam << 15);
-                        rc.y = lo | (hi << 16);
-                        (seam ? seams : recs).push_back(rc);
-                        ++cs;
-                    } else {
-                        // no entry touches cs: jump to the next key's window
-                        cs = (lo < n) ? std::max(cs + 1, ents[c0 + lo].key) : cs_end + 1;
-                    }
-                }
-                // longest ranges first: the threads that take them start early
-                std::stable_sort(recs.begin() + ro[2 * kc], recs.end(), [](const int2 &u, const int2 &v) {
-                    return ((u.y >> 16) - (u.y & 0xffff)) > ((v.y >> 16) - (v.y & 0xffff));
-                });
-                ro[2 * kc + 1] = (int)recs.size();
-                recs.insert(recs.end(), seams.begin(), seams.end());
-            }
-        }
-        if ((long long)kmax + w - 1 - kmin >= (1 << 15)) {
-            tc_plan_free(p);
-            return TC_ERR_UNSUPPORTED;
-        }
+    // spreading records for the default chunk; the entry keys and row offsets
+    // stay on the host so the chunk can be changed later (tc_plan_set_spread_chunk)
+    p->host = new PlanHost();
+    p->host->keys.resize(E);
+    for (size_t i = 0; i < E; ++i) p->host->keys[i] = ents[i].key;
+    p->host->row_off = cnt;
+    if ((long long)kmax + w - 1 - kmin >= (1 << 15)) {
+        tc_plan_free(p);
+        return TC_ERR_UNSUPPORTED;
     }
-    k.nch = nch;
+    std::vector<int2> recs;
+    std::vector<int> roff;
+    k.chunk = TC_SPREAD_CHUNK_DEFAULT;
+    k.nch = build_spread_records(p->host->keys, cnt, R, w, G, kmin, k.chunk, recs, roff);
 
     // Bluestein tables when D has a large prime factor (and L stays <= 8192)
     std::vector<float2> chirp, bhat, twL;
@@ -489,6 +538,8 @@ int tc_plan_build(const tc_geom *geom, int max_batch, tc_plan **out) {
     UP(p->ent, epk);
     UP(p->rec, recs);
     UP(p->rec_off, roff);
+    p->host->n_rec = recs.size();
+    p->host->n_roff = roff.size();
     UP(p->angle_flip, flip);
     UP(p->shiftD, shiftD);
     UP(p->chirp, chirp);
@@ -522,7 +573,7 @@ int tc_plan_build(const tc_geom *geom, int max_batch, tc_plan **out) {
     p->threads_row = std::max(128, N / 8);
     p->threads_det = k.blue ? std::max(256, k.L / 16) : 256;
     p->smem_row_fwd = (size_t)(2 * fft_tstride(N)) * sizeof(float2);
-    p->smem_row_adj = p->smem_row_fwd + (size_t)SPREAD_CHUNK * sizeof(float4);
+    p->smem_row_adj = p->smem_row_fwd + (size_t)k.chunk * sizeof(float4);
     p->smem_det = k.blue ? (size_t)spad_size(k.L) * sizeof(float2)
                          : (size_t)(3 * D + k.rp.rad[0]) * sizeof(float2);
     if (p->threads_row > 512 || p->smem_det > 200 * 1024 || p->smem_row_adj > 200 * 1024) {

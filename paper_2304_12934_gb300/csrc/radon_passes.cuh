@@ -332,13 +332,14 @@ __device__ __forceinline__ void adj_row_body(const float2 *__restrict__ V, float
     constexpr int N = 1 << LOGN, G = 2 * N;
     constexpr int ts = fft_tstride(N), hsz = 2 * ts;              // grid row: 2 transforms
     // staged entries: (u = phi_y V[p], key, -ex / h); hsz is even, so 16-byte aligned
-    float4 *ce = reinterpret_cast<float4 *>(sm + hsz);             // [SPREAD_CHUNK]
+    float4 *ce = reinterpret_cast<float4 *>(sm + hsz);             // [g.chunk]
     const int e0 = g.row_off[r], e1 = g.row_off[r + 1];
     for (int c = threadIdx.x; c < hsz; c += blockDim.x) sm[c] = make_float2(0.f, 0.f);
     const float2 *Vb = V + (size_t)b * g.w * g.AM;
     const int *roff = g.rec_off + (size_t)r * (2 * g.nch + 1);
-    for (int kc = 0, c0 = e0; c0 < e1; ++kc, c0 += SPREAD_CHUNK) {
-        const int n = (e1 - c0) < SPREAD_CHUNK ? (e1 - c0) : SPREAD_CHUNK;
+    const int chunk = g.chunk;
+    for (int kc = 0, c0 = e0; c0 < e1; ++kc, c0 += chunk) {
+        const int n = (e1 - c0) < chunk ? (e1 - c0) : chunk;
 #pragma unroll 2
         for (int i = threadIdx.x; i < n; i += blockDim.x) {
             const int4 en = g.ent[c0 + i];

@@ -98,11 +98,18 @@ GROUP_GEOMS = [dict(n=256, n_angles=48, n_det=362), dict(n=64, n_angles=33, n_de
 GROUP_COUNTS = [3, 5, 2, 4]
 
 
-def test_plan_group_equals_per_geometry_plans_bitwise(api):
-    """One persistent launch per stage over all geometries: A, A^T, and the
-    MBIR gradient with weights and the 26-neighbour prior (objective terms
-    included) equal those of one plan per geometry bit for bit, eagerly and
-    replayed from a CUDA graph."""
+def _rel(a, b):
+    return float((a.double() - b.double()).norm() / b.double().norm())
+
+
+def test_plan_group_matches_per_geometry_plans(api):
+    """Persistent launches over the group's work lists (one per stage and
+    geometry class): A, A^T, and the MBIR gradient with weights and the
+    26-neighbour prior (objective terms included) agree with one plan per
+    geometry to FP32 rounding (the grouped kernels are compiled apart from
+    the per-plan ones, so a multiply-add may be fused differently; 1e-6
+    relative per geometry, objective 1e-9), and a CUDA-graph replay of the
+    group equals its eager run bit for bit."""
     dev = torch.device("cuda:0")
     rng = np.random.default_rng(9)
     with api.PlanGroup(GROUP_GEOMS, GROUP_COUNTS, device=dev) as grp:
@@ -127,10 +134,12 @@ def test_plan_group_equals_per_geometry_plans_bitwise(api):
                 ref_g.append(g1.flatten())
                 ref_o.append(o1)
                 torch.cuda.synchronize()
-        assert torch.equal(yg, torch.cat(ref_y))
-        assert torch.equal(xg, torch.cat(ref_x))
-        assert torch.equal(gg, torch.cat(ref_g))
-        assert torch.equal(og, torch.stack(ref_o))
+        for got, ref, split in ((yg, ref_y, grp.split_sinos), (xg, ref_x, grp.split_images),
+                                (gg, ref_g, grp.split_images)):
+            for part_got, part_ref in zip(split(got), ref):
+                assert _rel(part_got.flatten(), part_ref) <= 1e-6
+        ref_o = torch.stack(ref_o)
+        assert float(((og - ref_o).abs() / ref_o.abs()).max()) <= 1e-9
         # the same work captured once and replayed
         yo, xo, go = torch.empty_like(yg), torch.empty_like(xg), torch.empty_like(gg)
         oo = torch.zeros_like(og)
@@ -155,3 +164,26 @@ def test_plan_group_rejects_bad_arguments(api):
     with api.PlanGroup([(64, 10, 92)], [2]) as grp:
         with pytest.raises(ValueError):
             api.radon_fwd_group(grp, torch.zeros(grp.image_numel + 1, device="cuda:0"))
+
+
+def test_spread_chunk_is_a_plan_choice_and_autotuned(api):
+    """The spreading chunk (entries staged per pass over a grid row) changes
+    only the grouping of each cell's FP32 sum: A^T stays within 1e-6 of the
+    default and of the oracle-checked operator, each chunk size is
+    bit-reproducible, and the autotuner keeps one of the sizes."""
+    dev = torch.device("cuda:0")
+    n, a, d, b = 256, 64, 362, 4
+    rng = np.random.default_rng(6)
+    y = torch.tensor(rng.standard_normal((b, a, d)), dtype=torch.float32, device=dev)
+    with api.Plan(n, a, d, max_batch=b) as p:
+        assert p.spread_chunk == 1024
+        ref = api.radon_adj(p, y).clone()
+        for ch in (256, 512, 1024):
+            p.spread_chunk = ch
+            x1 = api.radon_adj(p, y).clone()
+            assert torch.equal(api.radon_adj(p, y), x1)
+            assert float((x1 - ref).norm() / ref.norm()) <= 1e-6
+        with pytest.raises(api.TcError):
+            p.spread_chunk = 300
+        best = p.autotune_spread(reps=1)
+        assert best in (256, 512, 1024) and p.spread_chunk == best
