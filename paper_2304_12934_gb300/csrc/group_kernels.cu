@@ -1,16 +1,21 @@
 // Batches of slices with uneven geometry (image side, angle count, detector
-// width) in persistent launches over work lists.
+// width): one launch per pipeline stage and geometry class over a work list.
 //
 // A plan group holds one plan per geometry, sized for all of that geometry's
-// slices.  Per pipeline stage, the geometries fall into classes that share a
-// launch shape: the image side for the column and row passes, the detector
-// transform (Bluestein length, or mixed radix) for the detector passes.  Each
-// (stage, class) runs as one persistent launch of as many CTAs as fit on the
-// GPU; every CTA takes the next (geometry, slice, tile) item of the class's
-// work list from an atomic ticket -- a column strip, a grid row or an angle
-// pair -- runs the same pass body as the per-plan kernels (radon_passes.cuh)
-// with that item's geometry, and takes another until the list is empty.
-// Items are listed largest geometry first, so the small ones fill the tail.
+// slices.  Per stage, the geometries fall into classes that share a launch
+// shape: the image side for the column and row passes, the detector transform
+// (Bluestein length, or mixed radix) for the detector passes.  Each class
+// (up to GK_MAXG geometries) runs as one launch whose work list is every
+// (geometry, slice, tile) item of the class -- column strips, grid rows or
+// angle pairs -- largest geometry first; CTA i runs item i, and the GPU's
+// block scheduler hands the items out in list order as SMs free up, so the
+// small geometries fill the tail of the large ones.  The geometries travel in
+// the launch's parameter block and a switch picks the item's one, so every
+// pass body reads its geometry from the constant bank at a fixed offset, as
+// the per-plan kernels do.  (A software work queue -- CTAs looping over
+// tickets -- made the compiler keep each body's geometry-derived values live
+// across items: 600 to 2,500 bytes of register spills per thread at the
+// per-plan kernels' occupancy, where one item per CTA needs 44 registers.)
 // Stage boundaries are kernel boundaries: no CTA ever waits for another.
 // The arithmetic is the per-plan kernels'; results agree with the
 // per-geometry plans to FP32 rounding (separately compiled kernels may fuse a
@@ -44,51 +49,53 @@ struct GroupGeom {
     int tiles[GS_COUNT];      // items per slice of each stage
 };
 
-// The persistent loop over the items [first, end) of one class: take tickets
-// until the list is exhausted; f runs item (geometry G, tile t, slice b) with
-// the whole block.  starts[pos] is the first item of the pos-th geometry of the
-// stage's list (geo[pos] its index in gg); the class's geometries begin at
-// position pos0.
+// One class launch: its geometries and the first item of each.
+constexpr int GK_MAXG = 4;
+struct ClassParams {
+    int ng;                    // geometries of this launch (1..GK_MAXG)
+    int starts[GK_MAXG + 1];   // first item of each geometry; starts[ng] = items of the launch
+    GroupGeom geo[GK_MAXG];
+};
+
+// Item blockIdx.x of the launch: f(G, tile, slice) with G the item's
+// geometry, chosen by a switch so each branch reads its geometry at a fixed
+// parameter offset.
 template <class F>
-__device__ __forceinline__ void run_items(const GroupGeom *__restrict__ gg, const int *__restrict__ starts,
-                                          const int *__restrict__ geo, int pos0, int stage, int first, int end,
-                                          int *__restrict__ ticket, F &&f) {
-    __shared__ int item_s;
-    for (;;) {
-        __syncthreads();  // the previous item is done with shared memory and item_s
-        if (threadIdx.x == 0) item_s = first + atomicAdd(ticket, 1);
-        __syncthreads();
-        const int item = item_s;
-        if (item >= end) return;
-        int pos = pos0;
-        while (item >= starts[pos + 1]) ++pos;
-        const GroupGeom &G = gg[geo[pos]];
-        const int local = item - starts[pos], nt = G.tiles[stage];
-        f(G, local % nt, local / nt);
+__device__ __forceinline__ void run_item(const ClassParams &cp, int stage, F &&f) {
+    const int item = blockIdx.x;
+    int pos = 0;
+    while (pos + 1 < cp.ng && item >= cp.starts[pos + 1]) ++pos;
+    const int local = item - cp.starts[pos];
+    auto go = [&](const GroupGeom &G) { f(G, local % G.tiles[stage], local / G.tiles[stage]); };
+    switch (pos) {
+        case 0: go(cp.geo[0]); break;
+        case 1: go(cp.geo[1]); break;
+        case 2: go(cp.geo[2]); break;
+        default: go(cp.geo[3]); break;
     }
 }
+static_assert(GK_MAXG == 4, "run_item's switch covers GK_MAXG geometries");
 
-#define GK_ARGS const GroupGeom *__restrict__ gg, const int *__restrict__ starts, const int *__restrict__ geo, \
-                int pos0, int first, int end, int *__restrict__ ticket
-
+// launch bounds as the per-plan kernels of the same passes
 template <int LOGN>
-__global__ void __launch_bounds__(512) gk_fwd_col(GK_ARGS, const float *__restrict__ x) {
-    run_items(gg, starts, geo, pos0, GS_FWD_COL, first, end, ticket, [&](const GroupGeom &G, int t, int b) {
+__global__ void __launch_bounds__(512) gk_fwd_col(const __grid_constant__ ClassParams cp, const float *__restrict__ x) {
+    run_item(cp, GS_FWD_COL, [&](const GroupGeom &G, int t, int b) {
         fwd_col_body<LOGN, false>(x + G.xoff, G.tu, G.k, G.cp, nullptr, nullptr, t, b);
     });
 }
 
 template <int LOGN>
-__global__ void __launch_bounds__(LOGN == 11 ? 256 : 512, LOGN == 11 ? 5 : 1) gk_fwd_row(GK_ARGS) {
-    run_items(gg, starts, geo, pos0, GS_FWD_ROW, first, end, ticket,
-              [&](const GroupGeom &G, int t, int b) { fwd_row_body<LOGN>(G.tu, G.pv, G.k, t, b); });
+__global__ void __launch_bounds__(LOGN == 11 ? 256 : 512, LOGN == 11 ? 5 : 1)
+    gk_fwd_row(const __grid_constant__ ClassParams cp) {
+    run_item(cp, GS_FWD_ROW, [&](const GroupGeom &G, int t, int b) { fwd_row_body<LOGN>(G.tu, G.pv, G.k, t, b); });
 }
 
 // y (sinograms out, may be null), bs and ws (may be null): mode as k_fwd_det
 template <bool BLUE, int LOGL>
-__global__ void __launch_bounds__(512) gk_fwd_det(GK_ARGS, float *__restrict__ y, const float *__restrict__ bs,
-                                                  const float *__restrict__ ws, int mode) {
-    run_items(gg, starts, geo, pos0, GS_FWD_DET, first, end, ticket, [&](const GroupGeom &G, int t, int b) {
+__global__ void __launch_bounds__(512, 2) gk_fwd_det(const __grid_constant__ ClassParams cp, float *__restrict__ y,
+                                                  const float *__restrict__ bs, const float *__restrict__ ws,
+                                                  int mode) {
+    run_item(cp, GS_FWD_DET, [&](const GroupGeom &G, int t, int b) {
         fwd_det_body<BLUE, LOGL>(G.pv, y ? y + G.yoff : nullptr, bs ? bs + G.yoff : nullptr,
                                  ws ? ws + G.yoff : nullptr, G.sr, G.part, G.k, mode, t, b, G.tiles[GS_FWD_DET]);
     });
@@ -96,21 +103,20 @@ __global__ void __launch_bounds__(512) gk_fwd_det(GK_ARGS, float *__restrict__ y
 
 // the adjoint's input: y (concatenated sinograms), or each geometry's residual when y is null
 template <bool BLUE, int LOGL>
-__global__ void __launch_bounds__(512) gk_adj_det(GK_ARGS, const float *__restrict__ y) {
-    run_items(gg, starts, geo, pos0, GS_ADJ_DET, first, end, ticket, [&](const GroupGeom &G, int t, int b) {
+__global__ void __launch_bounds__(512, 2) gk_adj_det(const __grid_constant__ ClassParams cp, const float *__restrict__ y) {
+    run_item(cp, GS_ADJ_DET, [&](const GroupGeom &G, int t, int b) {
         adj_det_body<BLUE, LOGL>(y ? y + G.yoff : G.sr, G.pv, G.k, t, b);
     });
 }
 
 template <int LOGN>
-__global__ void __launch_bounds__(512) gk_adj_row(GK_ARGS) {
-    run_items(gg, starts, geo, pos0, GS_ADJ_ROW, first, end, ticket,
-              [&](const GroupGeom &G, int t, int b) { adj_row_body<LOGN>(G.pv, G.tu, G.k, t, b); });
+__global__ void __launch_bounds__(512) gk_adj_row(const __grid_constant__ ClassParams cp) {
+    run_item(cp, GS_ADJ_ROW, [&](const GroupGeom &G, int t, int b) { adj_row_body<LOGN>(G.pv, G.tu, G.k, t, b); });
 }
 
 template <int LOGN>
-__global__ void __launch_bounds__(512) gk_adj_col(GK_ARGS, float *__restrict__ x) {
-    run_items(gg, starts, geo, pos0, GS_ADJ_COL, first, end, ticket, [&](const GroupGeom &G, int t, int b) {
+__global__ void __launch_bounds__(512) gk_adj_col(const __grid_constant__ ClassParams cp, float *__restrict__ x) {
+    run_item(cp, GS_ADJ_COL, [&](const GroupGeom &G, int t, int b) {
         adj_col_body<LOGN, COL_DEAPOD>(G.tu, x + G.xoff, G.k, G.cp, nullptr, nullptr, nullptr, t, b,
                                        G.tiles[GS_ADJ_COL]);
     });
@@ -131,14 +137,14 @@ __global__ void gk_data_finalize(const GroupGeom *__restrict__ gg, double *__res
 
 }  // namespace
 
-// One persistent launch: the items [first, end) of one class of one stage.
+// One persistent launch: up to GK_MAXG geometries of one class of one stage.
 struct ClassLaunch {
     int stage;
     int key;        // log2 N (column / row passes); Bluestein log2 L, 0 run-time L, -1 mixed radix (detector)
-    int pos0;       // first position of the class in the stage's geometry order
-    int first, end; // item range
+    int items;
     int grid, threads;
     size_t smem;
+    ClassParams par;
 };
 
 struct tc_plan_group {
@@ -147,9 +153,6 @@ struct tc_plan_group {
     std::vector<int> counts;
     std::vector<long long> xoff, yoff;
     GroupGeom *dgeoms = nullptr;     // caller's order
-    int *dstarts = nullptr;          // [GS_COUNT][ng + 1] first item of each position of the stage's order
-    int *dgeo = nullptr;             // [GS_COUNT][ng] position -> geometry
-    int *tickets = nullptr;          // one per class launch
     std::vector<ClassLaunch> launches;
     long long bytes = 0;
 };
@@ -159,7 +162,7 @@ namespace {
 void group_free(tc_plan_group *g) {
     if (!g) return;
     for (tc_plan *p : g->plans) tc_plan_free(p);
-    for (void *q : {(void *)g->dgeoms, (void *)g->dstarts, (void *)g->dgeo, (void *)g->tickets})
+    for (void *q : {(void *)g->dgeoms})
         if (q) cudaFree(q);
     delete g;
 }
@@ -202,18 +205,15 @@ int with_class_kernel(int stage, int key, F &&f) {
     return TC_ERR_INVALID_ARG;
 }
 
-// Occupancy-sized grid of one class launch (and its shared-memory opt-in).
-int class_config(ClassLaunch &c, int device) {
+// A class launch's shared-memory opt-in (raise only: the limit is a
+// process-wide attribute of the kernel).
+int class_config(ClassLaunch &c) {
     return with_class_kernel(c.stage, c.key, [&](auto *kern) -> int {
         cudaFuncAttributes at;
         TC_CUDA(cudaFuncGetAttributes(&at, kern));
         if ((size_t)at.maxDynamicSharedSizeBytes < c.smem)
             TC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem));
-        int per_sm = 0, sms = 0;
-        TC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, c.threads, c.smem));
-        TC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
-        if (per_sm < 1) return TC_ERR_UNSUPPORTED;
-        c.grid = std::max(1, std::min(c.end - c.first, per_sm * sms));
+        c.grid = c.items;
         return TC_OK;
     });
 }
@@ -222,14 +222,12 @@ int class_config(ClassLaunch &c, int device) {
 // out; b, w, mode: the forward detector pass's epilogue; xo: images out).
 int launch_stage(tc_plan_group *g, int st, cudaStream_t s, const float *x, float *y, const float *b,
                  const float *w, int mode, float *xo) {
-    const int *starts = g->dstarts + (size_t)st * (g->ng + 1), *geo = g->dgeo + (size_t)st * g->ng;
     for (size_t li = 0; li < g->launches.size(); ++li) {
         const ClassLaunch &c = g->launches[li];
         if (c.stage != st) continue;
-        int *tk = g->tickets + li;
         const dim3 grid(c.grid), blk(c.threads);
         const size_t sm = c.smem;
-#define GK_PASS g->dgeoms, starts, geo, c.pos0, c.first, c.end, tk
+#define GK_PASS c.par
         int rc = TC_OK;
         switch (st) {
             case GS_FWD_COL:
@@ -339,8 +337,8 @@ int tc_plan_group_create(const tc_geom *geoms, const int *counts, int n_geoms, t
         yo += (long long)counts[i] * p->k.A * p->k.D;
         g->bytes += p->bytes;
     }
-    // per stage: geometries ordered by class, then largest first; one launch per class
-    std::vector<int> starts((size_t)GS_COUNT * (n + 1)), geo((size_t)GS_COUNT * n);
+    // per stage: geometries grouped by class, largest first; one launch per
+    // class (per GK_MAXG geometries of a class)
     for (int st = 0; st < GS_COUNT; ++st) {
         const bool det = st == GS_FWD_DET || st == GS_ADJ_DET;
         auto key = [&](int i) { return det ? det_key(g->plans[i]->k) : g->plans[i]->k.log2N; };
@@ -350,25 +348,22 @@ int tc_plan_group_create(const tc_geom *geoms, const int *counts, int n_geoms, t
         std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) {
             return key(a) != key(b) ? key(a) < key(b) : cost(a) > cost(b);
         });
-        long long item = 0;
-        for (int pos = 0; pos < n; ++pos) {
-            geo[(size_t)st * n + pos] = ord[pos];
-            starts[(size_t)st * (n + 1) + pos] = (int)item;
-            item += cost(ord[pos]);
-            if (item >= (1LL << 31)) {
-                group_free(g);
-                return TC_ERR_UNSUPPORTED;
-            }
-        }
-        starts[(size_t)st * (n + 1) + n] = (int)item;
         for (int p0 = 0; p0 < n;) {
-            int p1 = p0;
             ClassLaunch c{};
             c.stage = st;
             c.key = key(ord[p0]);
-            c.pos0 = p0;
-            while (p1 < n && key(ord[p1]) == c.key) {
-                const tc_plan *p = g->plans[ord[p1]];
+            long long item = 0;
+            int p1 = p0;
+            while (p1 < n && key(ord[p1]) == c.key && c.par.ng < GK_MAXG) {
+                const int i = ord[p1];
+                const tc_plan *p = g->plans[i];
+                c.par.starts[c.par.ng] = (int)item;
+                c.par.geo[c.par.ng++] = hg[i];
+                item += cost(i);
+                if (item >= (1LL << 31)) {
+                    group_free(g);
+                    return TC_ERR_UNSUPPORTED;
+                }
                 if (st == GS_FWD_COL || st == GS_ADJ_COL) {
                     c.threads = std::max(c.threads, p->threads_col);
                     c.smem = std::max(c.smem, p->smem_col);
@@ -381,27 +376,22 @@ int tc_plan_group_create(const tc_geom *geoms, const int *counts, int n_geoms, t
                 }
                 ++p1;
             }
-            c.first = starts[(size_t)st * (n + 1) + p0];
-            c.end = starts[(size_t)st * (n + 1) + p1];
-            if (c.end > c.first) g->launches.push_back(c);
+            c.par.starts[c.par.ng] = (int)item;
+            c.items = (int)item;
+            if (c.items > 0) g->launches.push_back(c);
             p0 = p1;
         }
     }
     int rc = TC_OK;
-    if (cudaMalloc(&g->dgeoms, sizeof(GroupGeom) * n) != cudaSuccess ||
-        cudaMalloc(&g->dstarts, sizeof(int) * starts.size()) != cudaSuccess ||
-        cudaMalloc(&g->dgeo, sizeof(int) * geo.size()) != cudaSuccess ||
-        cudaMalloc(&g->tickets, sizeof(int) * std::max<size_t>(1, g->launches.size())) != cudaSuccess) {
+    if (cudaMalloc(&g->dgeoms, sizeof(GroupGeom) * n) != cudaSuccess) {
         cudaGetLastError();
         group_free(g);
         return TC_ERR_OOM;
     }
-    if (cudaMemcpy(g->dgeoms, hg.data(), sizeof(GroupGeom) * n, cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(g->dstarts, starts.data(), sizeof(int) * starts.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(g->dgeo, geo.data(), sizeof(int) * geo.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+    if (cudaMemcpy(g->dgeoms, hg.data(), sizeof(GroupGeom) * n, cudaMemcpyHostToDevice) != cudaSuccess)
         rc = tc_cuda_fail(cudaGetLastError(), "tc_plan_group_create");
     for (ClassLaunch &c : g->launches)
-        if (!rc) rc = class_config(c, g->device);
+        if (!rc) rc = class_config(c);
     if (rc) {
         group_free(g);
         return rc;
@@ -425,7 +415,6 @@ int radon_fwd_group(tc_plan_group *g, const float *x, float *y, void *stream) {
     GroupDevice dg(g->device);
     if (!dg.ok) return TC_ERR_CUDA;
     cudaStream_t s = (cudaStream_t)stream;
-    TC_CUDA(cudaMemsetAsync(g->tickets, 0, sizeof(int) * g->launches.size(), s));
     int rc;
     if ((rc = launch_stage(g, GS_FWD_COL, s, x, nullptr, nullptr, nullptr, 0, nullptr)) ||
         (rc = launch_stage(g, GS_FWD_ROW, s, nullptr, nullptr, nullptr, nullptr, 0, nullptr)) ||
@@ -439,7 +428,6 @@ int radon_adj_group(tc_plan_group *g, const float *y, float *x, void *stream) {
     GroupDevice dg(g->device);
     if (!dg.ok) return TC_ERR_CUDA;
     cudaStream_t s = (cudaStream_t)stream;
-    TC_CUDA(cudaMemsetAsync(g->tickets, 0, sizeof(int) * g->launches.size(), s));
     int rc;
     if ((rc = launch_stage(g, GS_ADJ_DET, s, nullptr, const_cast<float *>(y), nullptr, nullptr, 0, nullptr)) ||
         (rc = launch_stage(g, GS_ADJ_ROW, s, nullptr, nullptr, nullptr, nullptr, 0, nullptr)) ||
@@ -458,7 +446,6 @@ int mbir_grad_group(tc_plan_group *g, const float *x, const float *b, const floa
     GroupDevice dg(g->device);
     if (!dg.ok) return TC_ERR_CUDA;
     cudaStream_t s = (cudaStream_t)stream;
-    TC_CUDA(cudaMemsetAsync(g->tickets, 0, sizeof(int) * g->launches.size(), s));
     if (obj) TC_CUDA(cudaMemsetAsync(obj, 0, sizeof(double) * 2 * g->ng, s));
     const int mode = DET_RESID | (obj ? DET_OBJ : 0);
     int rc;

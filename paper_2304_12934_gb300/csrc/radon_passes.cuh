@@ -322,6 +322,16 @@ __device__ __forceinline__ float2 spread_record(const float4 *__restrict__ ce, i
 // The per-plan spreading kernel runs slices fastest in its grid (blockIdx.x =
 // slice, blockIdx.y = grid row): the CTAs in flight share one row's entry and
 // record tables, read once from DRAM per launch instead of once per slice.
+// iterations of the spreading pass's entry staging, and of the inverse column
+// pass's grid-row loads, unrolled so that their global loads are in flight together
+#ifndef TC_ADJ_ROW_STAGE_UNROLL
+#define TC_ADJ_ROW_STAGE_UNROLL 2
+#endif
+#ifndef TC_ADJ_COL_LOAD_UNROLL
+#define TC_ADJ_COL_LOAD_UNROLL 4
+#endif
+constexpr int kAdjRowStageUnroll = TC_ADJ_ROW_STAGE_UNROLL;
+constexpr int kAdjColLoadUnroll = TC_ADJ_COL_LOAD_UNROLL;
 #ifndef TC_ADJ_ROW_SLICES_FASTEST
 #define TC_ADJ_ROW_SLICES_FASTEST 1
 #endif
@@ -340,7 +350,7 @@ __device__ __forceinline__ void adj_row_body(const float2 *__restrict__ V, float
     const int chunk = g.chunk;
     for (int kc = 0, c0 = e0; c0 < e1; ++kc, c0 += chunk) {
         const int n = (e1 - c0) < chunk ? (e1 - c0) : chunk;
-#pragma unroll 2
+#pragma unroll kAdjRowStageUnroll
         for (int i = threadIdx.x; i < n; i += blockDim.x) {
             const int4 en = g.ent[c0 + i];
             const float2 u = cscale(Vb[entry_p(en)], entry_wy(en));
@@ -410,7 +420,7 @@ __device__ __forceinline__ void adj_col_body(const float2 *__restrict__ U, float
     // cells jy and G - jy (jy = 0..N) come from the same two grid rows: one
     // pair of loads gives both (the second cell's Hermitian parts are the
     // conjugates of the first's)
-#pragma unroll 4
+#pragma unroll kAdjColLoadUnroll
     for (int idx = threadIdx.x; idx < (N + 1) * CP; idx += blockDim.x) {
         const int pp = idx % CP, jy = idx / CP;
         const int xc = x0base + 2 * pp;

