@@ -113,10 +113,13 @@ __device__ __forceinline__ void dft_reg(float2 *v) {
 }
 
 // Transform stride (in padded elements) for cnt transforms of length n kept
-// back to back: the padded length rounded up to 8 (mod 16), so element i of
-// consecutive transforms falls in different bank halves.
+// back to back: the padded length rounded up to 4 (mod 16).  Element i of
+// transforms 0..3 then falls 32 bytes apart in the bank space, so a
+// half-warp that touches the same index of the even/odd pair of two column
+// pairs (the column passes' staging and output loops) hits four disjoint
+// bank groups; the FFT stages themselves never mix transforms in a warp.
 __host__ __device__ constexpr int fft_tstride(int n) {
-    return spad_size(n) + ((24 - (spad_size(n) & 15)) & 15);
+    return spad_size(n) + ((20 - (spad_size(n) & 15)) & 15);
 }
 
 // Per-stage twiddle tables of a length-n FFT (n = 2^log2n), concatenated for
