@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--profile-steps", type=int, default=3,
                     help="iterations of the separate per-kernel event pass")
+    ap.add_argument("--step", type=float, default=None,
+                    help="use this step instead of deriving it (profiling runs skip the power iteration)")
     ap.add_argument("--power-iter", type=int, default=30,
                     help="power iterations of the library-derived step (first, untimed call)")
     ap.add_argument("--uneven-slices", type=int, default=512,
@@ -188,18 +190,25 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
+def kernel_sources_sha256(files):
+    """sha256 over the concatenated source files that define a kernel."""
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, "paper_2304_12934_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
 def traffic_for(name, units):
     """DRAM bytes of one launch of `name` over `units` slices, from the committed
-    ncu counters (bytes per slice), or None when the kernel's source changed
-    since those counters were taken."""
+    ncu counters (bytes per slice), or None when one of the kernel's source
+    files changed since those counters were taken."""
     path = os.path.join(ROOT, "profiles", "dram_traffic.json")
     try:
         with open(path) as fh:
             ent = json.load(fh)["kernels"][name]
-        src = os.path.join(ROOT, "paper_2304_12934_gb300", "csrc", ent["source_file"])
-        with open(src, "rb") as fh:
-            if hashlib.sha256(fh.read()).hexdigest() != ent["source_sha256"]:
-                return None
+        if kernel_sources_sha256(ent["source_files"]) != ent["source_sha256"]:
+            return None
         return int(ent["bytes_per_slice"] * units)
     except Exception:
         return None
@@ -456,10 +465,13 @@ def run_ours(args):
     # ---- warm-up; the first call derives the step inside the library (power
     # iteration over the whole volume plus the prior's curvature bound)
     t_step = time.perf_counter()
-    api.mbir_solve(plan, b, wgt, x, 0, None, prior, state=st, power_iter=args.power_iter)
-    torch.cuda.synchronize()
+    if args.step is None:
+        api.mbir_solve(plan, b, wgt, x, 0, None, prior, state=st, power_iter=args.power_iter)
+        torch.cuda.synchronize()
+        step = st.step
+    else:
+        step = args.step
     t_step = time.perf_counter() - t_step
-    step = st.step
     api.mbir_solve(plan, b, wgt, x, args.warmup, step, prior, state=st)
     torch.cuda.synchronize()
 
