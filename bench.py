@@ -62,6 +62,11 @@ def parse():
                     help="slices of the uneven-size batching measurement (0 skips it)")
     ap.add_argument("--cpu-angles", type=int, default=16,
                     help="angles of one slice timed by the oracle for the CPU baseline")
+    ap.add_argument("--oracle-configs", action="store_true",
+                    help="instead of the headline: time the FP64 oracle's MBIR solve on the host cores and "
+                         "the library on the GPU for the single-slice 128^2 and the noisy 16 x 512^2 configurations")
+    ap.add_argument("--oracle-iters2", type=int, default=3,
+                    help="--oracle-configs: oracle iterations timed on one noisy 512^2 slice (of the 50)")
     ap.add_argument("--workload", default=None,
                     choices=["volume_2048x1024", "tb25_shape", "tb86_shape"],
                     help="set n, angles, det and slices from a named synthetic workload")
@@ -268,6 +273,100 @@ def run_reference(args):
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------- oracle against library timings ---
+def oracle_configs(args):
+    """FP64 oracle MBIR on the host cores next to the library on the GPU.
+
+    Single slice: 128^2 random-ellipse phantom, 90 angles, 184 bins, noise-free
+    b = A x_true with W = I, 8-neighbour prior, 20 iterations; the oracle runs
+    all of them (and its power iteration for the step) and the library runs
+    the same solve with the oracle's step.  Noisy: 16 slices of 512^2, 180
+    angles, 724 bins, Poisson data at I0 = 1e4 with count weights, 50
+    iterations; the library runs all 16 slices, the oracle one slice for
+    --oracle-iters2 iterations (its per-iteration cost is constant), and the
+    library's iterate of that slice after as many iterations is compared."""
+    import numpy as np
+    import torch
+    import oracle
+    from paper_2304_12934_gb300 import api, synth
+    oracle.build()
+    api.load()
+    dev = torch.device("cuda:0")
+    lam = 1e-2
+    out = {"mode": "oracle_configs", "cores": os.cpu_count()}
+
+    def gpu_solve(plan, b, w, iters, step, prior, reps=3):
+        ts = []
+        for _ in range(reps):
+            x = torch.zeros((b.shape[0], plan.n, plan.n), device=dev)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st = api.mbir_solve(plan, b, w, x, iters, step, prior)
+            torch.cuda.synchronize()
+            ts.append(time.perf_counter() - t0)
+        return x, st, min(ts)
+
+    # ---- single slice, noise-free, 20 iterations
+    N, A, D, it1 = 128, 90, 184, 20
+    ells = synth.random_ellipses(N, synth.BASE_SEED, scale=1.0 / N)
+    f = synth.rasterize(N, ells)[None]
+    t0 = time.perf_counter()
+    b = oracle.radon_fwd(f[0], A, D)[None]
+    w = np.ones_like(b)
+    lam_max = oracle.power_norm(N, A, D, None, synth.random_start((1, N, N), synth.BASE_SEED + 1), 30)
+    step = 1.0 / (1.05 * lam_max + lam * oracle.prior_lipschitz(**oracle.PAPER_PRIOR))
+    t1 = time.perf_counter()
+    xo = oracle.mbir_solve(b, w, N, it1, step, lam=lam, prior=oracle.PAPER_PRIOR, dims=2)
+    t2 = time.perf_counter()
+    prior = api.Prior(lam=lam, dims=2)
+    with api.Plan(N, A, D, max_batch=1, device=dev) as plan:
+        bt = torch.tensor(b, dtype=torch.float32, device=dev)
+        wt = torch.tensor(w, dtype=torch.float32, device=dev)
+        xg, st, tg = gpu_solve(plan, bt, wt, it1, step, prior)
+    err = float(np.linalg.norm(xg.cpu().double().numpy() - xo) / np.linalg.norm(xo))
+    out["single_128"] = {"workload": f"1 slice {N}^2, {A} angles, {D} bins, noise-free, W = I, 8-nbr prior, "
+                                     f"{it1} iterations", "oracle_data_and_step_s": round(t1 - t0, 3),
+                         "oracle_solve_s": round(t2 - t1, 3), "gpu_solve_s": round(tg, 5),
+                         "speedup": round((t2 - t1) / tg, 1), "rel_l2_gpu_vs_oracle": err}
+    print(json.dumps(out), flush=True)
+
+    # ---- noisy, 16 slices of 512^2, 50 iterations
+    N, A, D, B, it2 = 512, 180, 724, 16, 50
+    th = oracle.default_angles(A)
+    _, ells = synth.phantom_slices(N, B, scale=1.0 / N, seed0=synth.BASE_SEED + 512)
+    p = np.stack([synth.ellipse_line_integrals(e, th, D) for e in ells])
+    b, w = synth.poisson_measurement(p, 1e4, synth.BASE_SEED + 513)
+    prior = api.Prior(lam=lam, dims=2)
+    with api.Plan(N, A, D, max_batch=B, device=dev) as plan:
+        bt = torch.tensor(b, dtype=torch.float32, device=dev)
+        wt = torch.tensor(w, dtype=torch.float32, device=dev)
+        x = torch.zeros((B, N, N), device=dev)
+        st = api.mbir_solve(plan, bt, wt, x, 0, None, prior)   # the library derives the step
+        torch.cuda.synchronize()
+        step = st.step
+        _, st, tg = gpu_solve(plan, bt, wt, it2, step, prior)
+    k = max(1, args.oracle_iters2)
+    b0, w0 = b[:1].astype(np.float32).astype(np.float64), w[:1].astype(np.float32).astype(np.float64)
+    t0 = time.perf_counter()
+    xo = oracle.mbir_solve(b0, w0, N, k, step, lam=lam, prior=oracle.PAPER_PRIOR, dims=2)
+    to = time.perf_counter() - t0
+    with api.Plan(N, A, D, max_batch=1, device=dev) as plan:
+        xk, _, _ = gpu_solve(plan, torch.tensor(b0, dtype=torch.float32, device=dev),
+                             torch.tensor(w0, dtype=torch.float32, device=dev), k, step, prior, reps=1)
+    err = float(np.linalg.norm(xk.cpu().double().numpy() - xo) / np.linalg.norm(xo))
+    per_it = to / k
+    out["noisy_512x16"] = {"workload": f"{B} slices {N}^2, {A} angles, {D} bins, Poisson I0=1e4, count weights, "
+                                       f"8-nbr prior, {it2} iterations",
+                           "gpu_solve_s": round(tg, 4), "gpu_slice_iter_s": round(B * it2 / tg, 1),
+                           "oracle_sample": f"1 slice, {k} of {it2} iterations, step from the library",
+                           "oracle_s": round(to, 2), "oracle_s_per_slice_iter": round(per_it, 3),
+                           "oracle_slice_iter_s": round(1.0 / per_it, 5),
+                           "oracle_full_run_s_projected": round(per_it * B * it2, 1),
+                           "speedup": round(per_it * B * it2 / tg, 1),
+                           "rel_l2_gpu_vs_oracle_slice0": err}
+    print(json.dumps(out), flush=True)
 
 
 # ------------------------------------------------- uneven-size batching ---
@@ -619,7 +718,9 @@ def run_ours(args):
 
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.oracle_configs:
+        oracle_configs(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)
