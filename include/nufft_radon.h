@@ -413,8 +413,8 @@ int tc_selftest_wait_timeout(void *stream);
  * doubles (512 KiB) declared at file scope in the library's device code; every
  * GPU that loads the library holds it until the process exits.  The first call
  * on a device looks up that array's device address (cudaGetSymbolAddress, with
- * the device current), caches it and sets the prior kernel's shared-memory
- * attribute, so make the first call on each device before any stream capture.  All calls share the array and each call
+ * the device current) and caches it, so make the first call on each device
+ * before any stream capture.  All calls share the array and each call
  * overwrites the part it uses (nothing has to start at zero), so calls that
  * overlap on the GPU (concurrent streams) race and must be serialised.
  * Asynchronous on `stream`; calls no cudaMalloc, cudaFree or allocating

@@ -13,8 +13,10 @@
 #include "common.cuh"
 #include "profile.cuh"
 
-// Maximum number of per-block partials: one per 32 x 12 voxel column of the
-// prior kernel, enough for N = 4096 (128 x 342 = 43776 blocks).
+// Maximum number of per-block partials: one per CTA of the prior kernel (60
+// columns x 16 rows of voxel columns, times its z chunks), enough for one z
+// chunk at N = 4096 (69 x 256 = 17664 blocks); the launch cuts the z chunks
+// to what fits.
 #define TC_NOALLOC_PARTIALS 65536
 
 static __device__ __align__(256) double g_noalloc_partials[TC_NOALLOC_PARTIALS];
@@ -40,7 +42,7 @@ int noalloc_scratch(double **out) {
     if (!g_addr[dev]) {
         void *ptr = nullptr;
         TC_CUDA(cudaGetSymbolAddress(&ptr, g_noalloc_partials));
-        const int rc = prior_configure_kernels();
+        const int rc = prior_configure_kernels();   // nothing to opt into today; kept for future kernels
         if (rc) return rc;
         g_addr[dev] = static_cast<double *>(ptr);
     }

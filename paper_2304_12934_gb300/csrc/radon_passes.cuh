@@ -180,11 +180,25 @@ __device__ __forceinline__ void fwd_det_body(const float2 *__restrict__ P, float
     }
     const float2 *Pb = P + (size_t)b * g.w * g.AM;
     for (int m = threadIdx.x; m < Mh; m += blockDim.x) {
+        // the w <= 8 tap-row partials, all loads in flight before the sums
+        // (taps summed in order s = 0 .. w-1)
+        float2 v0[8], v1[8];
+#pragma unroll
+        for (int s = 0; s < 8; ++s) {
+            v0[s] = v1[s] = make_float2(0.f, 0.f);
+            if (s < g.w) {
+                const float2 *pl = Pb + (size_t)s * g.AM;
+                v0[s] = pl[(size_t)a0 * Mh + m];
+                if (has1) v1[s] = pl[(size_t)(a0 + 1) * Mh + m];
+            }
+        }
         float2 c0 = make_float2(0.f, 0.f), c1 = make_float2(0.f, 0.f);
-        for (int s = 0; s < g.w; ++s) {
-            const float2 *pl = Pb + (size_t)s * g.AM;
-            c0 = cadd(c0, pl[(size_t)a0 * Mh + m]);
-            if (has1) c1 = cadd(c1, pl[(size_t)(a0 + 1) * Mh + m]);
+#pragma unroll
+        for (int s = 0; s < 8; ++s) {
+            if (s < g.w) {
+                c0 = cadd(c0, v0[s]);
+                c1 = cadd(c1, v1[s]);
+            }
         }
         if (g.angle_flip[a0]) c0 = cconj(c0);
         if (has1 && g.angle_flip[a0 + 1]) c1 = cconj(c1);
@@ -254,6 +268,7 @@ __device__ __forceinline__ void adj_det_body(const float *__restrict__ ysino, fl
         for (int k = threadIdx.x; k < R0; k += blockDim.x) root0[k] = g.twD[k * per0];
     }
     const float *y0 = ysino + ((size_t)b * A + a0) * D;
+#pragma unroll 4
     for (int i = threadIdx.x; i < D; i += blockDim.x)
         bufA[didx<BLUE>(i)] = make_float2(y0[i], has1 ? y0[D + i] : 0.f);
     __syncthreads();
