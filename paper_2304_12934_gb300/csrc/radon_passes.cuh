@@ -40,6 +40,21 @@ __host__ __device__ constexpr int cell_slot(int t0, int ts, int c) {
     return (t0 + (c & 1)) * ts + spad(c >> 1);
 }
 
+#ifndef TC_ADJ_ROW_REC_UNROLL
+#define TC_ADJ_ROW_REC_UNROLL 1
+#endif
+#ifndef TC_ADJ_ROW_REC_PREFETCH
+#define TC_ADJ_ROW_REC_PREFETCH 2
+#endif
+#ifndef TC_FWD_ROW_INTERP_UNROLL
+#define TC_FWD_ROW_INTERP_UNROLL 4
+#endif
+// loop iterations unrolled so that their table loads are in flight together:
+// the spreading pass's records, the interpolation's entries
+constexpr int kAdjRowRecUnroll = TC_ADJ_ROW_REC_UNROLL;
+constexpr int kRecAhead = TC_ADJ_ROW_REC_PREFETCH > 0 ? TC_ADJ_ROW_REC_PREFETCH : 1;   // records read ahead
+constexpr int kFwdRowInterpUnroll = TC_FWD_ROW_INTERP_UNROLL;
+
 // ------------------------------------------------------------ forward ------
 // The pass kernels take the image side as a template parameter (N = 2^LOGN),
 // so their FFTs and shared-memory layouts are fixed at compile time.
@@ -130,6 +145,7 @@ __device__ __forceinline__ void fwd_row_body(const float2 *__restrict__ T, float
     float2 *Pb = P + (size_t)b * g.w * g.AM;
     const int e1 = g.row_off[r + 1];
     constexpr int Gm = 2 * N - 1;
+#pragma unroll kFwdRowInterpUnroll
     for (int e = g.row_off[r] + threadIdx.x; e < e1; e += blockDim.x) {
         const int4 en = g.ent[e];
         const int key = entry_key(en);
@@ -371,8 +387,29 @@ __device__ __forceinline__ void adj_row_body(const float2 *__restrict__ V, float
             const float2 u = cscale(Vb[entry_p(en)], entry_wy(en));
             ce[i] = make_float4(u.x, u.y, (float)entry_key(en), -entry_ex(en) * g.inv_h);
         }
-        __syncthreads();
         const int rb = roff[2 * kc], rs = roff[2 * kc + 1], re = roff[2 * kc + 2];
+#if TC_ADJ_ROW_REC_PREFETCH
+        // each thread's next kRecAhead records are read ahead (the first ones
+        // before the staging barrier), so a record's table load is not waited for
+        const int bd = blockDim.x;
+        int q = rb + threadIdx.x;
+        int2 rn[kRecAhead];
+#pragma unroll
+        for (int k = 0; k < kRecAhead; ++k) rn[k] = q + k * bd < rs ? g.rec[q + k * bd] : make_int2(0, 0);
+        __syncthreads();
+        for (; q < rs; q += bd) {
+            const int2 rc = rn[0];
+#pragma unroll
+            for (int k = 0; k + 1 < kRecAhead; ++k) rn[k] = rn[k + 1];
+            if (q + kRecAhead * bd < rs) rn[kRecAhead - 1] = g.rec[q + kRecAhead * bd];
+            const int cs = (rc.x & 0x7fff) + g.kmin;
+            const float2 acc = spread_record(ce, cs, rc.y & 0xffff, rc.y >> 16, g);
+            float2 &hc = sm[cell_slot(0, ts, cs & (G - 1))];
+            hc = cadd(hc, acc);
+        }
+#else
+        __syncthreads();
+#pragma unroll kAdjRowRecUnroll
         for (int q = rb + threadIdx.x; q < rs; q += blockDim.x) {
             const int2 rc = g.rec[q];
             const int cs = (rc.x & 0x7fff) + g.kmin;
@@ -380,6 +417,7 @@ __device__ __forceinline__ void adj_row_body(const float2 *__restrict__ V, float
             float2 &hc = sm[cell_slot(0, ts, cs & (G - 1))];
             hc = cadd(hc, acc);
         }
+#endif
         __syncthreads();
         if (threadIdx.x == 0) {
             for (int q = rs; q < re; ++q) {  // seam records, in order
