@@ -526,15 +526,26 @@ int check_solve(tc_plan *p, int batch, const tc_prior *prior, const tc_solve_opt
 }
 
 // Stream and events owned by one host-streamed solve.
+#ifndef TC_HOST_OUT_STREAM
+#define TC_HOST_OUT_STREAM 1
+#endif
+// The copy streams of a host-streamed solve: slabs go in on cs and come back
+// on cs_out, so that an outbound slab does not queue behind the inbound ones
+// (the two directions use separate copy engines).
 struct CopyStream {
-    cudaStream_t cs = nullptr;
+    cudaStream_t cs = nullptr, cs_out = nullptr;
     std::vector<cudaEvent_t> ev;      // inbound slabs (+ the start event); fixed during the solve
     std::vector<cudaEvent_t> out_ev;  // outbound slabs, appended while the last iteration runs
+    void sync() {
+        if (cs) cudaStreamSynchronize(cs);
+        if (cs_out && cs_out != cs) cudaStreamSynchronize(cs_out);
+    }
     ~CopyStream() {
         for (cudaEvent_t e : ev)
             if (e) cudaEventDestroy(e);
         for (cudaEvent_t e : out_ev)
             if (e) cudaEventDestroy(e);
+        if (cs_out && cs_out != cs) cudaStreamDestroy(cs_out);
         if (cs) cudaStreamDestroy(cs);
     }
 };
@@ -671,6 +682,8 @@ int mbir_solve_host(tc_plan *p, const float *b_host, const float *w_host, float 
     const int nslab = (batch + p->chunk - 1) / p->chunk;
     CopyStream cp;
     TC_CUDA(cudaStreamCreateWithFlags(&cp.cs, cudaStreamNonBlocking));
+    if (TC_HOST_OUT_STREAM) TC_CUDA(cudaStreamCreateWithFlags(&cp.cs_out, cudaStreamNonBlocking));
+    else cp.cs_out = cp.cs;
     cp.ev.assign(nslab, nullptr);
     // a step still to be derived needs the whole batch resident (and z, g as
     // its work vectors) before the first iteration
@@ -711,7 +724,7 @@ int mbir_solve_host(tc_plan *p, const float *b_host, const float *w_host, float 
         // the last gradient-restart iteration with a prior sends x back slab by
         // slab while it runs; otherwise x goes back after the solve
         const bool stream_out = opts->n_iter > 0 && opts->restart != 2 && prior && prior->lambda != 0.0;
-        const HostOut out{x_host, cp.cs, &cp.out_ev};
+        const HostOut out{x_host, cp.cs_out, &cp.out_ev};
         rc = solve_loop(p, dev_b, w_host ? dev_w : nullptr, dev_x, batch, prior, opts, st, s, derive,
                         overlap ? cp.ev.data() : nullptr, stream_out ? &out : nullptr);
         if (rc) return rc;
@@ -720,13 +733,14 @@ int mbir_solve_host(tc_plan *p, const float *b_host, const float *w_host, float 
             return rc;
         TC_CUDA(cudaStreamSynchronize(s));
         TC_CUDA(cudaStreamSynchronize(cp.cs));
+        if (cp.cs_out != cp.cs) TC_CUDA(cudaStreamSynchronize(cp.cs_out));
         return TC_OK;
     };
     const int rc = body();
     if (rc) {
         // copies already issued still read or write the caller's host buffers:
         // let them finish before the caller regains those buffers
-        cudaStreamSynchronize(cp.cs);
+        cp.sync();
         cudaStreamSynchronize(s);
     }
     return rc;

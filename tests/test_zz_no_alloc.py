@@ -104,3 +104,32 @@ def test_noalloc_at_sides_the_plans_never_use(api, n, batch, dims):
         gd = g.double().cpu().numpy()
         assert float(np.linalg.norm(gd - prior.lam * gh) / np.linalg.norm(prior.lam * gh)) <= TOL
         assert abs(float(h[0]) - prior.lam * Hv) <= TOL * prior.lam * Hv
+
+
+@pytest.mark.parametrize("p", [1.0, 2.0])
+def test_prior_at_the_ends_of_the_exponent_range(api, p):
+    """p = 1 and p = 2 (q = 2 - p = 1 and 0), on a piecewise-constant volume
+    whose neighbour differences are often exactly zero: at q = 0 the kernel's
+    |d|^q must still be 1 there (a zero difference gives a zero pair value,
+    not 0 * inf).  Against the FP64 oracle, 3D and 2D."""
+    import oracle
+    L = api.load()
+    stream = torch.cuda.current_stream()
+    n, batch = 64, 6
+    rng = np.random.default_rng(int(p * 10) + 1)
+    f = (np.round(rng.uniform(0, 1, (batch, n, n)) * 3) / 3).astype(np.float32)
+    for dims in (3, 2):
+        prior = api.Prior(p=p, lam=0.5, dims=dims)
+        x = torch.tensor(f, device="cuda:0")
+        g = torch.zeros_like(x)
+        h = torch.full((1,), -1.0, dtype=torch.float64, device="cuda:0")
+        pc = prior._c()
+        rc = L.tc_prior_grad_noalloc(x.data_ptr(), g.data_ptr(), n, batch, ctypes.byref(pc),
+                                     h.data_ptr(), ctypes.c_void_p(stream.cuda_stream))
+        torch.cuda.synchronize()
+        assert rc == 0
+        Hv, gh = oracle.prior_value_grad(f.astype(np.float64), dims, p=p, sigma=prior.sigma, c=prior.c)
+        gd = g.double().cpu().numpy()
+        assert np.isfinite(gd).all() and np.isfinite(float(h[0]))
+        assert float(np.linalg.norm(gd - prior.lam * gh) / np.linalg.norm(prior.lam * gh)) <= TOL, (p, dims)
+        assert abs(float(h[0]) - prior.lam * Hv) <= TOL * prior.lam * Hv, (p, dims)
