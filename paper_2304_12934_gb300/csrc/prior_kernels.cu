@@ -35,13 +35,18 @@ double prior_value_scale(const tc_prior *pr) { return 2.0 * pr->lambda / (pr->si
 
 dim3 tile_grid(int n) { return dim3((n + TX - 1) / TX, (n + TY - 1) / TY, 1); }
 
-// z chunks for nb slices: about 128 planes each, at most ZCHUNK_MAX and at
-// most what max_blocks partial sums allow
+// z chunks for nb slices: about 128 planes each, or more chunks (down to 32
+// planes) where that is needed for 8 waves of CTAs on 152 SMs (a launch over a
+// 64-slice slab); at most ZCHUNK_MAX and at most what max_blocks partial sums
+// allow
 int z_chunks(int n, int nb, int max_blocks) {
     const dim3 t = tile_grid(n);
+    const long long tiles = (long long)t.x * t.y, waves8 = 8LL * 152 * MIN_BLOCKS;
     int c = nb / 128;
+    const int c_fill = (int)((waves8 + tiles - 1) / tiles), c_cap = nb / 32;
+    if (c < c_fill) c = c_fill < c_cap ? c_fill : c_cap;
     c = c < 1 ? 1 : (c > ZCHUNK_MAX ? ZCHUNK_MAX : c);
-    while (c > 1 && (long long)c * t.x * t.y > max_blocks) --c;
+    while (c > 1 && (long long)c * tiles > max_blocks) --c;
     return c;
 }
 
