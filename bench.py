@@ -406,8 +406,9 @@ def uneven_batch(api, synth, dev, n_slices, reps=3):
                 api.mbir_grad(q["p1"], q["x"][k:k + 1], q["b"][k:k + 1], q["w"][k:k + 1], prior,
                               grad=q["grad"][k:k + 1], obj=q["obj"])
 
-    # the same batch as one plan group: one persistent launch per stage over the
-    # work list of every (geometry, slice, tile), the call captured in a graph
+    # the same batch as one plan group: one launch per stage and geometry class
+    # over the work list of its (geometry, slice, tile) items, one CTA per item,
+    # the call captured in a graph
     grp = api.PlanGroup([(q["n"], q["a"], q["d"]) for q in bufs], [q["cnt"] for q in bufs], device=dev)
     gx = torch.cat([q["x"].flatten() for q in bufs])
     gb = torch.cat([q["b"].flatten() for q in bufs])
@@ -446,7 +447,7 @@ def uneven_batch(api, synth, dev, n_slices, reps=3):
         q["p1"].close()
     grp.close()
     return {"metric": "slice-gradients/s (A, A^T, 8-neighbour prior)", "slices": n_slices,
-            "geometries": len(groups), "persistent_grouped": round(res["grouped"], 1),
+            "geometries": len(groups), "plan_group": round(res["grouped"], 1),
             "graph_batched": round(res["graph"], 1),
             "plain_one_slice_per_launch": round(res["plain"], 1),
             "speedup": round(res["graph"] / res["plain"], 3),

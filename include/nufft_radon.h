@@ -286,10 +286,12 @@ int mbir_solve(tc_plan *plan, const float *b, const float *w, float *x, int batc
  * x_host are HOST pointers (page-locked memory gives asynchronous copies);
  * dev_b, dev_w, dev_x are caller-owned DEVICE buffers of the same sizes that
  * receive the copies.  Inputs are copied host-to-device in slabs of max_batch
- * slices on a second stream (created and destroyed by the call); the first
- * iteration's chunk c starts as soon as slab c is resident, so the copies
- * overlap the first iteration's Radon work.  The result x is copied back to
- * x_host.  Synchronises before returning. */
+ * slices on a copy stream, and the result comes back on another (both
+ * created and destroyed by the call); the first iteration's chunk c starts as
+ * soon as slab c is resident, so the copies overlap the first iteration's
+ * Radon work, and in the last iteration (gradient restart with a prior) each
+ * slab's result leaves as soon as its prior is done.  The result x is copied
+ * back to x_host and is also left in dev_x.  Synchronises before returning. */
 int mbir_solve_host(tc_plan *plan, const float *b_host, const float *w_host,
                     float *x_host, float *dev_b, float *dev_w, float *dev_x,
                     int batch, const tc_prior *prior, const tc_solve_opts *opts,
@@ -301,10 +303,13 @@ int mbir_solve_host(tc_plan *plan, const float *b_host, const float *w_host,
  * geometry at a time).  A group holds one plan per geometry, sized for all of
  * that geometry's slices (counts[i] slices of geoms[i]), and a work list per
  * pipeline stage over every (geometry, slice, tile) item.  Each stage runs as
- * one persistent launch: as many CTAs as fit on the GPU take items from an
- * atomic ticket until the list is empty, largest geometries first.  Stage
- * boundaries are kernel boundaries (no CTA waits for another).  Results are
- * bit for bit those of the per-geometry plans.
+ * one launch per geometry class (the geometries of one image side and, for
+ * the detector passes, one detector-transform kind), one CTA per item, with up
+ * to four geometries in the launch's parameter block and the costliest items
+ * first.  Stage boundaries are kernel boundaries (no CTA waits for another).
+ * Results are those of the per-geometry plans to within 1e-6 relative (the
+ * group kernels are separate compilations of the same pass bodies, so a
+ * multiply-add may be fused differently), and deterministic.
  * Arrays of a group are the geometries' slices concatenated in the order
  * given: images geoms[0] x counts[0] slices of N0 x N0, then geoms[1]'s, ...;
  * sinograms likewise with A_i x D_i.  Calls are asynchronous, capturable into

@@ -137,7 +137,7 @@ __global__ void gk_data_finalize(const GroupGeom *__restrict__ gg, double *__res
 
 }  // namespace
 
-// One persistent launch: up to GK_MAXG geometries of one class of one stage.
+// One launch: up to GK_MAXG geometries of one class of one stage, one CTA per item.
 struct ClassLaunch {
     int stage;
     int key;        // log2 N (column / row passes); Bluestein log2 L, 0 run-time L, -1 mixed radix (detector)
