@@ -169,6 +169,8 @@ def algorithmic_bytes(name, N, A, D, w, B):
         "k_adj_row": 8 * AM + grid_rows,
         "k_adj_col": grid_rows + img,
         "k_prior": 4 * img,  # f, g read + g written, and x_prev for the fused restart dots
+        # the solver's fused form: f, g, x_prev read; x_{k+1} and the momentum point written
+        "k_prior_next": 5 * img,
         "k_dots_gzx_gg": 3 * img,
         "k_update": 3 * img,  # x_k and the next iterate read, z written (x_{k+1} stays where it was made)
         # normal operator A^T A (Toeplitz-plus-Hankel embedding): half-plane rows ky = 0..N
@@ -181,7 +183,7 @@ def algorithmic_bytes(name, N, A, D, w, B):
 
 def launch_units(name, B_total, chunk):
     """Slices processed by one launch of each kernel."""
-    if name in ("k_prior", "k_dots_gzx_gg", "k_update"):
+    if name in ("k_prior", "k_prior_next", "k_dots_gzx_gg", "k_update", "k_restart_fixup"):
         return B_total
     return chunk
 

@@ -250,7 +250,9 @@ typedef struct {
 
 /* Solver state; resuming with the same state continues the iteration exactly.
  *   z, g   caller-owned DEVICE buffers [batch][N][N] (momentum point; g is
- *          scratch: the gradient or the next iterate, depending on the step)
+ *          scratch: the gradient or the next momentum point, depending on the
+ *          step).  A solve with a prior may exchange the two pointers (see
+ *          mbir_solve): z always names the momentum point on return
  *   t      momentum scalar t_k (host copy, updated on return)
  *   k      iterations completed; k == 0 starts fresh (z := x, t := 1)
  *   n_restarts  restarts taken so far (monotone variant: rejected steps)
@@ -277,6 +279,14 @@ typedef struct {
 
 /* Run opts->n_iter iterations on device buffers.
  *   b, w   [batch][A][D] (w may be NULL);  x [batch][N][N] in/out.
+ * With a prior (lambda != 0) and restart 0 or 1, each iteration forms z_{k+1}
+ * inside the prior pass: x_{k+1} is written over x_k and the momentum point
+ * of an iteration without restart over the gradient buffer, so the buffers
+ * behind state->z and state->g exchange roles every iteration (after a
+ * restart a check-and-copy kernel sets z_{k+1} = x_{k+1}).  On return x holds
+ * x_k, and the call may have EXCHANGED the pointers state->z and state->g:
+ * state->z then names the buffer that holds z_k (read the pointers back
+ * after every call; on an error return the state is undefined).
  * Synchronises the stream before returning (to fill the host fields of state). */
 int mbir_solve(tc_plan *plan, const float *b, const float *w, float *x, int batch,
                const tc_prior *prior, const tc_solve_opts *opts,

@@ -313,9 +313,10 @@ def power_norm(n, n_angles, n_det, wt, v0, n_iter, theta=None):
 
 
 def mbir_solve(b, wt, n, n_iter, step, lam=1.0, prior=None, dims=2,
-               theta=None, x0=None, restart=True, return_log=False):
+               theta=None, x0=None, restart=True, return_log=False, z0=None, t0=1.0):
     """Accelerated gradient on Phi = G + lam H (Sec. 3), from x_0 = z_0 = x0
-    (zero by default) with t_0 = 1; all scalars FP64.
+    (zero by default) with t_0 = 1; all scalars FP64.  z0 and t0 continue an
+    iteration from a given state (x_k, z_k, t_k) instead: x_0 = x0, z_0 = z0.
 
     Reading of "monotonic accelerated gradient method with restart":
         v       = z_k - step * grad Phi(z_k)
@@ -332,8 +333,8 @@ def mbir_solve(b, wt, n, n_iter, step, lam=1.0, prior=None, dims=2,
     monotone = restart == "monotone"
     B = b.shape[0]
     x = np.zeros((B, n, n)) if x0 is None else np.asarray(x0, np.float64).copy()
-    z = x.copy()
-    t = 1.0
+    z = x.copy() if z0 is None else np.asarray(z0, np.float64).copy()
+    t = float(t0)
     phi_x = sum(objective_value(x, b, wt, lam, prior, dims, theta)) if monotone else None
     log = []
     for k in range(n_iter):

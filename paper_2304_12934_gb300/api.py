@@ -508,6 +508,11 @@ class SolveState:
         return s
 
     def _load(self, s):
+        # the solve may hand back z and g exchanged: s.z names the buffer of z_k
+        if s.z != self.z.data_ptr():
+            if s.z != self.g.data_ptr():
+                raise RuntimeError("solver state: z points to neither of the state's buffers")
+            self.z, self.g = self.g, self.z
         self.t, self.k, self.n_restarts = s.t, s.k, s.n_restarts
         self.obj = (s.obj[0], s.obj[1])
         self.step = s.step

@@ -78,10 +78,13 @@ int data_grad_chunk(tc_plan *p, const float *x, const float *b, const float *w, 
 // dot_x: with a prior, the prior kernel also forms the restart-test inner
 // products <grad, x - dot_x> and <grad, grad>.
 // atb: A^T b of the whole batch for the normal-operator data term (W = I).
+// next (with dot_x): the prior kernel leaves the next iterate in dot_x and the
+// momentum point of an iteration without restart in grad (launch_prior_grad).
 int grad_impl(tc_plan *p, const float *x, const float *b, const float *w,
               const tc_prior *prior, float *grad, int batch, cudaStream_t s,
               bool want_value = true, const cudaEvent_t *ready = nullptr,
-              const float *dot_x = nullptr, double step = 0.0, const float *atb = nullptr) {
+              float *dot_x = nullptr, double step = 0.0, const float *atb = nullptr,
+              bool next = false) {
     int rc = data_init(p, atb, s);
     if (rc) return rc;
     const size_t ni = img_elems(p), ns = sino_elems(p);
@@ -94,7 +97,7 @@ int grad_impl(tc_plan *p, const float *x, const float *b, const float *w,
     }
     if (prior && prior->lambda != 0.0) {
         rc = launch_prior_grad(p, x, grad, batch, prior, want_value ? p->scal + SC_PRIOR : nullptr, s, dot_x,
-                               0, -1, step);
+                               0, -1, step, next);
         if (rc) return rc;
     }
     return TC_OK;
@@ -364,42 +367,42 @@ struct HostOut {
 // streamed out slab by slab: x_{k+1} = z_k - step g_k needs no global scalar,
 // so a slab's x_{k+1} is final once its data gradient and its prior (which
 // reads a one-slice halo) are done; its copy to the host then overlaps the
-// remaining chunks.  The restart test and z_{k+1} follow at the end.  The
-// result equals the in-place update bit for bit.
-// x holds x_k and gb is the gradient buffer; on return x holds x_{k+1}.
-int last_iteration_streamed(tc_plan *p, const float *b, const float *w, float *x, float *gb, int batch,
-                            const tc_prior *prior, const tc_solve_opts *opts, double step, tc_solve_state *st,
-                            cudaStream_t s, const cudaEvent_t *ready, const HostOut &out,
-                            const float *atb) {
+// remaining chunks.  The prior kernel writes x_{k+1} over x_k and the momentum
+// point of an iteration without restart over the gradient (as every fused
+// iteration does); the restart test, and the copy of x_{k+1} over z_{k+1}
+// after a restart, follow at the end.  Same result as the resident iteration.
+// x holds x_k, z holds z_k and gb is the gradient buffer; on return x holds
+// x_{k+1} and gb holds z_{k+1}.
+int last_iteration_streamed(tc_plan *p, const float *b, const float *w, float *x, const float *z, float *gb,
+                            int batch, const tc_prior *prior, const tc_solve_opts *opts, double step,
+                            cudaStream_t s, const cudaEvent_t *ready, const HostOut &out, const float *atb) {
     int rc0 = data_init(p, atb, s);
     if (rc0) return rc0;
     const size_t ni = img_elems(p), ns = sino_elems(p);
     const int nslab = (batch + p->chunk - 1) / p->chunk;
     auto finish = [&](int j) -> int {
         const int z0 = j * p->chunk, z1 = z0 + p->chunk < batch ? z0 + p->chunk : batch;
-        // the prior kernel leaves x_{k+1} = z - step g of the slab in gb
-        int rc = launch_prior_grad(p, st->z, gb, batch, prior, p->scal + SC_PRIOR, s, x, z0, z1,
-                                   step);
+        int rc = launch_prior_grad(p, z, gb, batch, prior, p->scal + SC_PRIOR, s, x, z0, z1, step, true);
         if (rc) return rc;
         cudaEvent_t e = nullptr;
         TC_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
         out.ev->push_back(e);
         TC_CUDA(cudaEventRecord(e, s));
         TC_CUDA(cudaStreamWaitEvent(out.cs, e, 0));
-        return host_copy_async(out.x_host + z0 * ni, gb + z0 * ni, (size_t)(z1 - z0) * ni * sizeof(float),
+        return host_copy_async(out.x_host + z0 * ni, x + z0 * ni, (size_t)(z1 - z0) * ni * sizeof(float),
                                cudaMemcpyDeviceToHost, out.cs);
     };
     for (int c = 0; c < nslab; ++c) {
         const int c0 = c * p->chunk, nb = batch - c0 < p->chunk ? batch - c0 : p->chunk;
         if (ready) TC_CUDA(cudaStreamWaitEvent(s, ready[c], 0));
-        int rc = data_grad_chunk(p, st->z + c0 * ni, b + c0 * ns, w ? w + c0 * ns : nullptr, gb + c0 * ni, nb,
+        int rc = data_grad_chunk(p, z + c0 * ni, b + c0 * ns, w ? w + c0 * ns : nullptr, gb + c0 * ni, nb,
                                  atb ? atb + c0 * ni : nullptr, true, s);
         if (!rc && c > 0) rc = finish(c - 1);  // slab c holds the upper halo of slab c - 1
         if (rc) return rc;
     }
     int rc = finish(nslab - 1);
     if (!rc) rc = launch_solver_scalar(p, opts->restart, s);
-    if (!rc) rc = launch_update_monotone(p, x, st->z, gb, img_elems(p) * batch, s, 1);
+    if (!rc && opts->restart == 1) rc = launch_restart_fixup(p, gb, x, img_elems(p) * batch, s);
     return rc;
 }
 
@@ -461,39 +464,46 @@ int solve_loop(tc_plan *p, const float *b, const float *w, float *x, int batch,
             if ((rc = launch_update_monotone(p, x, st->z, st->g, n, s))) return rc;
         }
     }
-    // With a prior the iterate alternates between x and the scratch buffer
-    // g: the prior kernel writes x_{k+1} into the buffer not holding x_k, and
-    // the update then only writes z.  It returns to x at the end of the call.
-    float *xa = x, *xb = st->g;  // xa: x_k; xb: gradient / next iterate
-    for (int it = 0; it < (opts->restart == 2 ? 0 : opts->n_iter); ++it) {
-        // the prior's value H is only reported for the last gradient point
-        const bool fused = prior && prior->lambda != 0.0;  // dots inside the prior kernel
-        if (out && fused && it == opts->n_iter - 1) {
-            if ((rc = last_iteration_streamed(p, b, w, xa, xb, batch, prior, opts, step, st, s,
-                                              it == 0 ? ready : nullptr, *out, atb)))
-                return rc;
-            continue;
+    if (prior && prior->lambda != 0.0 && opts->restart != 2) {
+        // Gradient restart or plain momentum with a prior: the prior kernel
+        // forms the restart dots, writes x_{k+1} = z_k - step g over x_k (x
+        // always holds the iterate) and the momentum point of an iteration
+        // without restart, x_{k+1} + beta (x_{k+1} - x_k), over the gradient.
+        // z_{k+1} is thus made where the gradient was, and the buffer of z_k
+        // takes the next gradient: no update pass.  After a restart (beta = 0)
+        // a check-and-copy kernel sets z_{k+1} = x_{k+1}.
+        float *zc = st->z, *gc = st->g;
+        for (int it = 0; it < opts->n_iter; ++it) {
+            const bool last = it == opts->n_iter - 1;  // the prior's value H is reported for the last point
+            const cudaEvent_t *rd = it == 0 ? ready : nullptr;
+            if (out && last) {
+                rc = last_iteration_streamed(p, b, w, x, zc, gc, batch, prior, opts, step, s, rd, *out, atb);
+            } else {
+                rc = grad_impl(p, zc, b, w, prior, gc, batch, s, last, rd, x, step, atb, true);
+                if (!rc) rc = launch_solver_scalar(p, opts->restart, s);
+                if (!rc && opts->restart == 1) rc = launch_restart_fixup(p, gc, x, n, s);
+            }
+            if (rc) return rc;
+            float *t = zc;
+            zc = gc;
+            gc = t;
         }
-        // fused: the prior kernel also forms the restart dots and leaves
-        // x_{k+1} = z_k - step g in xb; otherwise separate dots and update
-        if ((rc = grad_impl(p, st->z, b, w, prior, xb, batch, s, it == opts->n_iter - 1,
-                            it == 0 ? ready : nullptr, fused ? xa : nullptr, step, atb)))
-            return rc;
-        if (!fused && (rc = launch_dots_gzx_gg(p, xb, st->z, xa, n, s))) return rc;
-        if ((rc = launch_solver_scalar(p, opts->restart, s))) return rc;
-        if (fused && it == opts->n_iter - 1 && xa == x) {
-            // last step with x_k in x: write x_{k+1} there too (cheaper than a copy back)
-            if ((rc = launch_update_monotone(p, xa, st->z, xb, n, s, 1, 0))) return rc;
-        } else if (fused) {
-            if ((rc = launch_update_monotone(p, xa, st->z, xb, n, s, 1, 1))) return rc;  // z only
-            float *t = xa;
-            xa = xb;
-            xb = t;
-        } else if ((rc = launch_update(p, xa, st->z, xb, n, s))) {
-            return rc;
+        // z_k ends in one of the two caller buffers: the state names it
+        if (zc != st->z) {
+            st->g = st->z;
+            st->z = zc;
+        }
+    } else {
+        // no prior: separate restart dots and update
+        for (int it = 0; it < (opts->restart == 2 ? 0 : opts->n_iter); ++it) {
+            if ((rc = grad_impl(p, st->z, b, w, prior, st->g, batch, s, it == opts->n_iter - 1,
+                                it == 0 ? ready : nullptr, nullptr, step, atb)))
+                return rc;
+            if ((rc = launch_dots_gzx_gg(p, st->g, st->z, x, n, s))) return rc;
+            if ((rc = launch_solver_scalar(p, opts->restart, s))) return rc;
+            if ((rc = launch_update(p, x, st->z, st->g, n, s))) return rc;
         }
     }
-    if (xa != x && (rc = launch_copy(x, xa, n, s))) return rc;
     double sc[SC_COUNT];
     TC_CUDA(cudaMemcpyAsync(sc, p->scal, sizeof(sc), cudaMemcpyDeviceToHost, s));
     TC_CUDA(cudaStreamSynchronize(s));

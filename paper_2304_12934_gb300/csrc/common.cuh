@@ -201,7 +201,8 @@ enum {
     SC_PRIOR_X,      // lambda H(x_k)
     SC_ACCEPT,       // 1: this iteration's candidate was accepted
     SC_BB,           // 1/2 ||b||^2 of a normal-operator solve
-    SC_COUNT = 16
+    SC_RESTARTED,    // 1: this iteration's gradient test restarted the momentum
+    SC_COUNT = 17
 };
 
 // Launchers (defined in radon_kernels.cu / mbir_kernels.cu).
@@ -220,12 +221,16 @@ int normal_prepare(tc_plan *p, cudaStream_t s);
 // g += lambda grad H(x); h_acc (or NULL) = lambda H(x); with dot_x, also
 // scal[SC_DOT_GZX] = <g, x - dot_x>, scal[SC_DOT_GG] = <g, g> of the final g,
 // and g then receives x - step g (the solver's next iterate) instead.
+// next (with dot_x): the next iterate x - step g goes to dot_x (over x_k)
+// instead, and g receives the momentum point x_{k+1} + beta (x_{k+1} - x_k)
+// with the beta of an iteration without restart (from scal[SC_T]).
 // x holds nb slices; only slices [z0, z1) (z1 < 0: nb) get their gradient
 // (neighbours outside the range are read) and enter the sums, which a slab
 // with z0 > 0 adds to those already held.
 int launch_prior_grad(tc_plan *p, const float *x, float *g, int nb,
                       const tc_prior *pr, double *h_acc, cudaStream_t s,
-                      const float *dot_x = nullptr, int z0 = 0, int z1 = -1, double step = 0.0);
+                      float *dot_x = nullptr, int z0 = 0, int z1 = -1, double step = 0.0,
+                      bool next = false);
 // Tiles of one prior launch on N x N slices, and the FP64 partial-sum slots
 // its z-chunked grid may use.
 int prior_tile_count(int n);
@@ -247,6 +252,9 @@ int launch_dots_gzx_gg(tc_plan *p, const float *g, const float *z, const float *
 int launch_solver_scalar(tc_plan *p, int restart, cudaStream_t s);
 int launch_update(tc_plan *p, float *x, float *z, const float *g, size_t n,
                   cudaStream_t s);
+// After a prior pass with next = true: z := x where the gradient test has just
+// restarted the momentum (scal[SC_RESTARTED]); otherwise the kernel returns.
+int launch_restart_fixup(tc_plan *p, float *z, const float *x, size_t n, cudaStream_t s);
 int launch_dot(tc_plan *p, const float *a, const float *b, size_t n,
                double *out_acc, cudaStream_t s);
 int launch_scale_by_inv_sqrt(float *v, size_t n, const double *sq, cudaStream_t s);

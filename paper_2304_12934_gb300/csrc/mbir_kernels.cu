@@ -79,10 +79,12 @@ __global__ void k_solver_scalar(double *sc, int restart) {
     // <g, x_{k+1} - x_k> with x_{k+1} = z_k - step g
     const double dot = sc[SC_DOT_GZX] - step * sc[SC_DOT_GG];
     double t = sc[SC_T];
-    if (restart && dot > 0.0) {
+    const bool rs = restart && dot > 0.0;
+    if (rs) {
         t = 1.0;
         sc[SC_RESTARTS] += 1.0;
     }
+    sc[SC_RESTARTED] = rs ? 1.0 : 0.0;
     const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
     sc[SC_BETA] = (t - 1.0) / tn;
     sc[SC_T] = tn;
@@ -109,6 +111,16 @@ __global__ void k_update(float4 *__restrict__ x, float4 *__restrict__ z,
         x[i] = xn;
         z[i] = zn;
     }
+}
+
+// z := x after a restart (beta = 0 gives z_{k+1} = x_{k+1}), when the prior
+// pass has written the momentum point of an iteration without restart.
+__global__ void k_restart_fixup(float4 *__restrict__ z, const float4 *__restrict__ x, size_t n4,
+                                const double *__restrict__ sc) {
+    if (sc[SC_RESTARTED] == 0.0) return;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4;
+         i += (size_t)gridDim.x * blockDim.x)
+        z[i] = x[i];
 }
 
 // Monotone variant (function-value test), all decisions in FP64 on the device.
@@ -289,6 +301,15 @@ int launch_update(tc_plan *p, float *x, float *z, const float *g, size_t n,
         reinterpret_cast<float4 *>(x), reinterpret_cast<float4 *>(z),
         reinterpret_cast<const float4 *>(g), n4, p->scal));
     TC_LAUNCHED("k_update");
+    return TC_OK;
+}
+
+int launch_restart_fixup(tc_plan *p, float *z, const float *x, size_t n, cudaStream_t s) {
+    const size_t n4 = n / 4;
+    TC_PROFILED(TCK_FIXUP, s,
+                k_restart_fixup<<<grid_for(n4), TC_RED_THREADS, 0, s>>>(
+        reinterpret_cast<float4 *>(z), reinterpret_cast<const float4 *>(x), n4, p->scal));
+    TC_LAUNCHED("k_restart_fixup");
     return TC_OK;
 }
 

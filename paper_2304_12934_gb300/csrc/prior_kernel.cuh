@@ -38,6 +38,13 @@
 // The grid's third dimension cuts the z range into chunks (a chunk other than
 // the first starts one plane below, evaluating that plane's z+1 pairs only).
 //
+// In the solver (DOTS) the gradient is not stored: the next iterate
+// x_{k+1} = f - step g is, in place of g (DOTS = 1), or in place of x_prev
+// (DOTS = 2, which also writes the momentum point of an iteration without
+// restart, x_{k+1} + beta (x_{k+1} - x_k), in place of g, so the solver
+// needs no separate update pass).  Both x_prev and g are read only at the
+// warp's own cells, once, before these stores.
+//
 // Sums: H per step in FP32 (one plane's rows of one lane) added into a
 // compensated pair; the restart-test inner products <g, f - x_prev> and
 // <g, g> from error-free differences and products (TwoSum, FMA) into
@@ -90,6 +97,7 @@ struct PriorArgs {
     unsigned long long wh2[3];   // w per weight class (the H terms)
     unsigned long long gscale2;  // 2 lambda / (sigma^2 c)
     unsigned long long nstep2;   // DOTS: minus the solver's step (g receives f - step grad)
+    const double *scal;          // DOTS = 2: the solver's scalars (momentum t_k at SC_T)
 };
 
 __device__ __forceinline__ float lg2a(float x) {
@@ -213,20 +221,21 @@ __device__ __forceinline__ void load_inputs(const float *g, const float *xprev, 
 struct MarchCtx {
     const float *f;
     float *g;
-    const float *xprev;
+    float *xprev;
     long long NN, off0;   // plane size; offset of register row 0, cell 0
     int N, B, za, zb, zl;
     bool ilane, in0, in1;
     bool go;                 // true (a runtime value: the blocks of pairs stay separate)
     unsigned xm0, xm1, rm;   // border strips: (cell, neighbour at dx) inside, bit dx + 1; rows inside, bit i
     unsigned long long ql2, lk2, one2, wq[3], wp[3], wh[3], gscale2, nstep2;
+    unsigned long long beta2;   // DOTS = 2: the momentum coefficient without restart
 };
 
 // One step of the march: plane z in Pc, plane z + 1 in Pn (3D), their
 // gradient sums in Ac / An (Ac already holding the z+1 closings from plane
 // z - 1).  FAST: plane z is produced by this chunk and (3D) has a plane above,
 // so no pair needs a branch.  On return Pc, Pn, Ac hold the next step's.
-template <bool WANT_H, bool DOTS, bool GRAD, int DIMS, bool EVEN, bool MK, bool FAST>
+template <bool WANT_H, int DOTS, bool GRAD, int DIMS, bool EVEN, bool MK, bool FAST>
 __device__ __forceinline__ void prior_step(const MarchCtx &c, int z, float2 (&Pc)[RR], float2 (&Pn)[RR],
                                            float2 (&Ac)[RR], float2 (&An)[RR], float2 (&Gi)[RR],
                                            float2 (&Xi)[RR], Acc2 &ah, Acc2 &ad1, Acc2 &ad2) {
@@ -246,9 +255,9 @@ __device__ __forceinline__ void prior_step(const MarchCtx &c, int z, float2 (&Pc
         if (GRAD) An[i] = make_float2(0.f, 0.f);
     }
     if (GRAD && own) {
-        load_inputs<EVEN, DOTS>(c.g, c.xprev, zo + N, c.ilane && ROW_IN(1), c.in0, c.in1, NN, z + 2 < c.zb, Gi[1], Xi[1]);
+        load_inputs<EVEN, DOTS != 0>(c.g, c.xprev, zo + N, c.ilane && ROW_IN(1), c.in0, c.in1, NN, z + 2 < c.zb, Gi[1], Xi[1]);
         if (R >= 2)
-            load_inputs<EVEN, DOTS>(c.g, c.xprev, zo + 2 * N, c.ilane && ROW_IN(2), c.in0, c.in1, NN, z + 2 < c.zb,
+            load_inputs<EVEN, DOTS != 0>(c.g, c.xprev, zo + 2 * N, c.ilane && ROW_IN(2), c.in0, c.in1, NN, z + 2 < c.zb,
                                     Gi[2], Xi[2]);
     }
     // closing shares for the next lane's cell 0 (toR) and the previous lane's
@@ -262,7 +271,7 @@ __device__ __forceinline__ void prior_step(const MarchCtx &c, int z, float2 (&Pc
     for (int i = 0; i < RR; ++i) {
         const bool intr = i >= 1 && i <= R;
         if (GRAD && intr && i + 2 <= R && own)
-            load_inputs<EVEN, DOTS>(c.g, c.xprev, zo + (i + 2) * N, c.ilane && ROW_IN(i + 2), c.in0, c.in1, NN,
+            load_inputs<EVEN, DOTS != 0>(c.g, c.xprev, zo + (i + 2) * N, c.ilane && ROW_IN(i + 2), c.in0, c.in1, NN,
                                     z + 2 < c.zb, Gi[i + 2], Xi[i + 2]);
         // shifted copies of the rows this row is the first to need
         if (i + 1 < RR) {
@@ -342,11 +351,22 @@ __device__ __forceinline__ void prior_step(const MarchCtx &c, int z, float2 (&Pc
                 acc.y -= from_next(toLc[i]);
                 const float2 gn = fma2k(acc, c.gscale2, Gi[i]);
                 const float2 out = DOTS ? fma2k(gn, c.nstep2, fm) : gn;
+                // DOTS = 2: x_{k+1} over x_prev, z_{k+1} = x_{k+1} + beta (x_{k+1} - x_k) over g
+                float *const dst = DOTS == 2 ? c.xprev : c.g;
                 if (EVEN) {
-                    stg2_if(c.g + o, out, m0);
+                    stg2_if(dst + o, out, m0);
                 } else {
-                    stg1_if(c.g + o, out.x, m0);
-                    stg1_if(c.g + o + 1, out.y, m1);
+                    stg1_if(dst + o, out.x, m0);
+                    stg1_if(dst + o + 1, out.y, m1);
+                }
+                if (DOTS == 2) {
+                    const float2 zn = fma2k(sub2(out, Xi[i]), c.beta2, out);
+                    if (EVEN) {
+                        stg2_if(c.g + o, zn, m0);
+                    } else {
+                        stg1_if(c.g + o, zn.x, m0);
+                        stg1_if(c.g + o + 1, zn.y, m1);
+                    }
                 }
                 if (DOTS) {
                     // <g, f - x_prev>: f - x_prev exactly as dd + de, then exact products (TwoSum)
@@ -394,11 +414,11 @@ __device__ __forceinline__ void prior_step(const MarchCtx &c, int z, float2 (&Pc
 
 // The march of one warp over its z chunk.  MK: a border strip (a mask per
 // pair); else every cell of the strip, halo included, lies in the volume.
-template <bool WANT_H, bool DOTS, bool GRAD, int DIMS, bool EVEN, bool MK>
+template <bool WANT_H, int DOTS, bool GRAD, int DIMS, bool EVEN, bool MK>
 __device__ __forceinline__ void prior_march(const float *__restrict__ f, float *__restrict__ g,
-                                            const float *__restrict__ xprev, const PriorArgs &a,
-                                            int gx, int y0, int za, int zb, Acc2 &ah, Acc2 &ad1,
-                                            Acc2 &ad2) {
+                                            float *__restrict__ xprev, const PriorArgs &a,
+                                            unsigned long long beta2, int gx, int y0, int za, int zb,
+                                            Acc2 &ah, Acc2 &ad1, Acc2 &ad2) {
     MarchCtx c;
     c.f = f;
     c.g = g;
@@ -439,6 +459,7 @@ __device__ __forceinline__ void prior_march(const float *__restrict__ f, float *
     }
     c.gscale2 = a.gscale2;
     c.nstep2 = a.nstep2;
+    c.beta2 = beta2;
 
     const int zs = (DIMS == 3 && za > 0) ? za - 1 : za;
     float2 Pc[RR], Pn[RR], Ac[RR], An[RR], Gi[RR], Xi[RR];
@@ -465,10 +486,10 @@ __device__ __forceinline__ void prior_march(const float *__restrict__ f, float *
     if (z < zb) prior_step<WANT_H, DOTS, GRAD, DIMS, EVEN, MK, false>(c, z, Pc, Pn, Ac, An, Gi, Xi, ah, ad1, ad2);
 }
 
-template <bool WANT_H, bool DOTS, bool GRAD, int DIMS, bool EVEN>
+template <bool WANT_H, int DOTS, bool GRAD, int DIMS, bool EVEN>
 __global__ void __launch_bounds__(THREADS, MIN_BLOCKS)
     k_prior(const float *__restrict__ f, float *__restrict__ g, double *__restrict__ part_h,
-            const PriorArgs a, const float *__restrict__ xprev, double *__restrict__ pd1,
+            const PriorArgs a, float *__restrict__ xprev, double *__restrict__ pd1,
             double *__restrict__ pd2) {
     __shared__ double red[WPB];
     const int N = a.N;
@@ -481,10 +502,23 @@ __global__ void __launch_bounds__(THREADS, MIN_BLOCKS)
     ah.zero();
     ad1.zero();
     ad2.zero();
+    unsigned long long beta2 = 0;
+    if (DOTS == 2) {
+        // beta of an iteration without restart, as the solver's scalar step
+        // forms it from t_k (the restart test that follows this pass may
+        // still set beta = 0; the solver then copies x_{k+1} over z_{k+1})
+        const double t = a.scal[SC_T];
+        const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
+        const float bf = (float)((t - 1.0) / tn);
+        beta2 = f2_pack(make_float2(bf, bf));
+    }
     if (y0 < N && za < zb) {
         const bool full = EVEN && x0 >= 2 && x0 + TX + 2 <= N && y0 >= 1 && y0 + R + 1 <= N;
-        if (full) prior_march<WANT_H, DOTS, GRAD, DIMS, EVEN, false>(f, g, xprev, a, gx, y0, za, zb, ah, ad1, ad2);
-        else prior_march<WANT_H, DOTS, GRAD, DIMS, EVEN, true>(f, g, xprev, a, gx, y0, za, zb, ah, ad1, ad2);
+        if (full)
+            prior_march<WANT_H, DOTS, GRAD, DIMS, EVEN, false>(f, g, xprev, a, beta2, gx, y0, za, zb, ah, ad1,
+                                                              ad2);
+        else
+            prior_march<WANT_H, DOTS, GRAD, DIMS, EVEN, true>(f, g, xprev, a, beta2, gx, y0, za, zb, ah, ad1, ad2);
     }
     const int bid = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
     if (WANT_H) {

@@ -18,7 +18,8 @@ namespace {
 const char *kNames[TCK_COUNT] = {
     "k_fwd_col", "k_fwd_row", "k_fwd_det", "k_adj_det", "k_adj_row", "k_adj_col",
     "k_prior", "k_dots_gzx_gg", "k_update", "k_reduce_finalize", "k_solver_scalar",
-    "k_dot", "k_scale_inv_sqrt", "k_fill_scalars", "k_nrm_col_fwd", "k_nrm_row", "k_nrm_col_adj"};
+    "k_dot", "k_scale_inv_sqrt", "k_fill_scalars", "k_nrm_col_fwd", "k_nrm_row", "k_nrm_col_adj",
+    "k_prior_next", "k_restart_fixup"};
 
 struct Rec {
     int id;

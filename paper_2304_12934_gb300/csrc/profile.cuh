@@ -6,7 +6,7 @@
 enum {
     TCK_FWD_COL = 0, TCK_FWD_ROW, TCK_FWD_DET, TCK_ADJ_DET, TCK_ADJ_ROW, TCK_ADJ_COL,
     TCK_PRIOR, TCK_DOTS, TCK_UPDATE, TCK_REDUCE, TCK_SCALAR, TCK_DOT, TCK_SCALE, TCK_FILL,
-    TCK_NRM_COL_FWD, TCK_NRM_ROW, TCK_NRM_COL_ADJ,
+    TCK_NRM_COL_FWD, TCK_NRM_ROW, TCK_NRM_COL_ADJ, TCK_PRIOR_NEXT, TCK_FIXUP,
     TCK_COUNT
 };
 

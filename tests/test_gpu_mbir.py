@@ -150,6 +150,45 @@ def test_resume_equals_uninterrupted_bitwise(api):
     assert torch.equal(x1, x2)
 
 
+@pytest.mark.parametrize("restart", [True, False])
+def test_fused_momentum_point_across_calls_and_restarts(api, restart):
+    """Every iteration with a prior makes z_{k+1} inside the prior pass (a copy
+    of x_{k+1} after a restart), and the state's z and g buffers exchange roles
+    each iteration.  One call of 13 iterations and 13 calls of one iteration
+    (the exchange handed back through the state) give the same x, z, t and
+    restart count, bit for bit.  Both resume from x = z = 0 with momentum
+    t = 20, from which the gradient test restarts (at the fourth iteration in
+    the FP64 oracle), so both branches of the check-and-copy run; the result
+    matches the oracle's iteration from the same state to 1e-3."""
+    f, b = _data(2)
+    lam = 1e-3
+    step = _step(lam)
+    prior = api.Prior(lam=lam, dims=3)
+    n = 13
+    xo, log = oracle.mbir_solve(b, None, N, n, step, lam=lam, prior=dict(p=prior.p, sigma=prior.sigma, c=prior.c),
+                                dims=3, restart=restart, return_log=True, z0=np.zeros((2, N, N)), t0=20.0)
+    with api.Plan(N, A, D, max_batch=2) as plan:
+        bt = t32(b)
+        out = []
+        for single in (False, True):
+            x = torch.zeros((2, N, N), device="cuda:0")
+            st = api.SolveState(x)
+            st.z.zero_()
+            st.t, st.k = 20.0, 1
+            for _ in range(n if single else 1):
+                api.mbir_solve(plan, bt, None, x, 1 if single else n, step, prior, restart=restart, state=st)
+            out.append((x, st))
+    (x1, st1), (x2, st2) = out
+    assert st1.k == st2.k == n + 1
+    assert st1.n_restarts == st2.n_restarts == sum(e["restart"] for e in log)
+    if restart:
+        assert st1.n_restarts > 0
+    assert torch.equal(x1, x2)
+    assert torch.equal(st1.z, st2.z)
+    assert st1.t == st2.t
+    assert rel(np64(x1), xo) <= 1e-3
+
+
 def test_host_buffer_solve_matches_device_solve(api):
     f, b = _data(1)
     step = _step(1e-3)
