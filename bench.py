@@ -181,6 +181,28 @@ def algorithmic_bytes(name, N, A, D, w, B):
     return per.get(name, 0) * B
 
 
+def prior_roofline(api, dev, name, N, units, dims, avg_s, hbm, timing):
+    """The prior kernel's roof is the special-function unit, not HBM: every
+    unordered neighbour pair costs one lg2, one ex2 and one rcp per cell
+    (13 pairs per voxel with 26 neighbours, 4 with 8), and 20 bytes per voxel
+    would stream in a third of that time.  The unit's rates are measured here
+    (tc_sfu_throughput); the peak is the pair rate they allow,
+    1 / (1/r_lg2 + 1/r_ex2 + 1/r_rcp).  The HBM view is kept beside it."""
+    r = {op: api.sfu_throughput(op, dev) for op in ("lg2", "ex2", "rcp")}
+    peak = 1.0 / sum(1.0 / v for v in r.values())
+    pairs = (13 if dims == 3 else 4) * N * N * units
+    ach = pairs / avg_s
+    return {"bound": "alu", "kernel": name, "achieved": round(ach / 1e9, 1), "peak": round(peak / 1e9, 1),
+            "unit": "Gpair/s", "frac": round(ach / peak, 4), "traffic": hbm["traffic"],
+            "pairs_per_launch": pairs,
+            "peak_kind": ("special-function unit, measured in this run (lane-ops/s: "
+                          + ", ".join(f"{k} {v:.3e}" for k, v in r.items())
+                          + "); one lg2, ex2 and rcp per unordered pair and cell"),
+            "timing": timing,
+            "hbm": {"achieved": hbm["achieved"], "peak": hbm["peak"], "unit": "GB/s", "frac": hbm["frac"],
+                    "alg_bytes_per_launch": hbm["alg_bytes_per_launch"], "peak_kind": hbm["peak_kind"]}}
+
+
 def launch_units(name, B_total, chunk):
     """Slices processed by one launch of each kernel."""
     if name in ("k_prior", "k_prior_next", "k_dots_gzx_gg", "k_update", "k_restart_fixup"):
@@ -621,11 +643,14 @@ def run_ours(args):
                    "gbs_alg": round(algorithmic_bytes(k, N, A, D, plan.kernel_width,
                                                       launch_units(k, B, MB)) / (m / c / 1e3) / 1e9, 1)}
                for k, (c, m) in sorted(prof.items(), key=lambda kv: -kv[1][1])}
+    timing = (f"CUDA events around each launch, separate pass of {prof_steps} iterations "
+              f"({prof_wall:.2f} s) right after the timed region")
     roofline = {"bound": "hbm", "kernel": dname, "achieved": round(achieved, 1), "peak": peak,
                 "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic_for(dname, units),
                 "alg_bytes_per_launch": alg, "peak_kind": f"{peak_kind} hbm_gbs (burst copy)",
-                "timing": f"CUDA events around each launch, separate pass of {prof_steps} iterations "
-                          f"({prof_wall:.2f} s) right after the timed region"}
+                "timing": timing}
+    if dname in ("k_prior", "k_prior_next"):
+        roofline = prior_roofline(api, dev, dname, N, units, prior.dims, avg_s, roofline, timing)
 
     # ---- batched vs plain on a subset (same inputs, same iteration)
     plain = None

@@ -391,6 +391,15 @@ const char *tc_profile_kernel_name(int id);
 /* Kernel launches issued by this library since it was loaded (host counter). */
 long long tc_launch_count(void);
 
+/* Throughput of the special-function unit on the current device (no
+ * counterpart in the paper; it is the roof of the prior kernel, whose pair
+ * evaluations take one lg2, one ex2 and one rcp per cell): op 0 lg2.approx,
+ * 1 ex2.approx, 2 rcp.approx.  Runs independent chains of the operation on
+ * 8 CTAs of 256 threads per SM and returns lane operations per second in
+ * *lane_ops_per_s (HOST).  Synchronous on `stream`; allocates nothing on the
+ * device.  TC_ERR_INVALID_ARG for another op or a NULL output. */
+int tc_sfu_throughput(int op, double *lane_ops_per_s, void *stream);
+
 /* ------------------------------------------------------ device status --- */
 /* Kernels that wait on a device barrier (the TMA-staged forward column pass)
  * bound each wait to one second; on expiry they record TC_ERR_TIMEOUT in the

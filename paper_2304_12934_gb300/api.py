@@ -62,7 +62,7 @@ SYMBOLS = ("tc_status_string", "tc_last_error_detail", "tc_plan_create", "tc_pla
            "tc_checkpoint_save", "tc_checkpoint_load", "tc_test_fail_copy_after",
            "tc_plan_group_create", "tc_plan_group_destroy", "tc_plan_group_device_bytes",
            "radon_fwd_group", "radon_adj_group", "mbir_grad_group", "tc_plan_set_spread_chunk",
-           "tc_plan_get_spread_chunk", "tc_plan_autotune_spread")
+           "tc_plan_get_spread_chunk", "tc_plan_autotune_spread", "tc_sfu_throughput")
 
 
 def lib_path() -> str:
@@ -124,6 +124,7 @@ def load(build_if_missing: bool = True):
     L.tc_plan_set_spread_chunk.argtypes = [vp, i]
     L.tc_plan_get_spread_chunk.argtypes = [vp]
     L.tc_plan_autotune_spread.argtypes = [vp, vp, vp, i, i, ctypes.POINTER(i), vp]
+    L.tc_sfu_throughput.argtypes = [i, ctypes.POINTER(d), vp]
     for fn in ("tc_profile_enable", "tc_profile_collect", "tc_plan_create", "tc_plan_destroy",
                "radon_fwd", "radon_adj", "mbir_grad", "mbir_power_norm", "mbir_solve",
                "mbir_solve_host", "tc_plan_autotune", "tc_plan_set_launch",
@@ -131,7 +132,7 @@ def load(build_if_missing: bool = True):
                "tc_checkpoint_save", "tc_checkpoint_load", "tc_test_fail_copy_after",
            "tc_plan_group_create", "tc_plan_group_destroy", "tc_plan_group_device_bytes",
            "radon_fwd_group", "radon_adj_group", "mbir_grad_group", "tc_plan_set_spread_chunk",
-           "tc_plan_get_spread_chunk", "tc_plan_autotune_spread"):
+           "tc_plan_get_spread_chunk", "tc_plan_autotune_spread", "tc_sfu_throughput"):
         getattr(L, fn).restype = i
     _LIB = L
     return L
@@ -619,6 +620,18 @@ def fail_copy_after(after: int):
     """Testing hook: the copy of mbir_solve_host after `after` more copies
     reports a CUDA failure instead of running (negative: off)."""
     _check("tc_test_fail_copy_after", load().tc_test_fail_copy_after(int(after)))
+
+
+def sfu_throughput(op: str, device=None) -> float:
+    """Lane operations per second of the special-function unit for op in
+    ("lg2", "ex2", "rcp"), measured on the device (tc_sfu_throughput)."""
+    code = {"lg2": 0, "ex2": 1, "rcp": 2}[op]
+    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    out = ctypes.c_double()
+    with torch.cuda.device(dev):
+        _check("tc_sfu_throughput", load().tc_sfu_throughput(code, ctypes.byref(out),
+                                                             _stream(None, dev)))
+    return out.value
 
 
 def profile_enable(on: bool = True):

@@ -59,6 +59,7 @@
 #include "common.cuh"
 #include "f32x2.cuh"
 #include "profile.cuh"
+#include "sfu.cuh"
 
 namespace {
 
@@ -99,22 +100,6 @@ struct PriorArgs {
     unsigned long long nstep2;   // DOTS: minus the solver's step (g receives f - step grad)
     const double *scal;          // DOTS = 2: the solver's scalars (momentum t_k at SC_T)
 };
-
-__device__ __forceinline__ float lg2a(float x) {
-    float r;
-    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return r;
-}
-__device__ __forceinline__ float ex2a(float x) {
-    float r;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return r;
-}
-__device__ __forceinline__ float rcpa(float x) {
-    float r;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return r;
-}
 
 // Global accesses under a predicate, without a branch (zeros when off).
 __device__ __forceinline__ float2 ldg2_if(const float *p, bool c) {

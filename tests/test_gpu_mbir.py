@@ -189,6 +189,21 @@ def test_fused_momentum_point_across_calls_and_restarts(api, restart):
     assert rel(np64(x1), xo) <= 1e-3
 
 
+def test_special_function_unit_probe(api):
+    """The measured lg2 / ex2 / rcp rates behind the prior kernel's roofline:
+    positive, at least one lane operation per clock and SM at 1 GHz (all
+    Blackwell parts run these at 16 lanes per clock and SM or more), and an
+    unknown operation is rejected before any launch."""
+    import ctypes
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    for op in ("lg2", "ex2", "rcp"):
+        r = api.sfu_throughput(op)
+        assert r > sms * 1e9, (op, r)
+    out = ctypes.c_double()
+    assert api.load().tc_sfu_throughput(3, ctypes.byref(out), None) == -1
+    assert api.load().tc_sfu_throughput(0, None, None) == -1
+
+
 def test_host_buffer_solve_matches_device_solve(api):
     f, b = _data(1)
     step = _step(1e-3)
