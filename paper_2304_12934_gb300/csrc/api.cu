@@ -78,13 +78,12 @@ int data_grad_chunk(tc_plan *p, const float *x, const float *b, const float *w, 
 // dot_x: with a prior, the prior kernel also forms the restart-test inner
 // products <grad, x - dot_x> and <grad, grad>.
 // atb: A^T b of the whole batch for the normal-operator data term (W = I).
-// next (with dot_x): the prior kernel leaves the next iterate in dot_x and the
+// With dot_x the prior kernel leaves the next iterate in dot_x and the
 // momentum point of an iteration without restart in grad (launch_prior_grad).
 int grad_impl(tc_plan *p, const float *x, const float *b, const float *w,
               const tc_prior *prior, float *grad, int batch, cudaStream_t s,
               bool want_value = true, const cudaEvent_t *ready = nullptr,
-              float *dot_x = nullptr, double step = 0.0, const float *atb = nullptr,
-              bool next = false) {
+              float *dot_x = nullptr, double step = 0.0, const float *atb = nullptr) {
     int rc = data_init(p, atb, s);
     if (rc) return rc;
     const size_t ni = img_elems(p), ns = sino_elems(p);
@@ -97,7 +96,7 @@ int grad_impl(tc_plan *p, const float *x, const float *b, const float *w,
     }
     if (prior && prior->lambda != 0.0) {
         rc = launch_prior_grad(p, x, grad, batch, prior, want_value ? p->scal + SC_PRIOR : nullptr, s, dot_x,
-                               0, -1, step, next);
+                               0, -1, step);
         if (rc) return rc;
     }
     return TC_OK;
@@ -382,7 +381,7 @@ int last_iteration_streamed(tc_plan *p, const float *b, const float *w, float *x
     const int nslab = (batch + p->chunk - 1) / p->chunk;
     auto finish = [&](int j) -> int {
         const int z0 = j * p->chunk, z1 = z0 + p->chunk < batch ? z0 + p->chunk : batch;
-        int rc = launch_prior_grad(p, z, gb, batch, prior, p->scal + SC_PRIOR, s, x, z0, z1, step, true);
+        int rc = launch_prior_grad(p, z, gb, batch, prior, p->scal + SC_PRIOR, s, x, z0, z1, step);
         if (rc) return rc;
         cudaEvent_t e = nullptr;
         TC_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
@@ -479,7 +478,7 @@ int solve_loop(tc_plan *p, const float *b, const float *w, float *x, int batch,
             if (out && last) {
                 rc = last_iteration_streamed(p, b, w, x, zc, gc, batch, prior, opts, step, s, rd, *out, atb);
             } else {
-                rc = grad_impl(p, zc, b, w, prior, gc, batch, s, last, rd, x, step, atb, true);
+                rc = grad_impl(p, zc, b, w, prior, gc, batch, s, last, rd, x, step, atb);
                 if (!rc) rc = launch_solver_scalar(p, opts->restart, s);
                 if (!rc && opts->restart == 1) rc = launch_restart_fixup(p, gc, x, n, s);
             }

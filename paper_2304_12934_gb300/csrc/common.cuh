@@ -218,19 +218,18 @@ int launch_radon_normal_chunk(tc_plan *p, const float *x, float *out, int nb, co
                               const float *xdot, double *obj_acc, cudaStream_t s);
 // Builds the embedding's tables once per plan (synchronous on s).
 int normal_prepare(tc_plan *p, cudaStream_t s);
-// g += lambda grad H(x); h_acc (or NULL) = lambda H(x); with dot_x, also
-// scal[SC_DOT_GZX] = <g, x - dot_x>, scal[SC_DOT_GG] = <g, g> of the final g,
-// and g then receives x - step g (the solver's next iterate) instead.
-// next (with dot_x): the next iterate x - step g goes to dot_x (over x_k)
-// instead, and g receives the momentum point x_{k+1} + beta (x_{k+1} - x_k)
-// with the beta of an iteration without restart (from scal[SC_T]).
+// g += lambda grad H(x); h_acc (or NULL) = lambda H(x).  With dot_x (the
+// solver's x_k), also scal[SC_DOT_GZX] = <g, x - dot_x> and scal[SC_DOT_GG] =
+// <g, g> of the final g, and the gradient is not stored: the next iterate
+// x - step g goes to dot_x (over x_k), and g receives the momentum point
+// x_{k+1} + beta (x_{k+1} - x_k) with the beta of an iteration without
+// restart (from scal[SC_T]).
 // x holds nb slices; only slices [z0, z1) (z1 < 0: nb) get their gradient
 // (neighbours outside the range are read) and enter the sums, which a slab
 // with z0 > 0 adds to those already held.
 int launch_prior_grad(tc_plan *p, const float *x, float *g, int nb,
                       const tc_prior *pr, double *h_acc, cudaStream_t s,
-                      float *dot_x = nullptr, int z0 = 0, int z1 = -1, double step = 0.0,
-                      bool next = false);
+                      float *dot_x = nullptr, int z0 = 0, int z1 = -1, double step = 0.0);
 // Tiles of one prior launch on N x N slices, and the FP64 partial-sum slots
 // its z-chunked grid may use.
 int prior_tile_count(int n);

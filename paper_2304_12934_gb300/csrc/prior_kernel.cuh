@@ -39,11 +39,10 @@
 // the first starts one plane below, evaluating that plane's z+1 pairs only).
 //
 // In the solver (DOTS) the gradient is not stored: the next iterate
-// x_{k+1} = f - step g is, in place of g (DOTS = 1), or in place of x_prev
-// (DOTS = 2, which also writes the momentum point of an iteration without
-// restart, x_{k+1} + beta (x_{k+1} - x_k), in place of g, so the solver
-// needs no separate update pass).  Both x_prev and g are read only at the
-// warp's own cells, once, before these stores.
+// x_{k+1} = f - step g goes in place of x_prev, and the momentum point of an
+// iteration without restart, x_{k+1} + beta (x_{k+1} - x_k), in place of g,
+// so the solver needs no separate update pass.  Both x_prev and g are read
+// only at the warp's own cells, once, before these stores.
 //
 // Sums: H per step in FP32 (one plane's rows of one lane) added into a
 // compensated pair; the restart-test inner products <g, f - x_prev> and
@@ -98,7 +97,7 @@ struct PriorArgs {
     unsigned long long wh2[3];   // w per weight class (the H terms)
     unsigned long long gscale2;  // 2 lambda / (sigma^2 c)
     unsigned long long nstep2;   // DOTS: minus the solver's step (g receives f - step grad)
-    const double *scal;          // DOTS = 2: the solver's scalars (momentum t_k at SC_T)
+    const double *scal;          // DOTS: the solver's scalars (momentum t_k at SC_T)
 };
 
 // Global accesses under a predicate, without a branch (zeros when off).
@@ -213,14 +212,14 @@ struct MarchCtx {
     bool go;                 // true (a runtime value: the blocks of pairs stay separate)
     unsigned xm0, xm1, rm;   // border strips: (cell, neighbour at dx) inside, bit dx + 1; rows inside, bit i
     unsigned long long ql2, lk2, one2, wq[3], wp[3], wh[3], gscale2, nstep2;
-    unsigned long long beta2;   // DOTS = 2: the momentum coefficient without restart
+    unsigned long long beta2;   // DOTS: the momentum coefficient without restart
 };
 
 // One step of the march: plane z in Pc, plane z + 1 in Pn (3D), their
 // gradient sums in Ac / An (Ac already holding the z+1 closings from plane
 // z - 1).  FAST: plane z is produced by this chunk and (3D) has a plane above,
 // so no pair needs a branch.  On return Pc, Pn, Ac hold the next step's.
-template <bool WANT_H, int DOTS, bool GRAD, int DIMS, bool EVEN, bool MK, bool FAST>
+template <bool WANT_H, bool DOTS, bool GRAD, int DIMS, bool EVEN, bool MK, bool FAST>
 __device__ __forceinline__ void prior_step(const MarchCtx &c, int z, float2 (&Pc)[RR], float2 (&Pn)[RR],
                                            float2 (&Ac)[RR], float2 (&An)[RR], float2 (&Gi)[RR],
                                            float2 (&Xi)[RR], Acc2 &ah, Acc2 &ad1, Acc2 &ad2) {
@@ -240,9 +239,9 @@ __device__ __forceinline__ void prior_step(const MarchCtx &c, int z, float2 (&Pc
         if (GRAD) An[i] = make_float2(0.f, 0.f);
     }
     if (GRAD && own) {
-        load_inputs<EVEN, DOTS != 0>(c.g, c.xprev, zo + N, c.ilane && ROW_IN(1), c.in0, c.in1, NN, z + 2 < c.zb, Gi[1], Xi[1]);
+        load_inputs<EVEN, DOTS>(c.g, c.xprev, zo + N, c.ilane && ROW_IN(1), c.in0, c.in1, NN, z + 2 < c.zb, Gi[1], Xi[1]);
         if (R >= 2)
-            load_inputs<EVEN, DOTS != 0>(c.g, c.xprev, zo + 2 * N, c.ilane && ROW_IN(2), c.in0, c.in1, NN, z + 2 < c.zb,
+            load_inputs<EVEN, DOTS>(c.g, c.xprev, zo + 2 * N, c.ilane && ROW_IN(2), c.in0, c.in1, NN, z + 2 < c.zb,
                                     Gi[2], Xi[2]);
     }
     // closing shares for the next lane's cell 0 (toR) and the previous lane's
@@ -256,7 +255,7 @@ __device__ __forceinline__ void prior_step(const MarchCtx &c, int z, float2 (&Pc
     for (int i = 0; i < RR; ++i) {
         const bool intr = i >= 1 && i <= R;
         if (GRAD && intr && i + 2 <= R && own)
-            load_inputs<EVEN, DOTS != 0>(c.g, c.xprev, zo + (i + 2) * N, c.ilane && ROW_IN(i + 2), c.in0, c.in1, NN,
+            load_inputs<EVEN, DOTS>(c.g, c.xprev, zo + (i + 2) * N, c.ilane && ROW_IN(i + 2), c.in0, c.in1, NN,
                                     z + 2 < c.zb, Gi[i + 2], Xi[i + 2]);
         // shifted copies of the rows this row is the first to need
         if (i + 1 < RR) {
@@ -336,15 +335,15 @@ __device__ __forceinline__ void prior_step(const MarchCtx &c, int z, float2 (&Pc
                 acc.y -= from_next(toLc[i]);
                 const float2 gn = fma2k(acc, c.gscale2, Gi[i]);
                 const float2 out = DOTS ? fma2k(gn, c.nstep2, fm) : gn;
-                // DOTS = 2: x_{k+1} over x_prev, z_{k+1} = x_{k+1} + beta (x_{k+1} - x_k) over g
-                float *const dst = DOTS == 2 ? c.xprev : c.g;
+                // DOTS: x_{k+1} over x_prev, z_{k+1} = x_{k+1} + beta (x_{k+1} - x_k) over g
+                float *const dst = DOTS ? c.xprev : c.g;
                 if (EVEN) {
                     stg2_if(dst + o, out, m0);
                 } else {
                     stg1_if(dst + o, out.x, m0);
                     stg1_if(dst + o + 1, out.y, m1);
                 }
-                if (DOTS == 2) {
+                if (DOTS) {
                     const float2 zn = fma2k(sub2(out, Xi[i]), c.beta2, out);
                     if (EVEN) {
                         stg2_if(c.g + o, zn, m0);
@@ -399,7 +398,7 @@ __device__ __forceinline__ void prior_step(const MarchCtx &c, int z, float2 (&Pc
 
 // The march of one warp over its z chunk.  MK: a border strip (a mask per
 // pair); else every cell of the strip, halo included, lies in the volume.
-template <bool WANT_H, int DOTS, bool GRAD, int DIMS, bool EVEN, bool MK>
+template <bool WANT_H, bool DOTS, bool GRAD, int DIMS, bool EVEN, bool MK>
 __device__ __forceinline__ void prior_march(const float *__restrict__ f, float *__restrict__ g,
                                             float *__restrict__ xprev, const PriorArgs &a,
                                             unsigned long long beta2, int gx, int y0, int za, int zb,
@@ -471,7 +470,7 @@ __device__ __forceinline__ void prior_march(const float *__restrict__ f, float *
     if (z < zb) prior_step<WANT_H, DOTS, GRAD, DIMS, EVEN, MK, false>(c, z, Pc, Pn, Ac, An, Gi, Xi, ah, ad1, ad2);
 }
 
-template <bool WANT_H, int DOTS, bool GRAD, int DIMS, bool EVEN>
+template <bool WANT_H, bool DOTS, bool GRAD, int DIMS, bool EVEN>
 __global__ void __launch_bounds__(THREADS, MIN_BLOCKS)
     k_prior(const float *__restrict__ f, float *__restrict__ g, double *__restrict__ part_h,
             const PriorArgs a, float *__restrict__ xprev, double *__restrict__ pd1,
@@ -488,7 +487,7 @@ __global__ void __launch_bounds__(THREADS, MIN_BLOCKS)
     ad1.zero();
     ad2.zero();
     unsigned long long beta2 = 0;
-    if (DOTS == 2) {
+    if (DOTS) {
         // beta of an iteration without restart, as the solver's scalar step
         // forms it from t_k (the restart test that follows this pass may
         // still set beta = 0; the solver then copies x_{k+1} over z_{k+1})

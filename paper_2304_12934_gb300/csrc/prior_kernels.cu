@@ -51,36 +51,30 @@ int z_chunks(int n, int nb, int max_blocks) {
     return c;
 }
 
-template <bool H, int DOTS, bool GRAD, int DIMS, bool EVEN>
+template <bool H, bool DOTS, bool GRAD, int DIMS, bool EVEN>
 void launch_one(dim3 grid, cudaStream_t s, bool profiled, const float *x, float *g, double *ph,
                 const PriorArgs &a, float *xp, double *p1, double *p2) {
     if (profiled)
-        TC_PROFILED(DOTS == 2 ? TCK_PRIOR_NEXT : TCK_PRIOR, s,
+        TC_PROFILED(DOTS ? TCK_PRIOR_NEXT : TCK_PRIOR, s,
                     (k_prior<H, DOTS, GRAD, DIMS, EVEN><<<grid, THREADS, 0, s>>>(x, g, ph, a, xp, p1, p2)));
     else
         k_prior<H, DOTS, GRAD, DIMS, EVEN><<<grid, THREADS, 0, s>>>(x, g, ph, a, xp, p1, p2);
 }
 
-// dispatch on (WANT_H, DOTS, DIMS) for the gradient kernels; dots: 0 none,
-// 1 with the next iterate in place of g, 2 with the next iterate in place of
-// x_prev and the momentum point in place of g
+// dispatch on (WANT_H, DOTS, DIMS) for the gradient kernels
 template <bool EVEN>
-void launch_grad(bool h, int dots, int dims, dim3 grid, cudaStream_t s, bool prof, const float *x, float *g,
+void launch_grad(bool h, bool dots, int dims, dim3 grid, cudaStream_t s, bool prof, const float *x, float *g,
                  double *ph, const PriorArgs &a, float *xp, double *p1, double *p2) {
     if (dims == 3) {
-        if (h && dots == 1) launch_one<true, 1, true, 3, EVEN>(grid, s, prof, x, g, ph, a, xp, p1, p2);
-        else if (h && dots == 2) launch_one<true, 2, true, 3, EVEN>(grid, s, prof, x, g, ph, a, xp, p1, p2);
-        else if (h) launch_one<true, 0, true, 3, EVEN>(grid, s, prof, x, g, ph, a, xp, p1, p2);
-        else if (dots == 1) launch_one<false, 1, true, 3, EVEN>(grid, s, prof, x, g, ph, a, xp, p1, p2);
-        else if (dots == 2) launch_one<false, 2, true, 3, EVEN>(grid, s, prof, x, g, ph, a, xp, p1, p2);
-        else launch_one<false, 0, true, 3, EVEN>(grid, s, prof, x, g, ph, a, xp, p1, p2);
+        if (h && dots) launch_one<true, true, true, 3, EVEN>(grid, s, prof, x, g, ph, a, xp, p1, p2);
+        else if (h) launch_one<true, false, true, 3, EVEN>(grid, s, prof, x, g, ph, a, xp, p1, p2);
+        else if (dots) launch_one<false, true, true, 3, EVEN>(grid, s, prof, x, g, ph, a, xp, p1, p2);
+        else launch_one<false, false, true, 3, EVEN>(grid, s, prof, x, g, ph, a, xp, p1, p2);
     } else {
-        if (h && dots == 1) launch_one<true, 1, true, 2, EVEN>(grid, s, prof, x, g, ph, a, xp, p1, p2);
-        else if (h && dots == 2) launch_one<true, 2, true, 2, EVEN>(grid, s, prof, x, g, ph, a, xp, p1, p2);
-        else if (h) launch_one<true, 0, true, 2, EVEN>(grid, s, prof, x, g, ph, a, xp, p1, p2);
-        else if (dots == 1) launch_one<false, 1, true, 2, EVEN>(grid, s, prof, x, g, ph, a, xp, p1, p2);
-        else if (dots == 2) launch_one<false, 2, true, 2, EVEN>(grid, s, prof, x, g, ph, a, xp, p1, p2);
-        else launch_one<false, 0, true, 2, EVEN>(grid, s, prof, x, g, ph, a, xp, p1, p2);
+        if (h && dots) launch_one<true, true, true, 2, EVEN>(grid, s, prof, x, g, ph, a, xp, p1, p2);
+        else if (h) launch_one<true, false, true, 2, EVEN>(grid, s, prof, x, g, ph, a, xp, p1, p2);
+        else if (dots) launch_one<false, true, true, 2, EVEN>(grid, s, prof, x, g, ph, a, xp, p1, p2);
+        else launch_one<false, false, true, 2, EVEN>(grid, s, prof, x, g, ph, a, xp, p1, p2);
     }
 }
 
@@ -96,8 +90,7 @@ int prior_block_slots(int n) { return prior_tile_count(n) * ZCHUNK_MAX; }
 
 int launch_prior_grad(tc_plan *p, const float *x, float *g, int nb,
                       const tc_prior *pr, double *h_acc, cudaStream_t s, float *dot_x,
-                      int z0, int z1, double step, bool next) {
-    if (next && !dot_x) return TC_ERR_INVALID_ARG;
+                      int z0, int z1, double step) {
     PriorArgs a = make_prior_args(p->k.N, nb, pr, step);
     a.scal = p->scal;
     if (z1 < 0) z1 = nb;
@@ -112,7 +105,7 @@ int launch_prior_grad(tc_plan *p, const float *x, float *g, int nb,
     if (blocks > p->slot) return TC_ERR_UNSUPPORTED;
     double *part = p->partials + (size_t)1 * p->slot;
     double *p1 = p->partials + (size_t)2 * p->slot, *p2 = p->partials + (size_t)3 * p->slot;
-    launch_grad<true>(h_acc != nullptr, dot_x ? (next ? 2 : 1) : 0, pr->dims, grid, s, true, x, g, part, a, dot_x,
+    launch_grad<true>(h_acc != nullptr, dot_x != nullptr, pr->dims, grid, s, true, x, g, part, a, dot_x,
                       dot_x ? p1 : nullptr, dot_x ? p2 : nullptr);
     TC_LAUNCHED("k_prior");
     if (dot_x) {
@@ -134,9 +127,9 @@ int launch_prior_value(tc_plan *p, const float *x, int nb, const tc_prior *pr,
     if (blocks > p->slot) return TC_ERR_UNSUPPORTED;
     double *part = p->partials + (size_t)1 * p->slot;
     if (pr->dims == 3)
-        launch_one<true, 0, false, 3, true>(grid, s, true, x, nullptr, part, a, nullptr, nullptr, nullptr);
+        launch_one<true, false, false, 3, true>(grid, s, true, x, nullptr, part, a, nullptr, nullptr, nullptr);
     else
-        launch_one<true, 0, false, 2, true>(grid, s, true, x, nullptr, part, a, nullptr, nullptr, nullptr);
+        launch_one<true, false, false, 2, true>(grid, s, true, x, nullptr, part, a, nullptr, nullptr, nullptr);
     TC_LAUNCHED("k_prior");
     return launch_reduce_finalize(part, blocks, h_acc, 0, prior_value_scale(pr), s);
 }
@@ -157,19 +150,19 @@ int launch_prior_kernel_into(const float *x, float *g, int n, int nb, const tc_p
     const bool h = h_out != nullptr, even = n % 2 == 0;
     if (pr->dims == 3) {
         if (even) {
-            if (h) launch_one<true, 0, true, 3, true>(grid, s, false, x, g, partials, a, nullptr, nullptr, nullptr);
-            else launch_one<false, 0, true, 3, true>(grid, s, false, x, g, partials, a, nullptr, nullptr, nullptr);
+            if (h) launch_one<true, false, true, 3, true>(grid, s, false, x, g, partials, a, nullptr, nullptr, nullptr);
+            else launch_one<false, false, true, 3, true>(grid, s, false, x, g, partials, a, nullptr, nullptr, nullptr);
         } else {
-            if (h) launch_one<true, 0, true, 3, false>(grid, s, false, x, g, partials, a, nullptr, nullptr, nullptr);
-            else launch_one<false, 0, true, 3, false>(grid, s, false, x, g, partials, a, nullptr, nullptr, nullptr);
+            if (h) launch_one<true, false, true, 3, false>(grid, s, false, x, g, partials, a, nullptr, nullptr, nullptr);
+            else launch_one<false, false, true, 3, false>(grid, s, false, x, g, partials, a, nullptr, nullptr, nullptr);
         }
     } else {
         if (even) {
-            if (h) launch_one<true, 0, true, 2, true>(grid, s, false, x, g, partials, a, nullptr, nullptr, nullptr);
-            else launch_one<false, 0, true, 2, true>(grid, s, false, x, g, partials, a, nullptr, nullptr, nullptr);
+            if (h) launch_one<true, false, true, 2, true>(grid, s, false, x, g, partials, a, nullptr, nullptr, nullptr);
+            else launch_one<false, false, true, 2, true>(grid, s, false, x, g, partials, a, nullptr, nullptr, nullptr);
         } else {
-            if (h) launch_one<true, 0, true, 2, false>(grid, s, false, x, g, partials, a, nullptr, nullptr, nullptr);
-            else launch_one<false, 0, true, 2, false>(grid, s, false, x, g, partials, a, nullptr, nullptr, nullptr);
+            if (h) launch_one<true, false, true, 2, false>(grid, s, false, x, g, partials, a, nullptr, nullptr, nullptr);
+            else launch_one<false, false, true, 2, false>(grid, s, false, x, g, partials, a, nullptr, nullptr, nullptr);
         }
     }
     TC_LAUNCHED("k_prior");
