@@ -316,7 +316,10 @@ int mbir_solve_host(tc_plan *plan, const float *b_host, const float *w_host,
  * one launch per geometry class (the geometries of one image side and, for
  * the detector passes, one detector-transform kind), one CTA per item, with up
  * to four geometries in the launch's parameter block and the costliest items
- * first.  Stage boundaries are kernel boundaries (no CTA waits for another).
+ * first.  The class launches of a stage, and the per-geometry prior launches,
+ * are independent and run side by side on up to 7 streams the group owns,
+ * forked from and joined back into the caller's stream with events.  Stage
+ * boundaries are kernel boundaries (no CTA waits for another).
  * Results are those of the per-geometry plans to within 1e-6 relative (the
  * group kernels are separate compilations of the same pass bodies, so a
  * multiply-add may be fused differently), and deterministic.

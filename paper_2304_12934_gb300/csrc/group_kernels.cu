@@ -16,7 +16,12 @@
 // tickets -- made the compiler keep each body's geometry-derived values live
 // across items: 600 to 2,500 bytes of register spills per thread at the
 // per-plan kernels' occupancy, where one item per CTA needs 44 registers.)
-// Stage boundaries are kernel boundaries: no CTA ever waits for another.
+// The class launches of one stage touch disjoint geometries, so they run side
+// by side on the group's streams (forked from the caller's stream by an event
+// and joined back before the next stage), as do the per-geometry prior
+// launches; the small geometries' launches then fill the SMs that the large
+// ones leave idle in their tails.  Stage boundaries are kernel boundaries: no
+// CTA ever waits for another.
 // The arithmetic is the per-plan kernels'; results agree with the
 // per-geometry plans to FP32 rounding (separately compiled kernels may fuse a
 // multiply and an add differently), and the data term's FP64 partials are
@@ -51,6 +56,7 @@ struct GroupGeom {
 
 // One class launch: its geometries and the first item of each.
 constexpr int GK_MAXG = 4;
+constexpr int GK_SIDE = 7;   // side streams of a group (besides the caller's)
 struct ClassParams {
     int ng;                    // geometries of this launch (1..GK_MAXG)
     int starts[GK_MAXG + 1];   // first item of each geometry; starts[ng] = items of the launch
@@ -155,12 +161,24 @@ struct tc_plan_group {
     GroupGeom *dgeoms = nullptr;     // caller's order
     std::vector<ClassLaunch> launches;
     long long bytes = 0;
+    // the class launches of one stage, and the per-geometry prior launches,
+    // are independent: they run side by side on these streams, forked from
+    // and joined back into the caller's stream with events (so a captured
+    // call stays one graph)
+    std::vector<cudaStream_t> side;
+    cudaEvent_t fork = nullptr;
+    std::vector<cudaEvent_t> join;
 };
 
 namespace {
 
 void group_free(tc_plan_group *g) {
     if (!g) return;
+    for (cudaStream_t q : g->side)
+        if (q) cudaStreamDestroy(q);
+    for (cudaEvent_t e : g->join)
+        if (e) cudaEventDestroy(e);
+    if (g->fork) cudaEventDestroy(g->fork);
     for (tc_plan *p : g->plans) tc_plan_free(p);
     for (void *q : {(void *)g->dgeoms})
         if (q) cudaFree(q);
@@ -220,11 +238,39 @@ int class_config(ClassLaunch &c) {
 
 // Runs every class launch of one stage (x: images in; y: sinograms in or
 // out; b, w, mode: the forward detector pass's epilogue; xo: images out).
-int launch_stage(tc_plan_group *g, int st, cudaStream_t s, const float *x, float *y, const float *b,
+// Runs f(q, j) for j = 0..n-1, the first on s and the others on the group's
+// side streams (round robin), each side stream forked from s before and
+// joined into s after.
+template <class F>
+int fan_out(tc_plan_group *g, cudaStream_t s, int n, F &&f) {
+    const int ns = (int)g->side.size();
+    if (n <= 1 || ns == 0) {
+        for (int j = 0; j < n; ++j) {
+            const int rc = f(s, j);
+            if (rc) return rc;
+        }
+        return TC_OK;
+    }
+    const int used = n - 1 < ns ? n - 1 : ns;
+    TC_CUDA(cudaEventRecord(g->fork, s));
+    for (int k = 0; k < used; ++k) TC_CUDA(cudaStreamWaitEvent(g->side[k], g->fork, 0));
+    int rc = TC_OK;
+    for (int j = 0; j < n && !rc; ++j) rc = f(j == 0 ? s : g->side[(j - 1) % ns], j);
+    // join even after a failed launch, so no side stream is left forked
+    for (int k = 0; k < used; ++k) {
+        TC_CUDA(cudaEventRecord(g->join[k], g->side[k]));
+        TC_CUDA(cudaStreamWaitEvent(s, g->join[k], 0));
+    }
+    return rc;
+}
+
+int launch_stage(tc_plan_group *g, int st, cudaStream_t s0, const float *x, float *y, const float *b,
                  const float *w, int mode, float *xo) {
-    for (size_t li = 0; li < g->launches.size(); ++li) {
-        const ClassLaunch &c = g->launches[li];
-        if (c.stage != st) continue;
+    std::vector<int> mine;
+    for (size_t li = 0; li < g->launches.size(); ++li)
+        if (g->launches[li].stage == st) mine.push_back((int)li);
+    return fan_out(g, s0, (int)mine.size(), [&](cudaStream_t s, int j) -> int {
+        const ClassLaunch &c = g->launches[mine[j]];
         const dim3 grid(c.grid), blk(c.threads);
         const size_t sm = c.smem;
 #define GK_PASS c.par
@@ -271,8 +317,8 @@ int launch_stage(tc_plan_group *g, int st, cudaStream_t s, const float *x, float
 #undef GK_PASS
         if (rc) return rc;
         TC_LAUNCHED("grouped pass");
-    }
-    return TC_OK;
+        return TC_OK;
+    });
 }
 
 struct GroupDevice {
@@ -392,6 +438,33 @@ int tc_plan_group_create(const tc_geom *geoms, const int *counts, int n_geoms, t
         rc = tc_cuda_fail(cudaGetLastError(), "tc_plan_group_create");
     for (ClassLaunch &c : g->launches)
         if (!rc) rc = class_config(c);
+    // side streams: as many as the widest stage (or the geometries, for the
+    // priors) needs beyond the caller's stream, at most GK_SIDE
+    int width = n;
+    for (int st = 0; st < GS_COUNT; ++st) {
+        int k = 0;
+        for (const ClassLaunch &c : g->launches) k += c.stage == st;
+        width = std::max(width, k);
+    }
+    const int nside = std::min(width - 1, GK_SIDE);
+    if (!rc && nside > 0) {
+        if (cudaEventCreateWithFlags(&g->fork, cudaEventDisableTiming) != cudaSuccess) rc = TC_ERR_CUDA;
+        for (int k = 0; k < nside && !rc; ++k) {
+            cudaStream_t q = nullptr;
+            cudaEvent_t e = nullptr;
+            if (cudaStreamCreateWithFlags(&q, cudaStreamNonBlocking) != cudaSuccess) {
+                rc = TC_ERR_CUDA;
+                break;
+            }
+            g->side.push_back(q);
+            if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+                rc = TC_ERR_CUDA;
+                break;
+            }
+            g->join.push_back(e);
+        }
+        if (rc) cudaGetLastError();
+    }
     if (rc) {
         group_free(g);
         return rc;
@@ -462,12 +535,13 @@ int mbir_grad_group(tc_plan_group *g, const float *x, const float *b, const floa
         (rc = launch_stage(g, GS_ADJ_COL, s, nullptr, nullptr, nullptr, nullptr, 0, grad)))
         return rc;
     if (prior && prior->lambda != 0.0) {
-        for (int i = 0; i < g->ng; ++i) {
+        // one prior launch (and its value reduction) per geometry, side by side
+        rc = fan_out(g, s, g->ng, [&](cudaStream_t q, int i) -> int {
             tc_plan *p = g->plans[i];
-            if ((rc = launch_prior_grad(p, x + g->xoff[i], grad + g->xoff[i], g->counts[i], prior,
-                                        obj ? obj + 2 * i + 1 : nullptr, s)))
-                return rc;
-        }
+            return launch_prior_grad(p, x + g->xoff[i], grad + g->xoff[i], g->counts[i], prior,
+                                     obj ? obj + 2 * i + 1 : nullptr, q);
+        });
+        if (rc) return rc;
     }
     return TC_OK;
 }

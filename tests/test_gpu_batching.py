@@ -103,7 +103,7 @@ def _rel(a, b):
 
 
 def test_plan_group_matches_per_geometry_plans(api):
-    """Persistent launches over the group's work lists (one per stage and
+    """Work-list launches over the group's items (one per stage and
     geometry class): A, A^T, and the MBIR gradient with weights and the
     26-neighbour prior (objective terms included) agree with one plan per
     geometry to FP32 rounding (the grouped kernels are compiled apart from
