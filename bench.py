@@ -172,7 +172,7 @@ def algorithmic_bytes(name, N, A, D, w, B):
         # the solver's fused form: f, g, x_prev read; x_{k+1} and the momentum point written
         "k_prior_next": 5 * img,
         "k_dots_gzx_gg": 3 * img,
-        "k_update": 3 * img,  # x_k and the next iterate read, z written (x_{k+1} stays where it was made)
+        "k_update": 5 * img,  # solver without a prior: x, z, g read; x_{k+1} and z_{k+1} written
         # normal operator A^T A (Toeplitz-plus-Hankel embedding): half-plane rows ky = 0..N
         "k_nrm_col_fwd": img + 8 * (N + 1) * N,
         "k_nrm_row": 2 * 8 * (N + 1) * N,
