@@ -109,3 +109,24 @@ def test_solver_options_layout_matches_the_header():
         names = re.findall(r"(\w+)\s*(?:\[\d+\])?\s*;", body)
         py_names = [f[0] for f in py._fields_]
         assert [n if n != "lambda" else "lam" for n in names] == py_names, (cname, names, py_names)
+
+
+def test_solver_state_follows_an_exchange_of_z_and_g():
+    """The solve may hand back state.z and state.g exchanged (a prior's solver
+    form makes z_{k+1} where the gradient was); the binding's SolveState then
+    swaps its two tensors to match, and refuses a pointer to neither."""
+    torch = pytest.importorskip("torch")
+    from paper_2304_12934_gb300 import api
+    st = api.SolveState(torch.zeros(2, 4, 4))
+    z0, g0 = st.z, st.g
+    cs = st._c()
+    cs.z, cs.g = g0.data_ptr(), z0.data_ptr()
+    cs.t, cs.k = 3.5, 7
+    st._load(cs)
+    assert st.z is g0 and st.g is z0 and st.k == 7 and st.t == 3.5
+    cs = st._c()
+    st._load(cs)  # not exchanged: unchanged
+    assert st.z is g0 and st.g is z0
+    cs.z = torch.zeros(1).data_ptr()
+    with pytest.raises(RuntimeError):
+        st._load(cs)
