@@ -130,3 +130,14 @@ def test_solver_state_follows_an_exchange_of_z_and_g():
     cs.z = torch.zeros(1).data_ptr()
     with pytest.raises(RuntimeError):
         st._load(cs)
+
+
+def test_sfu_probe_rejects_bad_arguments_without_gpu():
+    """tc_sfu_throughput checks its operation code and output pointer before
+    touching the device."""
+    from paper_2304_12934_gb300 import api
+    L = api.load()
+    out = ctypes.c_double()
+    for op in (-1, 3, 99):
+        assert L.tc_sfu_throughput(op, ctypes.byref(out), None) == -1
+    assert L.tc_sfu_throughput(0, None, None) == -1
