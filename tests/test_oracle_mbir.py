@@ -167,3 +167,30 @@ def test_monotone_variant_with_prior_and_weights():
     assert abs(phis[-1] - (G + Hl)) <= 1e-12 * phis[-1]
     G0, H0 = oracle.objective_value(np.zeros_like(x), b, w, lam, oracle.PAPER_PRIOR, 3, th)
     assert phis[-1] < 0.2 * (G0 + H0)
+
+
+def test_continuing_from_a_state_equals_the_uninterrupted_iteration():
+    """An iteration continued from (x_k, z_k, t_k) follows the uninterrupted
+    one: z_k is rebuilt from x_k, x_{k-1} and the logged t values by the
+    momentum rule, and two more iterations from there land on x_{k+2}
+    (rounding aside).  A high starting t makes the gradient test restart
+    early, so the continuation also carries a restart."""
+    N, A, D = 8, 10, 14
+    th, M = _tiny(N, A, D)
+    b = np.random.default_rng(0).standard_normal((1, A, D))
+    lam, k = 1e-3, 5  # from t = 20 this data restarts at the seventh iteration (index 6)
+    step = 1.0 / (1.05 * np.linalg.eigvalsh(M.T @ M).max() + lam * oracle.prior_lipschitz())
+    kw = dict(lam=lam, prior=oracle.PAPER_PRIOR, dims=2, theta=th, return_log=True)
+    z0 = np.zeros((1, N, N))
+    x_all, log_all = oracle.mbir_solve(b, None, N, k + 2, step, z0=z0, t0=20.0, **kw)
+    x_km1, _ = oracle.mbir_solve(b, None, N, k - 1, step, z0=z0, t0=20.0, **kw)
+    x_k, log_k = oracle.mbir_solve(b, None, N, k, step, z0=z0, t0=20.0, **kw)
+    t_prev = log_k[-2]["t"]  # t_{k-1} as used for z_k, unless iteration k restarted
+    if log_k[-1]["restart"]:
+        t_prev = 1.0
+    t_k = log_k[-1]["t"]
+    z_k = x_k + ((t_prev - 1.0) / t_k) * (x_k - x_km1)
+    x_cont, log_cont = oracle.mbir_solve(b, None, N, 2, step, x0=x_k, z0=z_k, t0=t_k, **kw)
+    assert any(e["restart"] for e in log_all)
+    assert [e["restart"] for e in log_cont] == [e["restart"] for e in log_all[k:]]
+    assert np.abs(x_cont - x_all).max() <= 1e-12 * max(1.0, np.abs(x_all).max())
