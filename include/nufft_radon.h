@@ -298,9 +298,11 @@ int mbir_solve(tc_plan *plan, const float *b, const float *w, float *x, int batc
  * receive the copies.  Inputs are copied host-to-device in slabs of max_batch
  * slices on a copy stream, and the result comes back on another (both
  * created and destroyed by the call); the first iteration's chunk c starts as
- * soon as slab c is resident, so the copies overlap the first iteration's
- * Radon work, and in the last iteration (gradient restart with a prior) each
- * slab's result leaves as soon as its prior is done.  The result x is copied
+ * soon as slab c is resident (for a resumed solve with a prior, as soon as its
+ * b and w are: only the prior reads x, and it waits for its slab), so the
+ * copies overlap the first iteration's Radon work, and in the last iteration
+ * (gradient restart or plain momentum with a prior) each slab's result leaves
+ * as soon as its prior is done.  The result x is copied
  * back to x_host and is also left in dev_x.  Synchronises before returning. */
 int mbir_solve_host(tc_plan *plan, const float *b_host, const float *w_host,
                     float *x_host, float *dev_b, float *dev_w, float *dev_x,

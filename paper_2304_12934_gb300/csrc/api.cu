@@ -80,10 +80,13 @@ int data_grad_chunk(tc_plan *p, const float *x, const float *b, const float *w, 
 // atb: A^T b of the whole batch for the normal-operator data term (W = I).
 // With dot_x the prior kernel leaves the next iterate in dot_x and the
 // momentum point of an iteration without restart in grad (launch_prior_grad).
+// x_ready: optional per-chunk events after which dot_x's slabs are resident
+// (ready then only covers b and w); the prior waits for all of them.
 int grad_impl(tc_plan *p, const float *x, const float *b, const float *w,
               const tc_prior *prior, float *grad, int batch, cudaStream_t s,
               bool want_value = true, const cudaEvent_t *ready = nullptr,
-              float *dot_x = nullptr, double step = 0.0, const float *atb = nullptr) {
+              float *dot_x = nullptr, double step = 0.0, const float *atb = nullptr,
+              const cudaEvent_t *x_ready = nullptr) {
     int rc = data_init(p, atb, s);
     if (rc) return rc;
     const size_t ni = img_elems(p), ns = sino_elems(p);
@@ -95,6 +98,8 @@ int grad_impl(tc_plan *p, const float *x, const float *b, const float *w,
         if (rc) return rc;
     }
     if (prior && prior->lambda != 0.0) {
+        // the copy stream is in order: its last slab's event covers every slab
+        if (x_ready) TC_CUDA(cudaStreamWaitEvent(s, x_ready[(batch - 1) / p->chunk], 0));
         rc = launch_prior_grad(p, x, grad, batch, prior, want_value ? p->scal + SC_PRIOR : nullptr, s, dot_x,
                                0, -1, step);
         if (rc) return rc;
@@ -371,16 +376,19 @@ struct HostOut {
 // iteration does); the restart test, and the copy of x_{k+1} over z_{k+1}
 // after a restart, follow at the end.  Same result as the resident iteration.
 // x holds x_k, z holds z_k and gb is the gradient buffer; on return x holds
-// x_{k+1} and gb holds z_{k+1}.
+// x_{k+1} and gb holds z_{k+1}.  ready: per-chunk events of the chunk's
+// inputs; x_ready (optional): of x's slabs, when ready covers b and w only.
 int last_iteration_streamed(tc_plan *p, const float *b, const float *w, float *x, const float *z, float *gb,
                             int batch, const tc_prior *prior, const tc_solve_opts *opts, double step,
-                            cudaStream_t s, const cudaEvent_t *ready, const HostOut &out, const float *atb) {
+                            cudaStream_t s, const cudaEvent_t *ready, const HostOut &out, const float *atb,
+                            const cudaEvent_t *x_ready = nullptr) {
     int rc0 = data_init(p, atb, s);
     if (rc0) return rc0;
     const size_t ni = img_elems(p), ns = sino_elems(p);
     const int nslab = (batch + p->chunk - 1) / p->chunk;
     auto finish = [&](int j) -> int {
         const int z0 = j * p->chunk, z1 = z0 + p->chunk < batch ? z0 + p->chunk : batch;
+        if (x_ready) TC_CUDA(cudaStreamWaitEvent(s, x_ready[j], 0));
         int rc = launch_prior_grad(p, z, gb, batch, prior, p->scal + SC_PRIOR, s, x, z0, z1, step);
         if (rc) return rc;
         cudaEvent_t e = nullptr;
@@ -405,9 +413,14 @@ int last_iteration_streamed(tc_plan *p, const float *b, const float *w, float *x
     return rc;
 }
 
+// ready: per-chunk events gating the first iteration (host streaming), after
+// which the chunk's b, w and x are resident; ready_bw (optional, z resident
+// already): after which its b and w are, so the chunk's data gradient can
+// start before its x arrives (only the prior reads x).
 int solve_loop(tc_plan *p, const float *b, const float *w, float *x, int batch,
                const tc_prior *prior, const tc_solve_opts *opts, tc_solve_state *st,
-               cudaStream_t s, bool fresh_z, const cudaEvent_t *ready, const HostOut *out = nullptr) {
+               cudaStream_t s, bool fresh_z, const cudaEvent_t *ready, const HostOut *out = nullptr,
+               const cudaEvent_t *ready_bw = nullptr) {
     const size_t n = img_elems(p) * batch;
     int rc;
     // the step: given, derived now (fresh solves only: z and g are free), or
@@ -444,6 +457,7 @@ int solve_loop(tc_plan *p, const float *b, const float *w, float *x, int batch,
         if ((rc = launch_dot(p, b, b, ns * batch, p->scal + SC_BB, s))) return rc;
         atb = st->atb;
         ready = nullptr;
+        ready_bw = nullptr;
     }
     if (opts->restart == 2) {
         // Monotone variant.  Phi(x_k) is recomputed at the start of every call
@@ -474,11 +488,14 @@ int solve_loop(tc_plan *p, const float *b, const float *w, float *x, int batch,
         float *zc = st->z, *gc = st->g;
         for (int it = 0; it < opts->n_iter; ++it) {
             const bool last = it == opts->n_iter - 1;  // the prior's value H is reported for the last point
-            const cudaEvent_t *rd = it == 0 ? ready : nullptr;
+            // the first iteration's chunks wait for their b and w (ready_bw) or
+            // all their inputs (ready); with ready_bw the priors wait for x
+            const cudaEvent_t *rd = it == 0 ? (ready_bw ? ready_bw : ready) : nullptr;
+            const cudaEvent_t *rx = it == 0 && ready_bw ? ready : nullptr;
             if (out && last) {
-                rc = last_iteration_streamed(p, b, w, x, zc, gc, batch, prior, opts, step, s, rd, *out, atb);
+                rc = last_iteration_streamed(p, b, w, x, zc, gc, batch, prior, opts, step, s, rd, *out, atb, rx);
             } else {
-                rc = grad_impl(p, zc, b, w, prior, gc, batch, s, last, rd, x, step, atb);
+                rc = grad_impl(p, zc, b, w, prior, gc, batch, s, last, rd, x, step, atb, rx);
                 if (!rc) rc = launch_solver_scalar(p, opts->restart, s);
                 if (!rc && opts->restart == 1) rc = launch_restart_fixup(p, gc, x, n, s);
             }
@@ -544,6 +561,7 @@ int check_solve(tc_plan *p, int batch, const tc_prior *prior, const tc_solve_opt
 struct CopyStream {
     cudaStream_t cs = nullptr, cs_out = nullptr;
     std::vector<cudaEvent_t> ev;      // inbound slabs (+ the start event); fixed during the solve
+    std::vector<cudaEvent_t> ev_bw;   // inbound b and w of each slab (when x is not needed first)
     std::vector<cudaEvent_t> out_ev;  // outbound slabs, appended while the last iteration runs
     void sync() {
         if (cs) cudaStreamSynchronize(cs);
@@ -553,6 +571,8 @@ struct CopyStream {
         for (cudaEvent_t e : ev)
             if (e) cudaEventDestroy(e);
         for (cudaEvent_t e : out_ev)
+            if (e) cudaEventDestroy(e);
+        for (cudaEvent_t e : ev_bw)
             if (e) cudaEventDestroy(e);
         if (cs_out && cs_out != cs) cudaStreamDestroy(cs_out);
         if (cs) cudaStreamDestroy(cs);
@@ -705,7 +725,12 @@ int mbir_solve_host(tc_plan *p, const float *b_host, const float *w_host, float 
         TC_CUDA(cudaEventRecord(start, s));
         TC_CUDA(cudaStreamWaitEvent(cp.cs, start, 0));
         // slab c of b, w and x goes in on the copy stream; the first iteration's
-        // chunk c starts once its slab is resident
+        // chunk c starts once its slab is resident.  A resumed solve with a
+        // prior (z resident, x read by the prior only) starts chunk c's data
+        // gradient once b and w have arrived, and each prior waits for its x.
+        const bool early = st->k > 0 && !derive && opts->n_iter > 0 && !opts->normal && opts->restart != 2 &&
+                           prior && prior->lambda != 0.0;
+        if (early) cp.ev_bw.assign(nslab, nullptr);
         int rc;
         for (int c = 0; c < nslab; ++c) {
             const size_t s0 = (size_t)c * p->chunk;
@@ -716,6 +741,10 @@ int mbir_solve_host(tc_plan *p, const float *b_host, const float *w_host, float 
             if (w_host && (rc = host_copy_async(dev_w + s0 * ns, w_host + s0 * ns, nb * ns * sizeof(float),
                                                 cudaMemcpyHostToDevice, cp.cs)))
                 return rc;
+            if (early) {
+                TC_CUDA(cudaEventCreateWithFlags(&cp.ev_bw[c], cudaEventDisableTiming));
+                TC_CUDA(cudaEventRecord(cp.ev_bw[c], cp.cs));
+            }
             if ((rc = host_copy_async(dev_x + s0 * ni, x_host + s0 * ni, nb * ni * sizeof(float),
                                       cudaMemcpyHostToDevice, cp.cs)))
                 return rc;
@@ -735,7 +764,8 @@ int mbir_solve_host(tc_plan *p, const float *b_host, const float *w_host, float 
         const bool stream_out = opts->n_iter > 0 && opts->restart != 2 && prior && prior->lambda != 0.0;
         const HostOut out{x_host, cp.cs_out, &cp.out_ev};
         rc = solve_loop(p, dev_b, w_host ? dev_w : nullptr, dev_x, batch, prior, opts, st, s, derive,
-                        overlap ? cp.ev.data() : nullptr, stream_out ? &out : nullptr);
+                        overlap ? cp.ev.data() : nullptr, stream_out ? &out : nullptr,
+                        early && overlap ? cp.ev_bw.data() : nullptr);
         if (rc) return rc;
         if (!stream_out &&
             (rc = host_copy_async(x_host, dev_x, (size_t)batch * ni * sizeof(float), cudaMemcpyDeviceToHost, s)))

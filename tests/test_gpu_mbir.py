@@ -243,6 +243,32 @@ def test_host_streamed_solve_in_slabs_matches_device_solve(api, n_iter):
     assert abs(sh.obj[1] - sd.obj[1]) <= 1e-9 * abs(sd.obj[1])
 
 
+@pytest.mark.parametrize("n_iter", [3, 1])
+def test_resumed_host_streamed_solve_matches_device_solve(api, n_iter):
+    """A resumed solve from host buffers (z already on the device) starts each
+    chunk's data gradient once the chunk's b and w have arrived, and each
+    prior waits for its slab of x: identical to the resumed device solve."""
+    B = 5
+    f, b = _data(B)
+    rng = np.random.default_rng(11)
+    w = rng.uniform(0.5, 1.0, b.shape)
+    step = _step(1e-3)
+    prior = api.Prior(lam=1e-3, dims=3)
+    with api.Plan(N, A, D, max_batch=2) as plan:
+        x = torch.zeros((B, N, N), device="cuda:0")
+        sd = api.mbir_solve(plan, t32(b), t32(w), x, 2, step, prior)
+        api.mbir_solve(plan, t32(b), t32(w), x, n_iter, step, prior, state=sd)
+        bh = torch.tensor(b, dtype=torch.float32).pin_memory()
+        wh = torch.tensor(w, dtype=torch.float32).pin_memory()
+        xh = torch.zeros((B, N, N), dtype=torch.float32).pin_memory()
+        dev = {}
+        sh = api.mbir_solve_host(plan, bh, wh, xh, 2, step, prior, dev=dev)
+        api.mbir_solve_host(plan, bh, wh, xh, n_iter, step, prior, state=sh, dev=dev)
+    assert torch.equal(xh, x.cpu())
+    assert sh.k == sd.k == 2 + n_iter and sh.n_restarts == sd.n_restarts
+    assert torch.equal(sh.z.cpu(), sd.z.cpu())
+
+
 @pytest.mark.parametrize("dims", [3, 2])
 def test_prior_on_a_tall_volume_matches_oracle(api, dims):
     """150 slices of 128^2: tiles inside the volume and at its border, and
