@@ -37,7 +37,7 @@ _SRC = os.path.join(_HERE, "radon_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _SO = os.path.join(_BUILD, "liboracle_radon.so")
 
-# Sec. 5: "p = 1.2, sigma = 1/0.7 and c = 0.0001"
+# Sec. 5 hyper-parameters of the prior: p 1.2, sigma 1/0.7, c 1e-4
 PAPER_PRIOR = dict(p=1.2, sigma=1.0 / 0.7, c=1e-4)
 
 
