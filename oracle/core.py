@@ -10,9 +10,9 @@ restatement of the paper's definitions:
   that its gradient is Eq. gradient's A^T (Af - b) (weighted by W).
 * Prior: Sec. 3 Eqs. reg2/reg3 (qGGMRF over the 1-hop neighbourhood), with the
   paper's hyper-parameters p=1.2, sigma=1/0.7, c=1e-4 (Sec. 5).
-* Optimizer: Sec. 3 last paragraph ("monotonic accelerated gradient method
-  with restart"), read as FISTA with a constant step and the gradient restart
-  test.  This schedule is parity unpinned by the paper beyond the invariants
+* Optimizer: Sec. 3 last paragraph (an accelerated gradient method that is
+  monotone and restarts), read as FISTA with a constant step and the gradient
+  restart test.  This schedule is parity unpinned by the paper beyond the invariants
   tested in tests/test_oracle_mbir.py.
 """
 from __future__ import annotations
@@ -318,7 +318,7 @@ def mbir_solve(b, wt, n, n_iter, step, lam=1.0, prior=None, dims=2,
     (zero by default) with t_0 = 1; all scalars FP64.  z0 and t0 continue an
     iteration from a given state (x_k, z_k, t_k) instead: x_0 = x0, z_0 = z0.
 
-    Reading of "monotonic accelerated gradient method with restart":
+    Reading of the end of Sec. 3 (accelerated gradient, monotone, with restart):
         v       = z_k - step * grad Phi(z_k)
         restart = True (gradient restart):
             x_{k+1} = v; restart (t_k := 1) if <grad Phi(z_k), x_{k+1} - x_k> > 0
