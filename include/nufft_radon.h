@@ -5,7 +5,7 @@
  *   A   = discrete Radon transform R (Sec. 2.1 Eq. radon_transform, Eq. line_eqn),
  *         evaluated through the Fourier-slice theorem (Eq. fourier_radon) with a
  *         NUFFT: row DFT, gridding on a 2x oversampled Cartesian grid, 2D FFT and
- *         deapodisation (Sec. 2.2 Eqs. nufft, nufft2, nufft3, "in reverse order").
+ *         deapodisation (Sec. 2.2 Eqs. nufft, nufft2, nufft3, run backwards, as Sec. 2.2 notes for the Radon transform).
  *   A^T = its exact adjoint R* (Sec. 3 Eq. transpose).
  *   MBIR objective  Phi(f) = 1/2 ||A f - b||_W^2 + lambda H(f)  (Sec. 3 Eq. objfn,
  *         gradient Eq. gradient), H the qGGMRF prior (Sec. 3 Eqs. reg2, reg3).
